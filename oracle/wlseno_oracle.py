@@ -1,0 +1,574 @@
+"""Plain, slow FP64 CPU oracle of the WLS-ENO finite-volume hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls or
+executes this file: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` do.  It shares no
+code with the CUDA library (paper_1602_02694_gb300/csrc) and imports nothing
+from the package; its inputs are plain numpy arrays.
+
+Everything is FP64 and written cell by cell, in the paper's order and
+notation, from:
+
+  Liu & Jiao, "WLS-ENO: Weighted-Least-Squares Based Essentially
+  Non-Oscillatory Schemes for Finite Volume Methods on Unstructured Meshes"
+  (arXiv 1602.02694).
+
+  Sec. 1, Eq. (fvm) and Eq. (flux) ....... finite-volume update, LF flux
+  Sec. 3.1.1, Eq. (average_eq), Eq. (WLS)  Taylor-moment system, weighted LS
+  Sec. 3.1.2, Eqs. (smoothness indicator), (weight)   beta_j, omega_j
+  Sec. 3.2 ............................... 2-D/3-D moments about the centroid,
+                                           k-ring stencils (1/2- and 1/3-ring)
+  Sec. 3.3.1 ............................. half-facet sibling adjacency
+  Sec. 3.3.2, Eq. (scaled_WLS) ........... column scaling, QR with column
+                                           pivoting, rank-truncated solve
+  Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta)  TVD-RK3 (Shu-Osher)
+
+Readings where the paper is silent, garbled or ambiguous (each is listed in
+the design notes of the repository):
+  * Eq. (fvm) prints the boundary integral multiplied by |tau_i|; it is
+    divided by |tau_i| here (the definition of the cell average above it).
+  * moments are divided by |tau_j| (the stencil cell), factorials per term.
+  * h in eps*h^2 is the mean edge length of the centre cell tau_i.
+  * beta_i of the centre cell is the minimum of beta_j over the stencil cells
+    that share a facet with tau_i (1-D: tau_{i-1}, tau_{i+1}).
+  * rows of the least-squares system are multiplied by omega_j (not sqrt).
+  * the expansion point is the centroid of tau_i in every dimension; the
+    unknowns are h-normalised, d_kappa = h_i^|kappa| d^kappa u(x_i).
+  * numerical rank r = #{k : |R_kk| > rank_tol * |R_11|}; coefficients of
+    dropped columns are 0 (basic solution).
+  * facet quadrature: Gauss-Legendre with 2 points per edge in 2-D, the
+    degree-2 three-point rule at barycentric (2/3,1/6,1/6) in 3-D.
+  * Lax-Friedrichs alpha: |velocity| for advection; per facet the maximum
+    over its quadrature points and both sides of |F'(u).n| for Burgers and
+    of |u.n| + c for Euler.
+  * time step dt = CFL * min_i r_i / lambda_max with r_i = d|tau_i|/|d tau_i|.
+  * periodic meshes: each stencil cell is taken at its minimum-image copy.
+  * transmissive boundary facets use u+ = u-.
+
+Parity of every function here is pinned in tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+
+
+# ----------------------------------------------------------------------------
+# geometry (Sec. 1: cells tau_i, volumes |tau_i|, centroids; Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def min_image(delta, period):
+    """Wrap a coordinate difference into the nearest periodic image."""
+    delta = np.array(delta, dtype=np.float64)
+    for c in range(delta.shape[-1]):
+        if period[c] > 0:
+            delta[..., c] -= period[c] * np.round(delta[..., c] / period[c])
+    return delta
+
+
+def unwrap_cell(vertices, cell, period):
+    """Vertex coordinates of one cell as a connected simplex (minimum image
+    relative to its first vertex)."""
+    x0 = vertices[cell[0]]
+    return np.array([x0 + min_image(vertices[v] - x0, period) for v in cell])
+
+
+def simplex_volume(X):
+    d = X.shape[1]
+    return abs(np.linalg.det((X[1:] - X[0]).reshape(d, d))) / math.factorial(d)
+
+
+def facet_measure(F):
+    """(d-1)-measure of a facet given by d points in R^d."""
+    d = F.shape[1]
+    if d == 1:
+        return 1.0
+    E = (F[1:] - F[0])
+    G = E @ E.T
+    return math.sqrt(max(np.linalg.det(G), 0.0)) / math.factorial(d - 1)
+
+
+@dataclass
+class Geometry:
+    coords: np.ndarray      # [N][d+1][d] unwrapped vertex coordinates
+    centroid: np.ndarray    # [N][d]
+    volume: np.ndarray      # [N]
+    h: np.ndarray           # [N] mean edge length
+    inradius: np.ndarray    # [N] d*|tau| / |d tau|
+
+
+def geometry(vertices, cells, period):
+    N, dp1 = cells.shape
+    d = dp1 - 1
+    coords = np.array([unwrap_cell(vertices, cells[c], period) for c in range(N)])
+    centroid = coords.mean(axis=1)
+    volume = np.array([simplex_volume(coords[c]) for c in range(N)])
+    h = np.zeros(N)
+    inr = np.zeros(N)
+    for c in range(N):
+        edges = [np.linalg.norm(coords[c][a] - coords[c][b])
+                 for a, b in itertools.combinations(range(dp1), 2)]
+        h[c] = float(np.mean(edges))
+        bnd = sum(facet_measure(np.delete(coords[c], f, axis=0)) for f in range(dp1))
+        inr[c] = d * volume[c] / bnd
+    return Geometry(coords, centroid, volume, h, inr)
+
+
+# ----------------------------------------------------------------------------
+# half-facet adjacency (Sec. 3.3.1) and k-ring stencils (Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def sibling_half_facets(cells):
+    """For each half-facet (cell c, local facet f = the facet opposite local
+    vertex f) the sibling (c', f'), or (-1, -1) on the boundary."""
+    N, dp1 = cells.shape
+    owner = {}
+    sib = -np.ones((N, dp1, 2), dtype=np.int64)
+    for c in range(N):
+        for f in range(dp1):
+            key = tuple(sorted(int(v) for k, v in enumerate(cells[c]) if k != f))
+            if key in owner:
+                c2, f2 = owner.pop(key)
+                sib[c, f] = (c2, f2)
+                sib[c2, f2] = (c, f)
+            else:
+                owner[key] = (c, f)
+    return sib
+
+
+def sharing_neighbours(cells, min_shared):
+    """Cells sharing at least ``min_shared`` vertices with each cell
+    (d vertices: facet neighbours; 1 vertex: the 1-ring)."""
+    N = cells.shape[0]
+    v2c = {}
+    for c in range(N):
+        for v in cells[c]:
+            v2c.setdefault(int(v), []).append(c)
+    out = []
+    for c in range(N):
+        count = {}
+        for v in cells[c]:
+            for c2 in v2c[int(v)]:
+                if c2 != c:
+                    count[c2] = count.get(c2, 0) + 1
+        out.append(sorted(c2 for c2, k in count.items() if k >= min_shared))
+    return out
+
+
+def ring_levels(d, ring):
+    """Decompose a ring size into increments: 2-D uses 1/2-ring steps
+    (edge-sharing) and 1-ring steps (vertex-sharing); 3-D uses 1/3 (face),
+    2/3 (edge) and 1 (vertex) steps, as in Sec. 3.2."""
+    k = int(math.floor(ring + 1e-9))
+    frac = ring - k
+    steps = ["vertex"] * k
+    if abs(frac) < 1e-6:
+        return steps
+    if d == 2 and abs(frac - 0.5) < 1e-6:
+        return steps + ["facet"]
+    if d == 3 and abs(frac - 1.0 / 3.0) < 1e-3:
+        return steps + ["facet"]
+    if d == 3 and abs(frac - 2.0 / 3.0) < 1e-3:
+        return steps + ["edge"]
+    raise ValueError(f"ring {ring} is not a valid increment in {d}-D")
+
+
+def k_ring(c, steps, nbr):
+    """The k-ring neighbourhood of cell c: start from {c}; each step adds the
+    neighbours (of the step's kind) of every cell collected so far."""
+    ring = {c}
+    for kind in steps:
+        grown = set(ring)
+        for c2 in ring:
+            grown.update(nbr[kind][c2])
+        ring = grown
+    return ring
+
+
+def build_stencils(cells, ring, dim, radius_cut=0.0, centroid=None, h=None, period=None):
+    """Stencil S(i) of every cell: the centre cell first, then the others in
+    increasing cell index.  With radius_cut > 0, cells of the next whole
+    vertex-sharing ring (ceil(ring) rings) whose centroid lies within
+    radius_cut * h_i of x_i are added too."""
+    nbr = {"facet": sharing_neighbours(cells, dim),
+           "vertex": sharing_neighbours(cells, 1)}
+    if dim == 3:
+        nbr["edge"] = sharing_neighbours(cells, 2)
+    steps = ring_levels(dim, ring)
+    out = []
+    for c in range(cells.shape[0]):
+        S = k_ring(c, steps, nbr)
+        if radius_cut > 0:
+            outer = k_ring(c, ["vertex"] * (int(math.floor(ring + 1e-9)) + 1), nbr) - S
+            for c2 in outer:
+                dx = min_image(centroid[c2] - centroid[c], period)
+                if np.linalg.norm(dx) <= radius_cut * h[c]:
+                    S.add(c2)
+        out.append([c] + sorted(S - {c}))
+    return out, nbr["facet"]
+
+
+def grow_to_min_rows(stencils, cells, dim, min_rows):
+    """Transmissive boundaries: grow a short stencil by facet-neighbour
+    increments until it has at least min_rows cells."""
+    nbr = sharing_neighbours(cells, dim)
+    out = []
+    for S in stencils:
+        s = set(S)
+        while len(s) < min_rows:
+            grown = set(s)
+            for c2 in s:
+                grown.update(nbr[c2])
+            if grown == s:
+                break
+            s = grown
+        out.append([S[0]] + sorted(s - {S[0]}))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Taylor moments (Sec. 3.1.1, Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def multi_indices(d, p):
+    """Exponents kappa with |kappa| <= p-1: degree-major, then descending
+    powers of x, then y (1, x, y, x^2, xy, y^2, ...)."""
+    out = []
+    for q in range(p):
+        for kappa in itertools.product(range(q, -1, -1), repeat=d):
+            if sum(kappa) == q:
+                out.append(kappa)
+    # itertools.product with descending ranges already lists x-major first
+    return out
+
+
+def compositions(k, parts):
+    """All tuples of ``parts`` non-negative integers summing to k."""
+    if parts == 1:
+        yield (k,)
+        return
+    for a in range(k, -1, -1):
+        for rest in compositions(k - a, parts - 1):
+            yield (a,) + rest
+
+
+def simplex_monomial_integral(Y, kappa):
+    """Exact integral over the simplex with vertices Y [d+1][d] of
+    prod_c y_c^kappa_c, from y = sum_v lambda_v Y_v, the multinomial theorem
+    and int_T lambda^alpha = d! |T| alpha! / (|alpha| + d)!."""
+    dp1, d = Y.shape
+    vol = simplex_volume(Y)
+    per_axis = [list(compositions(kappa[c], dp1)) for c in range(d)]
+    total = 0.0
+    for choice in itertools.product(*per_axis):
+        coef = 1.0
+        alpha = [0] * dp1
+        for c in range(d):
+            beta = choice[c]
+            coef *= math.factorial(kappa[c])
+            for v in range(dp1):
+                coef /= math.factorial(beta[v])
+                coef *= Y[v, c] ** beta[v]
+                alpha[v] += beta[v]
+        a_fact = 1.0
+        for v in range(dp1):
+            a_fact *= math.factorial(alpha[v])
+        total += coef * math.factorial(d) * vol * a_fact / math.factorial(sum(alpha) + d)
+    return total
+
+
+def moment_row(Yj, xi, hi, kappas):
+    """Row of A for stencil cell tau_j: (1/|tau_j|) int_{tau_j}
+    prod_c ((x_c - x_i,c)/h_i)^kappa_c / kappa_c!  for every kappa."""
+    Y = (Yj - xi) / hi
+    volY = simplex_volume(Y)
+    row = np.empty(len(kappas))
+    for k, kappa in enumerate(kappas):
+        fact = 1.0
+        for e in kappa:
+            fact *= math.factorial(e)
+        row[k] = simplex_monomial_integral(Y, kappa) / (volY * fact)
+    return row
+
+
+def stencil_coords(geo, S, i, period):
+    """Vertex coordinates of every stencil cell at its minimum-image copy
+    nearest to tau_i."""
+    out = []
+    for j in S:
+        shift = min_image(geo.centroid[j] - geo.centroid[i], period) - (geo.centroid[j] - geo.centroid[i])
+        out.append(geo.coords[j] + shift)
+    return out
+
+
+def moment_matrix(geo, S, i, p, period):
+    """The n x m matrix A of Eq. (average_eq) for cell i on stencil S, in
+    h_i-normalised unknowns."""
+    d = geo.coords.shape[2]
+    kappas = multi_indices(d, p)
+    Ys = stencil_coords(geo, S, i, period)
+    return np.array([moment_row(Yj, geo.centroid[i], geo.h[i], kappas) for Yj in Ys])
+
+
+# ----------------------------------------------------------------------------
+# weights (Sec. 3.1.2) and the scaled weighted least squares (Sec. 3.3.2)
+# ----------------------------------------------------------------------------
+
+def wls_eno_weights(ubar_S, face_mask, h, eps=1e-2, alpha_c=1.5):
+    """omega_j of Eq. (weight) from beta_j of Eq. (smoothness indicator).
+
+    ubar_S[0] is the centre cell; face_mask marks the stencil cells that share
+    a facet with it (the centre's beta is their minimum)."""
+    ubar_S = np.asarray(ubar_S, dtype=np.float64)
+    n = len(ubar_S)
+    beta = np.empty(n)
+    for j in range(1, n):
+        beta[j] = (ubar_S[j] - ubar_S[0]) ** 2 + eps * h * h
+    beta[0] = min(beta[j] for j in range(1, n) if face_mask[j])
+    omega = 1.0 / beta
+    omega[0] = alpha_c / beta[0]
+    return omega
+
+
+def scaled_wls_solve(A, omega, rhs, rank_tol=1e-10):
+    """Minimise ||W A S d - W rhs||_2 (Eq. (scaled_WLS)) with W = diag(omega),
+    S = diag(1/||column of W A||), by QR with column pivoting
+    (W A S E = Q R); the solution is v = S E R^-1 Q^T W rhs restricted to the
+    numerical rank r (dropped coefficients are 0).  Returns (v, rank, R)."""
+    WA = omega[:, None] * A
+    s = 1.0 / np.linalg.norm(WA, axis=0)
+    B = WA * s[None, :]
+    Q, R, piv = scipy.linalg.qr(B, mode="economic", pivoting=True)
+    diag = np.abs(np.diag(R))
+    r = int(np.sum(diag > rank_tol * diag[0]))
+    c = Q[:, :r].T @ (omega * rhs)
+    y = scipy.linalg.solve_triangular(R[:r, :r], c, lower=False)
+    dvec = np.zeros(A.shape[1])
+    dvec[piv[:r]] = y
+    return s * dvec, r, R
+
+
+# ----------------------------------------------------------------------------
+# the reconstruction of every cell
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    vertices: np.ndarray
+    cells: np.ndarray
+    period: np.ndarray
+    p: int
+    ring: float
+    pde: int = ADVECTION
+    velocity: tuple = (1.0, 1.0, 0.0)
+    gamma: float = 1.4
+    eps: float = 1e-2
+    alpha_c: float = 1.5
+    rank_tol: float = 1e-10
+    radius_cut: float = 0.0
+    min_rows: int = 0
+
+    def __post_init__(self):
+        self.vertices = np.asarray(self.vertices, dtype=np.float64)
+        self.cells = np.asarray(self.cells, dtype=np.int64)
+        self.period = np.asarray(self.period, dtype=np.float64)
+        self.dim = self.cells.shape[1] - 1
+        self.geo = geometry(self.vertices, self.cells, self.period)
+        self.stencils, self.face_nbrs = build_stencils(
+            self.cells, self.ring, self.dim, self.radius_cut,
+            self.geo.centroid, self.geo.h, self.period)
+        if self.min_rows:
+            self.stencils = grow_to_min_rows(self.stencils, self.cells, self.dim, self.min_rows)
+        self.kappas = multi_indices(self.dim, self.p)
+        self.m = len(self.kappas)
+        self.sib = sibling_half_facets(self.cells)
+        self._A = {}
+
+    @property
+    def N(self):
+        return self.cells.shape[0]
+
+    def A(self, i):
+        if i not in self._A:
+            self._A[i] = moment_matrix(self.geo, self.stencils[i], i, self.p, self.period)
+        return self._A[i]
+
+    def reconstruct_cell(self, ubar, i):
+        """h-normalised Taylor coefficients d of cell i (v = d / h^|kappa|) and
+        the numerical rank of its scaled system."""
+        S = self.stencils[i]
+        face = set(self.face_nbrs[i])
+        mask = [j in face for j in S]
+        uS = np.asarray([ubar[j] for j in S])
+        omega = wls_eno_weights(uS, mask, self.geo.h[i], self.eps, self.alpha_c)
+        dvec, r, _ = scaled_wls_solve(self.A(i), omega, uS, self.rank_tol)
+        return dvec, r
+
+    def derivatives(self, dvec, i):
+        """Unscaled derivatives d^kappa u(x_i) from h-normalised coefficients."""
+        return np.array([dvec[k] / self.geo.h[i] ** sum(kap) for k, kap in enumerate(self.kappas)])
+
+    def eval_poly(self, dvec, i, x):
+        """Reconstruction of cell i at the point x (given near tau_i)."""
+        y = (np.asarray(x) - self.geo.centroid[i]) / self.geo.h[i]
+        total = 0.0
+        for k, kap in enumerate(self.kappas):
+            term = dvec[k]
+            for c, e in enumerate(kap):
+                term *= y[c] ** e / math.factorial(e)
+            total += term
+        return total
+
+
+# ----------------------------------------------------------------------------
+# facet quadrature and the Lax-Friedrichs flux (Sec. 1, Eq. (flux))
+# ----------------------------------------------------------------------------
+
+def facet_rule(F):
+    """Quadrature points and weights (summing to 1) on a facet with vertices F."""
+    d = F.shape[1]
+    if d == 1:
+        return F.copy(), np.array([1.0])
+    if d == 2:
+        g = 0.5 / math.sqrt(3.0)
+        t = np.array([0.5 - g, 0.5 + g])
+        return np.array([F[0] + tt * (F[1] - F[0]) for tt in t]), np.array([0.5, 0.5])
+    if d == 3:
+        bary = [(2 / 3, 1 / 6, 1 / 6), (1 / 6, 2 / 3, 1 / 6), (1 / 6, 1 / 6, 2 / 3)]
+        return np.array([sum(b[k] * F[k] for k in range(3)) for b in bary]), np.full(3, 1.0 / 3.0)
+    raise ValueError(d)
+
+
+def outward_normal(X, f):
+    """Unit normal of local facet f (opposite vertex f) pointing out of the simplex X."""
+    dp1, d = X.shape
+    F = np.delete(X, f, axis=0)
+    if d == 1:
+        n = np.array([1.0])
+    elif d == 2:
+        e = F[1] - F[0]
+        n = np.array([e[1], -e[0]])
+    else:
+        n = np.cross(F[1] - F[0], F[2] - F[0])
+    n = n / np.linalg.norm(n)
+    if np.dot(F.mean(axis=0) - X[f], n) < 0:
+        n = -n
+    return n
+
+
+def physical_flux(prob, u):
+    """F(u) for the scalar equations as a vector in R^d."""
+    d = prob.dim
+    if prob.pde == ADVECTION:
+        return np.asarray(prob.velocity[:d]) * u
+    if prob.pde == BURGERS:
+        return np.full(d, 0.5 * u * u)
+    raise ValueError(prob.pde)
+
+
+def normal_speed(prob, u, n):
+    if prob.pde == ADVECTION:
+        return float(np.linalg.norm(prob.velocity[:prob.dim]))
+    if prob.pde == BURGERS:
+        return abs(u * float(np.sum(n)))
+    raise ValueError(prob.pde)
+
+
+def lax_friedrichs(prob, um, up, n, alpha):
+    """Eq. (flux): 1/2 [ (F(u-) + F(u+)) . n - alpha (u+ - u-) ]."""
+    return 0.5 * (np.dot(physical_flux(prob, um) + physical_flux(prob, up), n) - alpha * (up - um))
+
+
+def facets(prob):
+    """Each facet once: (left cell L, its local facet fL, right cell R or -1)."""
+    out = []
+    for c in range(prob.N):
+        for f in range(prob.dim + 1):
+            c2, _ = prob.sib[c, f]
+            if c2 < 0 or c < c2:
+                out.append((c, f, int(c2)))
+    return out
+
+
+def reconstruct_all(prob, ubar):
+    return [prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)]
+
+
+def facet_states(prob, coeffs, L, fL, R):
+    """Quadrature points (in L's frame), weights, measure, outward normal of
+    L, and the traces u- (from L) and u+ (from R, or u- on a boundary)."""
+    X = prob.geo.coords[L]
+    F = np.delete(X, fL, axis=0)
+    pts, w = facet_rule(F)
+    area = facet_measure(F)
+    n = outward_normal(X, fL)
+    um = np.array([prob.eval_poly(coeffs[L], L, x) for x in pts])
+    if R < 0:
+        up = um.copy()
+    else:
+        # the same physical points seen from the nearest copy of tau_R
+        shift = min_image(prob.geo.centroid[R] - prob.geo.centroid[L], prob.period) - \
+            (prob.geo.centroid[R] - prob.geo.centroid[L])
+        up = np.array([prob.eval_poly(coeffs[R], R, x - shift) for x in pts])
+    return pts, w, area, n, um, up
+
+
+def facet_flux(prob, coeffs, L, fL, R):
+    """Integral of the LF numerical flux over the facet (outward from L)."""
+    pts, w, area, n, um, up = facet_states(prob, coeffs, L, fL, R)
+    if prob.pde == ADVECTION:
+        alpha = normal_speed(prob, 0.0, n)
+    else:
+        alpha = max(max(normal_speed(prob, a, n), normal_speed(prob, b, n)) for a, b in zip(um, up))
+    return area * sum(w[q] * lax_friedrichs(prob, um[q], up[q], n, alpha) for q in range(len(w)))
+
+
+def residual(prob, ubar, coeffs=None):
+    """L(ubar)_i = -(1/|tau_i|) * sum over facets of the integrated numerical
+    flux out of tau_i (Eq. (fvm), divided by |tau_i|)."""
+    if coeffs is None:
+        coeffs = reconstruct_all(prob, ubar)
+    flux_out = np.zeros(prob.N)
+    for L, fL, R in facets(prob):
+        g = facet_flux(prob, coeffs, L, fL, R)
+        flux_out[L] += g
+        if R >= 0:
+            flux_out[R] -= g
+    return -flux_out / prob.geo.volume
+
+
+def max_wave_speed(prob, ubar):
+    if prob.pde == ADVECTION:
+        return float(np.linalg.norm(prob.velocity[:prob.dim]))
+    if prob.pde == BURGERS:
+        return math.sqrt(prob.dim) * float(np.max(np.abs(ubar)))
+    raise ValueError(prob.pde)
+
+
+def cfl_dt(prob, ubar, cfl):
+    return cfl * float(np.min(prob.geo.inradius)) / max_wave_speed(prob, ubar)
+
+
+def rk3_step(L, u, dt):
+    """Eq. (3rd-order-Runge-Kutta): the Shu-Osher TVD-RK3 stage sequence."""
+    k1 = u + dt * L(u)
+    k2 = 0.75 * u + 0.25 * k1 + 0.25 * dt * L(k1)
+    return u / 3.0 + 2.0 / 3.0 * k2 + 2.0 / 3.0 * dt * L(k2)
+
+
+def rk3_run(prob, ubar, n_steps, cfl=None, dt=None):
+    """n_steps TVD-RK3 steps; dt from the CFL rule at the start of each step
+    unless given.  Returns (ubar, list of dt)."""
+    u = np.array(ubar, dtype=np.float64)
+    dts = []
+    for _ in range(n_steps):
+        step = dt if dt is not None else cfl_dt(prob, u, cfl)
+        u = rk3_step(lambda x: residual(prob, x), u, step)
+        dts.append(step)
+    return u, dts
