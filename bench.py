@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Throughput of the WLS-ENO hot path: cell-stage updates per second.
+
+Workload: 2-D Burgers u_t + (u^2/2)_x + (u^2/2)_y = 0 on the periodic unit
+square, 256 x 256 squares split into 131,072 jittered triangles (vertex
+jitter U(-0.2h, 0.2h), seed 1), cubic WLS-ENO reconstruction (p = 4, m = 10)
+on the 2-ring stencil (37 cells), Lax-Friedrichs flux with 2 Gauss points per
+edge, TVD-RK3 at CFL 0.3 with the time step recomputed every step on the
+device, initial data 0.5 + sin(2 pi (x + y)).  One step = one TVD-RK3 step
+(three stages) over all cells; value = cells x 3 x steps / device time.
+The headline is the FP32-bulk path; the plain FP64 GPU path runs the same
+steps from the same state for the speedup and the accuracy comparison.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+(N > 1 under torch.distributed.run: independent replicas, one per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1602_02694_gb300 import synth  # noqa: E402
+
+METRIC = "cell-stage updates/sec (WLS-ENO recon+flux) vs plain FP64 GPU, equal accuracy"
+UNIT = "cell-stage updates/s"
+WORKLOAD = ("2-D Burgers, periodic 256x256 jittered triangulated grid (131,072 cells), "
+            "p=4 (m=10), 2-ring stencil (37 cells), LF flux, TVD-RK3 CFL 0.3")
+N_SIDE, P_ORDER, RING, CFL, JITTER, SEED = 256, 4, 2.0, 0.3, 0.2, 1
+FP32_PEAK_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
+N_SMS = 152
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="wlseno", choices=["wlseno", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE, help="squares per side (default 256)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU work of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def algorithmic_flops_per_cell(n, m, npts):
+    """Floating-point work one cell's reconstruction needs by the algorithm
+    (weights, W A, column scaling, m Householder steps with recomputed
+    trailing norms on the n x (m+1) system, triangular solve, evaluation at
+    the facet points); padding lanes are not counted."""
+    f = 6 * n                       # differences, squares, eps h^2, divide
+    f += n * m + 3 * n * m          # W A; column norms and scaling
+    for k in range(m):
+        rows = n - k
+        cols = m - k
+        f += 2 * rows * cols        # trailing column norms
+        f += 4 * rows * cols        # reflector applied to the other columns and rhs
+        f += 3 * rows               # reflector
+    f += m * m                      # back substitution
+    f += npts * (2 * m + 8)         # monomials and dot product per facet point
+    return f
+
+
+def algorithmic_bytes_per_cell(n, m, npts, dim, a_bytes):
+    """Bytes one cell's reconstruction must move at least once: its stencil
+    rows of A, its stencil indices, its own state, h, facet neighbours and
+    points, and its facet values."""
+    return n * m * a_bytes + 4 * n + 8 + 8 + 4 * (dim + 1) + npts * dim * a_bytes + 8 * npts
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.rows = []
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# ----------------------------------------------------------------------------
+
+def oracle_cpu_rate(mesh, u0, seconds, patch=20):
+    """Oracle cell-stage updates/s on a compact patch of the workload's mesh:
+    patch x patch squares (2 patch^2 cells).  Each timed stage reconstructs the
+    patch cells and their facet neighbours, integrates the LF flux over every
+    facet of the patch cells and updates the patch.  The patch's moment
+    matrices are built before the clock starts (the GPU path precomputes
+    them too).  Returns (rate, description, cores)."""
+    from oracle import wlseno_oracle as O
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=P_ORDER, ring=RING, pde=O.BURGERS)
+    n = mesh.n
+    i0 = j0 = n // 2 - patch // 2
+    cells = [2 * ((j0 + j) * n + (i0 + i)) + t for j in range(patch) for i in range(patch) for t in (0, 1)]
+    cellset = set(cells)
+    need = set(cells)
+    for c in cells:
+        need.update(prob.face_nbrs[c])
+    facets = set()
+    for c in cells:
+        for f in range(3):
+            c2, f2 = prob.sib[c, f]
+            facets.add((c, f, int(c2)) if (c2 < 0 or c < c2) else (int(c2), int(f2), c))
+    for c in need:
+        prob.A(c)
+    u = np.array(u0, dtype=np.float64)
+    dt = 1e-5
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        coeffs = {c: prob.reconstruct_cell(u, c)[0] for c in need}
+        acc = {c: 0.0 for c in cells}
+        for L, fL, R in facets:
+            g = O.facet_flux(prob, coeffs, L, fL, R)
+            if L in cellset:
+                acc[L] += g
+            if R in cellset:
+                acc[R] -= g
+        for c in cells:
+            u[c] -= dt * acc[c] / prob.geo.volume[c]
+        done += len(cells)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    desc = (f"oracle (numpy/scipy, FP64, 1 thread): repeated RK stages on a {patch}x{patch}-square patch "
+            f"({len(cells)} cells, {len(need)} reconstructed per stage) of the same mesh, "
+            f"{done // len(cells)} stages in {el:.1f} s; moments built before timing")
+    return done / el, desc, 1
+
+
+# ----------------------------------------------------------------------------
+# GPU measurement
+# ----------------------------------------------------------------------------
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def make_context(precision, mesh, dev_index):
+    from paper_1602_02694_gb300.wlseno import Context
+    ctx = Context(dev_index, pde="burgers", precision=precision)
+    ctx.build_stencils(mesh, order_p=P_ORDER, ring=RING)
+    return ctx
+
+
+def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
+    """W untimed steps, then exactly `steps` timed TVD-RK3 steps bracketed by
+    a barrier and a device synchronisation; returns times and the state."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    t_setup = time.perf_counter()
+    ctx.precompute_moments()
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t_setup
+    u = torch.tensor(u0, dtype=torch.float64, device=dev)
+    shape = ctx.autotune(u, reps=3)
+    setup_s = time.perf_counter() - t_setup
+    ctx.rk_step(u, cfl=CFL, n_steps=warmup)
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(True)
+    launches0 = ctx.diagnostics()["kernel_launches"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    ctx.rk_step(u, cfl=CFL, n_steps=steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    diag = ctx.diagnostics()
+    ctx.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = max(1, diag["launches_by_kind"]["reconstruct"])
+    return {"ms": ms, "u": u, "diag": diag, "launches": diag["kernel_launches"] - launches0,
+            "clocks": clocks, "setup_s": setup_s, "shape": shape[:2],
+            "flagged_per_stage": diag["flagged_cells"] / stages}
+
+
+def run_e2e(torch, ctx, u0, steps):
+    """Same metric through the public call with a pinned HOST buffer: every
+    step copies the state host->device, runs one TVD-RK3 step and copies the
+    state back (both inside the timed region)."""
+    uh = torch.tensor(u0, dtype=torch.float64).pin_memory()
+    ctx.rk_step(uh, cfl=CFL, n_steps=1)  # warm the staging buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.rk_step(uh, cfl=CFL, n_steps=1)
+    el = time.perf_counter() - t0
+    return el, uh.numel() * 8
+
+
+def roofline(info, diag, n_cells, precision, peaks, sm_mhz):
+    n = info["stencil_nnz"] / n_cells
+    m = info["m"]
+    npts = (info["dim"] + 1) * info["quad_per_facet"]
+    launches = diag["launches_by_kind"]["reconstruct"]
+    ms = diag["kernel_ms"]["reconstruct"]
+    if launches == 0 or ms <= 0:
+        return None
+    dur = ms / launches * 1e-3
+    flops = algorithmic_flops_per_cell(n, m, npts) * n_cells
+    a_bytes = 4 if precision == "fp32_bulk" else 8
+    nbytes = algorithmic_bytes_per_cell(n, m, npts, info["dim"], a_bytes) * n_cells
+    clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if precision == "fp32_bulk":
+        alu_peak = N_SMS * FP32_PEAK_LANES_PER_SM * 2 * clock / 1e12
+    else:
+        alu_peak = FP64_NOMINAL_TFLOPS
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alu = flops / dur / 1e12
+    hbm = nbytes / dur / 1e9
+    out_alu = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": alu / alu_peak, "traffic": None,
+               "kernel": f"reconstruct ({precision})", "flops_per_launch": flops,
+               "launch_us": dur * 1e6}
+    out_hbm = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+               "frac": hbm / hbm_peak, "traffic": None,
+               "kernel": f"reconstruct ({precision})", "bytes_per_launch": nbytes,
+               "launch_us": dur * 1e6}
+    return (out_alu, out_hbm) if out_alu["frac"] >= out_hbm["frac"] else (out_hbm, out_alu)
+
+
+def burgers_exact_averages(mesh, t):
+    """Cell averages of the exact pre-shock solution of u_t + (u^2/2)_x +
+    (u^2/2)_y = 0 with u0 = 0.5 + sin(2 pi (x + y)): u = u0(x + y - 2 u t),
+    solved by Newton's method at each quadrature point (valid for
+    t < 1/(4 pi))."""
+    def f(P):
+        xi = P[:, 0] + P[:, 1]
+        u = 0.5 + np.sin(2 * np.pi * xi)
+        for _ in range(50):
+            ph = 2 * np.pi * (xi - 2 * u * t)
+            u = u - (u - 0.5 - np.sin(ph)) / (1 + 4 * np.pi * t * np.cos(ph))
+        return u
+    return synth.cell_averages(mesh, f, k=4)
+
+
+def accuracy_report(torch, mesh, u0, ctx32, ctx64, horizons=(3, 30)):
+    """Untimed: both paths from u0 at the same fixed dt (CFL 0.3 at t = 0);
+    FP32-bulk vs FP64 and each vs the exact solution after each horizon."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rmin = float(np.min(ctx64.geometry()["inradius"]))
+    dt = CFL * rmin / (math.sqrt(2.0) * float(np.max(np.abs(u0))))
+    out = {"dt": dt, "steps": list(horizons), "rel_l1_fp32_bulk_vs_fp64": [],
+           "rel_l1_vs_exact_fp64": [], "rel_l1_vs_exact_fp32_bulk": []}
+    us = {k: torch.tensor(u0, dtype=torch.float64, device=dev) for k in ("32", "64")}
+    done = 0
+    for h in horizons:
+        ctx32.rk_step(us["32"], dt=dt, n_steps=h - done)
+        ctx64.rk_step(us["64"], dt=dt, n_steps=h - done)
+        done = h
+        a32 = us["32"].cpu().numpy()
+        a64 = us["64"].cpu().numpy()
+        ex = burgers_exact_averages(mesh, h * dt)
+        out["rel_l1_fp32_bulk_vs_fp64"].append(float(np.sum(np.abs(a32 - a64)) / np.sum(np.abs(a64))))
+        out["rel_l1_vs_exact_fp64"].append(float(np.sum(np.abs(a64 - ex)) / np.sum(np.abs(ex))))
+        out["rel_l1_vs_exact_fp32_bulk"].append(float(np.sum(np.abs(a32 - ex)) / np.sum(np.abs(ex))))
+    return out
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n_cells = 2 * args.n * args.n
+    workload = WORKLOAD if args.n == N_SIDE else WORKLOAD.replace("256x256", f"{args.n}x{args.n}").replace(
+        "131,072", f"{n_cells:,}")
+    mesh = synth.tri_mesh(args.n, jitter=JITTER, seed=SEED)
+    u0 = synth.burgers_2d_initial(mesh)
+    config = {"workload": workload, "cells": n_cells, "p": P_ORDER, "stencil_ring": RING, "cfl": CFL,
+              "mesh_seed": SEED, "l2": "inputs larger than L2: the moment matrices stream from HBM "
+              "every stage (FP32 copy 194 MB, FP64 388 MB at 256x256)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        rate, desc, cores = oracle_cpu_rate(mesh, u0, max(2.0, args.cpu_seconds))
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": n_cells * 3 / rate * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = load_peaks()
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+
+    ctx32 = make_context("fp32_bulk", mesh, dev.index)
+    info = ctx32.info()
+    r32 = run_precision(torch, ctx32, u0, args.steps, args.warmup, dist, sampler)
+    ctx64 = make_context("fp64", mesh, dev.index)
+    r64 = run_precision(torch, ctx64, u0, args.steps, args.warmup, dist, None)
+    u32 = r32["u"].cpu().numpy()
+    u64 = r64["u"].cpu().numpy()
+    rel_l1 = float(np.sum(np.abs(u32 - u64)) / np.sum(np.abs(u64)))
+    accuracy = accuracy_report(torch, mesh, u0, ctx32, ctx64)
+    ctx64.close()
+
+    e2e_steps = max(3, min(args.steps, 50))
+    el, state_bytes = run_e2e(torch, ctx32, u0, e2e_steps)
+    if dist:
+        t = torch.tensor([el], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    ctx32.close()
+
+    total = world * n_cells * 3 * args.steps
+    value = total / (r32["ms"] * 1e-3)
+    value64 = total / (r64["ms"] * 1e-3)
+    clocks = r32["clocks"] or {}
+    roof = roofline(info, r32["diag"], n_cells, "fp32_bulk", peaks, None)
+    roof64 = roofline(info, r64["diag"], n_cells, "fp64", peaks, None)
+    kern = {k: {"launches": r32["diag"]["launches_by_kind"][k], "ms": r32["diag"]["kernel_ms"][k]}
+            for k in ("reconstruct", "flux", "dt")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32-bulk (f32 QR/evaluation/flux; f64 moments, weights, accumulation, RK)",
+            "data": "synthetic", "config": dict(config, parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+            "fp64_gpu": {"value": value64, "ms_per_step": r64["ms"] / args.steps,
+                         "speedup_fp32_bulk_vs_fp64": value / value64,
+                         "rel_l1_fp32_bulk_vs_fp64_after_timed_steps": rel_l1,
+                         "accuracy": accuracy,
+                         "roofline": roof64[0] if roof64 else None},
+            "e2e": {"value": world * n_cells * 3 * e2e_steps / el, "unit": UNIT,
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                    "steps": e2e_steps},
+            "gpu_launches": r32["launches"],
+            "kernels": kern,
+            "roofline": roof[0] if roof else None,
+            "roofline_other": roof[1] if roof else None,
+            "setup_s": {"moments_and_autotune_fp32": r32["setup_s"],
+                        "moments_and_autotune_fp64": r64["setup_s"]},
+            "kernel_shape": {"fp32_bulk": list(r32["shape"]), "fp64": list(r64["shape"])},
+            "refined_cells_per_stage": r32["flagged_per_stage"],
+            "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                       "reasons": clocks.get("reasons", [])},
+            "peaks": {"source": "MEASURED_PEAKS.json" if not peaks.get("fallback") else "fallback",
+                      "hbm_gbs": peaks.get("hbm_gbs")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, cores = oracle_cpu_rate(mesh, u0, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

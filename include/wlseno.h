@@ -1,0 +1,265 @@
+/*
+ * wlseno.h -- C ABI of the GB300 (sm_103a) WLS-ENO finite-volume hot path.
+ *
+ * Method: Liu & Jiao, "WLS-ENO: Weighted-Least-Squares Based Essentially
+ * Non-Oscillatory Schemes for Finite Volume Methods on Unstructured Meshes",
+ * arXiv 1602.02694.  Given the cell averages ubar_i of a conserved quantity on
+ * a simplex mesh (Sec. 1, Eq. (reconstruction)), every call below works on
+ * the cells' WLS-ENO reconstructions of degree p-1 (Sec. 3), the
+ * Lax-Friedrichs numerical flux through their facets (Sec. 1, Eq. (flux)),
+ * the finite-volume residual (Sec. 1, Eq. (fvm)) and TVD Runge-Kutta 3
+ * (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta)).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a wlseno_status; nothing aborts and no C++ exception
+ *    crosses the ABI.  wlseno_status_string() names a status.
+ *  - Cell order is the caller's: cell c of mesh k is global cell
+ *    (sum of n_cells of meshes 0..k-1) + c.  Per-cell arrays are
+ *    component-major: [n_comp][n_cells_total] float64.
+ *  - Array arguments marked "host or device" may be either: device pointers
+ *    are used in place (stream-ordered on `stream`, asynchronous); host
+ *    pointers are copied to and from the device inside the call, which then
+ *    synchronises `stream` before returning.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The context owns every derived array (geometry, stencils, moments,
+ *    workspace).  Caller buffers are never retained after a call returns (or,
+ *    for device pointers, after the stream work it enqueued completes).
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef WLSENO_H
+#define WLSENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WLSENO_OK = 0,
+  WLSENO_ERR_INVALID_ARG = -1, /* null pointer, bad size or option            */
+  WLSENO_ERR_MESH = -2,        /* inverted cell, non-manifold or bad facet    */
+  WLSENO_ERR_STENCIL = -3,     /* stencil too small (< m cells) or too large  */
+  WLSENO_ERR_CUDA = -4,        /* a CUDA runtime call failed                  */
+  WLSENO_ERR_OOM = -5,         /* device or host allocation failed            */
+  WLSENO_ERR_NUMERIC = -6,     /* non-finite value produced by the kernels    */
+  WLSENO_ERR_TIMEOUT = -7,     /* a bounded device wait gave up               */
+  WLSENO_ERR_STATE = -8        /* calls made in the wrong order               */
+} wlseno_status;
+
+enum { WLSENO_ADVECTION = 0, WLSENO_BURGERS = 1, WLSENO_EULER = 2 };
+enum { WLSENO_FP64 = 0, WLSENO_FP32_BULK = 1 };
+
+typedef struct wlseno_ctx wlseno_ctx; /* opaque */
+
+/* One conforming simplex mesh (triangles in 2-D, tetrahedra in 3-D).
+ * vertices: host [n_vertices][dim] float64.
+ * cells:    host [n_cells][dim+1] int64 vertex indices, positively oriented.
+ * period:   host [dim]; period[a] > 0 makes axis a periodic with that length
+ *           (cells and stencils are unwrapped to their minimum image),
+ *           0 makes it transmissive (boundary facets use u+ = u-). */
+typedef struct {
+  int dim;
+  int64_t n_vertices;
+  int64_t n_cells;
+  const double* vertices;
+  const int64_t* cells;
+  const double* period;
+} wlseno_mesh;
+
+/* Stencil selection (Sec. 3.2).
+ * order_p:    p; the reconstruction has degree p-1 and m = C(p-1+dim, dim)
+ *             Taylor coefficients.  Supported: 2-D p in {3,4}; 3-D p = 3.
+ * ring:       k-ring size in the paper's increments (2-D: multiples of 1/2,
+ *             1/2 = facet-sharing, 1 = vertex-sharing; 3-D: multiples of 1/3,
+ *             1/3 = face-, 2/3 = edge-, 1 = vertex-sharing).
+ * radius_cut: > 0 adds the cells of the next whole ring whose centroid lies
+ *             within radius_cut * h_i of the centre cell's centroid.
+ * min_rows:   grow stencils (by facet-neighbour increments) until they have at
+ *             least this many cells; 0 means ceil(1.5 m).
+ * lanes_per_cell, rows_per_lane: shape of the reconstruction kernel (a group
+ *             of lanes_per_cell lanes of a warp solves one cell, each lane
+ *             holding rows_per_lane stencil rows); 0, 0 picks the smallest
+ *             compiled shape that holds the largest stencil.  Compiled shapes:
+ *             (8,2) (8,3) (8,5) (16,3) (16,4). */
+typedef struct {
+  int order_p;
+  double ring;
+  double radius_cut;
+  int min_rows;
+  int lanes_per_cell;
+  int rows_per_lane;
+} wlseno_stencil_opts;
+
+/* Scheme parameters.
+ * pde:        WLSENO_ADVECTION (F = a u), WLSENO_BURGERS (F = u^2/2 (1,..,1)).
+ * n_comp:     number of conserved components (1 for the scalar equations).
+ * velocity:   advection velocity a (first dim entries used).
+ * eps:        epsilon of the non-smoothness indicator, Eq. (smoothness
+ *             indicator), e.g. 1e-2; h is the centre cell's mean edge length.
+ * alpha_c:    alpha > 1 of the centre weight, Eq. (weight), e.g. 1.5.
+ * rank_tol:   numerical rank: #{k : |R_kk| > rank_tol |R_11|}, e.g. 1e-10.
+ * kappa_flag: FP32-bulk mode: cells whose |R_11|/|R_rr| exceeds this get one
+ *             FP64-residual refinement sweep (e.g. 1e3).
+ * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and flux
+ *             in FP32; moments, residual accumulation and RK update in FP64). */
+typedef struct {
+  int pde;
+  int n_comp;
+  double velocity[3];
+  double eps;
+  double alpha_c;
+  double rank_tol;
+  double kappa_flag;
+  int precision;
+} wlseno_scheme;
+
+typedef struct {
+  int dim;
+  int order_p;
+  int m;                   /* Taylor coefficients per cell                      */
+  int n_comp;
+  int n_meshes;
+  int64_t n_cells;         /* over all meshes                                   */
+  int64_t stencil_nnz;     /* sum of stencil sizes                              */
+  int max_stencil;
+  int min_stencil;
+  int quad_per_facet;      /* 2 in 2-D, 3 in 3-D                                */
+  int lanes_per_cell;      /* kernel shape chosen for the reconstruction        */
+  int rows_per_lane;
+} wlseno_info;
+
+/* Kernel kinds of the per-kind launch counts and timings. */
+enum { WLSENO_KERNEL_MOMENTS = 0, WLSENO_KERNEL_RECONSTRUCT = 1, WLSENO_KERNEL_FLUX = 2,
+       WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_N_KERNEL_KINDS = 5 };
+
+typedef struct {
+  int64_t flagged_cells;   /* cells flagged ill-conditioned (last call)         */
+  int64_t rank_deficient;  /* cells with numerical rank < m (last call)         */
+  int64_t nonfinite;       /* non-finite values seen (last call)                */
+  int64_t kernel_launches; /* kernels launched by the context so far            */
+  double last_dt;          /* time step of the last rk_step step                */
+  int64_t launches_by_kind[WLSENO_N_KERNEL_KINDS]; /* since wlseno_set_timing   */
+  double kernel_ms[WLSENO_N_KERNEL_KINDS];         /* summed CUDA-event time of
+                                                      each kind since
+                                                      wlseno_set_timing (timing
+                                                      mode only)                */
+} wlseno_diagnostics;
+
+/* Create a context on CUDA device `device`; copies *scheme.
+ * Errors: INVALID_ARG (null, unsupported pde/precision), CUDA. */
+wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* scheme);
+
+/* Release every host and device allocation of the context (NULL is a no-op). */
+void wlseno_destroy(wlseno_ctx* ctx);
+
+/* Host setup (Sec. 3.2, Sec. 3.3.1): unwraps cells, computes centroids,
+ * volumes, mean edge lengths, facet normals and areas, half-facet siblings
+ * and the k-ring stencil of every cell of every mesh (stencils never cross
+ * meshes), then uploads them.  The mesh arrays are copied; nothing is kept.
+ * Errors: INVALID_ARG, MESH (inverted cell, facet shared by > 2 cells),
+ * STENCIL (a stencil with fewer than m cells, or more than the kernels hold),
+ * OOM, CUDA. */
+wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, int n_meshes,
+                                    const wlseno_stencil_opts* opts);
+
+/* Device precompute in FP64 (Sec. 3.2, Sec. 3.3.2): for every stencil row
+ * (i, j) the h_i-normalised cell average over tau_j of
+ * prod_c ((x_c - x_i,c)/h_i)^kappa_c / kappa_c!  (the matrix A of
+ * Eq. (average_eq) about the centroid of tau_i), exact by Gauss-Legendre
+ * product quadrature on the collapsed simplex; an FP32 copy for FP32-bulk
+ * mode; facet quadrature-point offsets.  Must follow wlseno_build_stencils.
+ * Errors: STATE, CUDA. */
+wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream);
+
+/* WLS-ENO reconstruction (Sec. 3.1, Sec. 3.2, Sec. 3.3.2).
+ * ubar:   [n_comp][n_cells] cell averages, host or device.
+ * coeffs: [n_comp][n_cells][m] output, host or device: h-normalised Taylor
+ *         coefficients d_kappa = h_i^|kappa| d^kappa u(x_i) (kappa ordered by
+ *         degree, then descending x power), so that
+ *         u_i(x) = sum_kappa d_kappa prod_c ((x_c - x_i,c)/h_i)^kappa_c / kappa_c!.
+ *         May be NULL.
+ * facet_values: [n_comp][n_cells][dim+1][quad_per_facet] output, host or
+ *         device, may be NULL: the reconstruction of cell i at the quadrature
+ *         points of its local facet f (the facet opposite its local vertex f).
+ *         Points are ordered by the facet's vertices sorted by global vertex
+ *         index: 2-D Gauss-Legendre t = 1/2 -+ sqrt(3)/6 from the lower to the
+ *         higher vertex; 3-D barycentric (2/3,1/6,1/6) on the lowest vertex
+ *         first, then the middle, then the highest.
+ * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
+wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* coeffs,
+                                 double* facet_values, void* stream);
+
+/* Spatial operator L(ubar) = -(1/|tau_i|) sum over facets of tau_i of the
+ * integrated Lax-Friedrichs flux out of tau_i (Sec. 1, Eq. (fvm) divided by
+ * |tau_i|, and Eq. (flux)).  Each facet's flux is computed once in the
+ * orientation of its lower-indexed cell and used with opposite signs, so the
+ * discrete update conserves sum |tau_i| ubar_i to round-off.
+ * ubar, residual: [n_comp][n_cells], host or device.
+ * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
+wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* residual,
+                                   void* stream);
+
+/* n_steps steps of TVD-RK3 (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta)) in place.
+ * ubar:   [n_comp][n_cells], host or device; overwritten with the result.
+ * dt:     > 0: fixed step;  <= 0: each step uses
+ *         dt = cfl * min_i r_i / lambda_max with r_i = dim |tau_i| / |d tau_i|
+ *         and lambda_max the largest wave speed over the cells (advection |a|,
+ *         Burgers sqrt(dim) max |ubar|), computed on the device per mesh.
+ * dt_out: optional host pointer receiving the last step's dt (of mesh 0); it
+ *         synchronises the stream when non-NULL.
+ * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
+wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
+                             double* dt_out, void* stream);
+
+/* Adjoint of one fixed-dt TVD-RK3 step of wlseno_rk_step:
+ * gbar_n = (d ubar^{n+1} / d ubar^n)^T gbar_next, including the derivative
+ * through the solution-dependent weights omega_j and the per-facet LF alpha.
+ * ubar_n: the step's input state (checkpoint); the stages are recomputed.
+ * All arrays [n_comp][n_cells], host or device.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
+                                  const double* gbar_next, double* gbar_n, void* stream);
+
+/* Autotuner: times the reconstruction kernel with every compiled shape
+ * (lanes_per_cell, rows_per_lane) whose rows hold the largest stencil, on
+ * `ubar` ([n_comp][n_cells], host or device), `reps` launches each after one
+ * warm-up launch, and keeps the fastest for the context.  best_us (host,
+ * nullable) receives its mean launch time in microseconds.  Synchronises
+ * `stream`.  Errors: STATE, INVALID_ARG, CUDA. */
+wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, void* stream,
+                              double* best_us);
+
+/* Sizes and the kernel shape in use.  Errors: STATE, INVALID_ARG. */
+wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out);
+
+/* Host copies of the stencils: row_ptr [n_cells+1], cols [stencil_nnz]
+ * (global cell indices, centre cell first, then increasing index).
+ * Errors: STATE, INVALID_ARG. */
+wlseno_status wlseno_get_stencils(const wlseno_ctx* ctx, int64_t* row_ptr, int64_t* cols);
+
+/* Host copies of per-cell geometry (any pointer may be NULL):
+ * centroid [n_cells][dim], volume [n_cells], h [n_cells] (mean edge length),
+ * inradius [n_cells].  Errors: STATE. */
+wlseno_status wlseno_get_geometry(const wlseno_ctx* ctx, double* centroid, double* volume,
+                                  double* h, double* inradius);
+
+/* Counters of the last call (synchronises the context's last stream). */
+wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out);
+
+/* Timing mode: enable != 0 records a CUDA event pair on the launching stream
+ * around every kernel the context launches; wlseno_get_diagnostics sums them
+ * per kernel kind.  Each wlseno_set_timing call resets the per-kind counts
+ * and times; otherwise they accumulate over calls.
+ * Errors: INVALID_ARG, CUDA. */
+wlseno_status wlseno_set_timing(wlseno_ctx* ctx, int enable);
+
+const char* wlseno_status_string(wlseno_status s);
+
+/* Human-readable detail of the last error the context reported ("" if none). */
+const char* wlseno_last_error_message(const wlseno_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WLSENO_H */

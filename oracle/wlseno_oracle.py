@@ -191,45 +191,63 @@ def k_ring(c, steps, nbr):
     return ring
 
 
-def build_stencils(cells, ring, dim, radius_cut=0.0, centroid=None, h=None, period=None):
-    """Stencil S(i) of every cell: the centre cell first, then the others in
-    increasing cell index.  With radius_cut > 0, cells of the next whole
-    vertex-sharing ring (ceil(ring) rings) whose centroid lies within
-    radius_cut * h_i of x_i are added too."""
+def neighbour_tables(cells, dim):
     nbr = {"facet": sharing_neighbours(cells, dim),
            "vertex": sharing_neighbours(cells, 1)}
     if dim == 3:
         nbr["edge"] = sharing_neighbours(cells, 2)
-    steps = ring_levels(dim, ring)
-    out = []
-    for c in range(cells.shape[0]):
-        S = k_ring(c, steps, nbr)
-        if radius_cut > 0:
-            outer = k_ring(c, ["vertex"] * (int(math.floor(ring + 1e-9)) + 1), nbr) - S
-            for c2 in outer:
-                dx = min_image(centroid[c2] - centroid[c], period)
-                if np.linalg.norm(dx) <= radius_cut * h[c]:
-                    S.add(c2)
-        out.append([c] + sorted(S - {c}))
+    return nbr
+
+
+def stencil_of(c, nbr, ring, dim, radius_cut=0.0, centroid=None, h=None, period=None,
+               min_rows=0):
+    """Stencil S(c): the centre cell first, then the others in increasing cell
+    index.  With radius_cut > 0, cells of the next whole vertex-sharing ring
+    (ceil(ring) rings) whose centroid lies within radius_cut * h_c of x_c are
+    added too.  With min_rows > 0 (transmissive boundaries) a short stencil
+    then grows by facet-neighbour increments until it has min_rows cells."""
+    S = k_ring(c, ring_levels(dim, ring), nbr)
+    if radius_cut > 0:
+        outer = k_ring(c, ["vertex"] * (int(math.floor(ring + 1e-9)) + 1), nbr) - S
+        for c2 in outer:
+            dx = min_image(centroid[c2] - centroid[c], period)
+            if np.linalg.norm(dx) <= radius_cut * h[c]:
+                S.add(c2)
+    while len(S) < min_rows:
+        grown = set(S)
+        for c2 in S:
+            grown.update(nbr["facet"][c2])
+        if grown == S:
+            break
+        S = grown
+    return [c] + sorted(S - {c})
+
+
+def build_stencils(cells, ring, dim, radius_cut=0.0, centroid=None, h=None, period=None,
+                   min_rows=0):
+    """Stencils of every cell (see stencil_of) and the facet-neighbour lists."""
+    nbr = neighbour_tables(cells, dim)
+    out = [stencil_of(c, nbr, ring, dim, radius_cut, centroid, h, period, min_rows)
+           for c in range(cells.shape[0])]
     return out, nbr["facet"]
 
 
-def grow_to_min_rows(stencils, cells, dim, min_rows):
-    """Transmissive boundaries: grow a short stencil by facet-neighbour
-    increments until it has at least min_rows cells."""
-    nbr = sharing_neighbours(cells, dim)
-    out = []
-    for S in stencils:
-        s = set(S)
-        while len(s) < min_rows:
-            grown = set(s)
-            for c2 in s:
-                grown.update(nbr[c2])
-            if grown == s:
-                break
-            s = grown
-        out.append([S[0]] + sorted(s - {S[0]}))
-    return out
+class LazyStencils:
+    """Stencils computed on first use (large meshes are only sampled)."""
+
+    def __init__(self, prob):
+        self.prob = prob
+        self.cache = {}
+
+    def __getitem__(self, c):
+        if c not in self.cache:
+            P = self.prob
+            self.cache[c] = stencil_of(c, P.nbr, P.ring, P.dim, P.radius_cut, P.geo.centroid,
+                                       P.geo.h, P.period, P.min_rows)
+        return self.cache[c]
+
+    def __len__(self):
+        return self.prob.N
 
 
 # ----------------------------------------------------------------------------
@@ -380,11 +398,9 @@ class Problem:
         self.period = np.asarray(self.period, dtype=np.float64)
         self.dim = self.cells.shape[1] - 1
         self.geo = geometry(self.vertices, self.cells, self.period)
-        self.stencils, self.face_nbrs = build_stencils(
-            self.cells, self.ring, self.dim, self.radius_cut,
-            self.geo.centroid, self.geo.h, self.period)
-        if self.min_rows:
-            self.stencils = grow_to_min_rows(self.stencils, self.cells, self.dim, self.min_rows)
+        self.nbr = neighbour_tables(self.cells, self.dim)
+        self.face_nbrs = self.nbr["facet"]
+        self.stencils = LazyStencils(self)
         self.kappas = multi_indices(self.dim, self.p)
         self.m = len(self.kappas)
         self.sib = sibling_half_facets(self.cells)

@@ -1,0 +1,661 @@
+// C ABI of libwlseno: context, device buffers, host/device pointer staging
+// and the entry points of include/wlseno.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wlseno_internal.h"
+
+using namespace wlseno;
+
+struct wlseno_ctx {
+  int device = 0;
+  wlseno_scheme scheme{};
+  SchemeParams sp{};
+  bool built = false;
+  bool moments_ready = false;
+  HostSetup host;
+  int G = 0, R = 0;
+  DeviceMesh dm{};
+  std::vector<void*> allocs;     // every device allocation of the context
+  int32_t* d_st_ptr = nullptr;
+  int32_t* d_st_idx = nullptr;
+  double* d_rmin = nullptr;
+  double* d_dt = nullptr;
+  unsigned long long* d_lmax = nullptr;
+  unsigned long long* d_counters = nullptr;
+  double* d_fvals = nullptr;     // [N][NP]
+  double* d_k1 = nullptr;        // [C][N] RK stage states
+  double* d_k2 = nullptr;
+  double* d_in = nullptr;        // [C][N] staging for host inputs / outputs
+  double* d_out = nullptr;       // [C][N] staging for host outputs
+  double* d_coef = nullptr;      // [C][N][m] staging for host coefficient output
+  double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
+  int64_t launches = 0;
+  int64_t by_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  // timing mode: event pairs recorded around launches, summed on demand
+  bool timing = false;
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<TimedLaunch> timed;
+  size_t events_used = 0;
+  cudaStream_t last_stream = nullptr;
+  double last_dt = 0.0;
+  std::string error;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+wlseno_status fail(wlseno_ctx* ctx, wlseno_status s, const std::string& msg) {
+  if (ctx) ctx->error = msg;
+  return s;
+}
+
+wlseno_status cuda_fail(wlseno_ctx* ctx, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(ctx, e == cudaErrorMemoryAllocation ? WLSENO_ERR_OOM : WLSENO_ERR_CUDA, msg);
+}
+
+template <typename T>
+wlseno_status dalloc(wlseno_ctx* ctx, T** p, size_t count) {
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+  ctx->allocs.push_back(raw);
+  *p = static_cast<T*>(raw);
+  return WLSENO_OK;
+}
+
+template <typename T>
+wlseno_status upload(wlseno_ctx* ctx, T** p, const std::vector<T>& v) {
+  wlseno_status s = dalloc(ctx, p, v.size());
+  if (s != WLSENO_OK) return s;
+  cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+  return WLSENO_OK;
+}
+
+void free_all(wlseno_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Shapes compiled into the reconstruction kernel (lanes per cell, rows per lane).
+const int kShapes[][2] = {{8, 2}, {8, 3}, {8, 5}, {16, 3}, {16, 4}};
+
+bool shape_ok(int G, int R) {
+  for (auto& s : kShapes)
+    if (s[0] == G && s[1] == R) return true;
+  return false;
+}
+
+void choose_shape(int max_n, int* G, int* R) {
+  int best = -1;
+  for (int k = 0; k < 5; ++k) {
+    int cap = kShapes[k][0] * kShapes[k][1];
+    if (cap < max_n) continue;
+    if (best < 0 || cap < kShapes[best][0] * kShapes[best][1]) best = k;
+  }
+  if (best < 0) {
+    *G = *R = 0;
+    return;
+  }
+  *G = kShapes[best][0];
+  *R = kShapes[best][1];
+}
+
+int points_per_cell(const wlseno_ctx* ctx) { return (ctx->dm.dim + 1) * ctx->dm.nq; }
+
+cudaEvent_t next_event(wlseno_ctx* ctx) {
+  if (ctx->events_used == ctx->event_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    ctx->event_pool.push_back(e);
+  }
+  return ctx->event_pool[ctx->events_used++];
+}
+
+// Brackets the launches of one kernel kind: counts them and, in timing mode,
+// records an event pair on the launching stream.
+struct KernelScope {
+  wlseno_ctx* ctx;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t start = nullptr;
+  KernelScope(wlseno_ctx* c, int k, cudaStream_t st) : ctx(c), kind(k), s(st) {
+    if (ctx->timing) {
+      start = next_event(ctx);
+      if (start) cudaEventRecord(start, s);
+    }
+  }
+  void done(int n_launches) {
+    ctx->launches += n_launches;
+    ctx->by_kind[kind] += n_launches;
+    if (start) {
+      cudaEvent_t stop = next_event(ctx);
+      if (stop) {
+        cudaEventRecord(stop, s);
+        ctx->timed.push_back({kind, start, stop});
+      }
+    }
+  }
+};
+
+void reset_kind_stats(wlseno_ctx* ctx) {
+  for (auto& v : ctx->by_kind) v = 0;
+  ctx->timed.clear();
+  ctx->events_used = 0;
+}
+
+
+cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
+                            cudaStream_t s) {
+  ReconOut out{coeffs, fvals, ctx->d_counters};
+  const DeviceMesh& dm = ctx->dm;
+  const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
+  cudaError_t e = cudaErrorInvalidValue;
+  KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
+  if (dm.dim == 2 && dm.m == 6)
+    e = f32 ? launch_reconstruct_inst<float, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
+            : launch_reconstruct_inst<double, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
+  else if (dm.dim == 2 && dm.m == 10)
+    e = f32 ? launch_reconstruct_inst<float, 2, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
+            : launch_reconstruct_inst<double, 2, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
+  else if (dm.dim == 3 && dm.m == 10)
+    e = f32 ? launch_reconstruct_inst<float, 3, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
+            : launch_reconstruct_inst<double, 3, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
+  scope.done(e == cudaSuccess ? 1 : 0);
+  return e;
+}
+
+cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, const double* u0,
+                     double a, double b, bool residual_only, double* out, cudaStream_t s) {
+  KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
+  cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, u, u0,
+                                         a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s);
+  scope.done(e == cudaSuccess ? 1 : 0);
+  return e;
+}
+
+wlseno_status check_ready(wlseno_ctx* ctx) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built || !ctx->moments_ready)
+    return fail(ctx, WLSENO_ERR_STATE, "call wlseno_build_stencils and wlseno_precompute_moments first");
+  return WLSENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wlseno_status_string(wlseno_status s) {
+  switch (s) {
+    case WLSENO_OK: return "ok";
+    case WLSENO_ERR_INVALID_ARG: return "invalid argument";
+    case WLSENO_ERR_MESH: return "invalid mesh";
+    case WLSENO_ERR_STENCIL: return "invalid stencil";
+    case WLSENO_ERR_CUDA: return "CUDA error";
+    case WLSENO_ERR_OOM: return "out of memory";
+    case WLSENO_ERR_NUMERIC: return "non-finite value";
+    case WLSENO_ERR_TIMEOUT: return "device wait timed out";
+    case WLSENO_ERR_STATE: return "calls made in the wrong order";
+  }
+  return "unknown status";
+}
+
+const char* wlseno_last_error_message(const wlseno_ctx* ctx) {
+  return ctx ? ctx->error.c_str() : "null context";
+}
+
+wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* scheme) {
+  if (!out || !scheme) return WLSENO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (scheme->pde != WLSENO_ADVECTION && scheme->pde != WLSENO_BURGERS)
+    return WLSENO_ERR_INVALID_ARG;
+  if (scheme->n_comp != 1) return WLSENO_ERR_INVALID_ARG;
+  if (scheme->precision != WLSENO_FP64 && scheme->precision != WLSENO_FP32_BULK)
+    return WLSENO_ERR_INVALID_ARG;
+  if (!(scheme->eps > 0.0) || !(scheme->alpha_c > 0.0) || !(scheme->rank_tol >= 0.0))
+    return WLSENO_ERR_INVALID_ARG;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return WLSENO_ERR_CUDA;
+  }
+  wlseno_ctx* ctx = new (std::nothrow) wlseno_ctx();
+  if (!ctx) return WLSENO_ERR_OOM;
+  ctx->device = device;
+  ctx->scheme = *scheme;
+  ctx->sp.pde = scheme->pde;
+  for (int a = 0; a < 3; ++a) ctx->sp.vel[a] = scheme->velocity[a];
+  ctx->sp.eps = scheme->eps;
+  ctx->sp.alpha_c = scheme->alpha_c;
+  ctx->sp.rank_tol = scheme->rank_tol;
+  ctx->sp.kappa_flag = scheme->kappa_flag > 0.0 ? scheme->kappa_flag : 1e3;
+  *out = ctx;
+  return WLSENO_OK;
+}
+
+void wlseno_destroy(wlseno_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    free_all(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  }
+  delete ctx;
+}
+
+wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, int n_meshes,
+                                    const wlseno_stencil_opts* opts) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  free_all(ctx);
+  ctx->built = ctx->moments_ready = false;
+  std::string err;
+  HostSetup& H = ctx->host;
+  wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err);
+  if (st != WLSENO_OK) return fail(ctx, st, err);
+  if ((H.dim == 2 && H.m != 6 && H.m != 10) || (H.dim == 3 && H.m != 10))
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "order p not compiled for this dimension");
+  int G = opts->lanes_per_cell, R = opts->rows_per_lane;
+  if (G == 0 && R == 0) {
+    choose_shape(H.max_n, &G, &R);
+  } else if (!shape_ok(G, R)) {
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "lanes_per_cell/rows_per_lane not compiled");
+  }
+  if (G * R < H.max_n || G == 0)
+    return fail(ctx, WLSENO_ERR_STENCIL, "largest stencil (" + std::to_string(H.max_n) +
+                                             " cells) exceeds the kernel's rows");
+  ctx->G = G;
+  ctx->R = R;
+  const int64_t N = H.N;
+  std::vector<int32_t> ptr32(N + 1), idx32(H.nnz);
+  for (int64_t i = 0; i <= N; ++i) ptr32[i] = static_cast<int32_t>(H.row_ptr[i]);
+  for (int64_t i = 0; i < H.nnz; ++i) idx32[i] = static_cast<int32_t>(H.cols[i]);
+  std::vector<float> fpts32(H.fpts.begin(), H.fpts.end());
+  DeviceMesh& dm = ctx->dm;
+  dm = DeviceMesh{};
+  dm.dim = H.dim;
+  dm.p = H.p;
+  dm.m = H.m;
+  dm.nq = H.nq;
+  dm.N = N;
+  dm.nnz = H.nnz;
+  double *coords, *centroid, *h, *vol, *inr, *period, *fgeo, *fpts;
+  int32_t *mesh_of, *nbr;
+  float* fp32;
+  if ((st = upload(ctx, &ctx->d_st_ptr, ptr32)) || (st = upload(ctx, &ctx->d_st_idx, idx32)) ||
+      (st = upload(ctx, &coords, H.coords)) || (st = upload(ctx, &centroid, H.centroid)) ||
+      (st = upload(ctx, &h, H.h)) || (st = upload(ctx, &vol, H.volume)) ||
+      (st = upload(ctx, &inr, H.inradius)) || (st = upload(ctx, &mesh_of, H.mesh_of)) ||
+      (st = upload(ctx, &period, H.period)) || (st = upload(ctx, &nbr, H.nbr)) ||
+      (st = upload(ctx, &fgeo, H.fgeo)) || (st = upload(ctx, &fpts, H.fpts)) ||
+      (st = upload(ctx, &fp32, fpts32)) || (st = upload(ctx, &ctx->d_rmin, H.rmin)))
+    return st;
+  dm.st_ptr = ctx->d_st_ptr;
+  dm.st_idx = ctx->d_st_idx;
+  dm.coords = coords;
+  dm.centroid = centroid;
+  dm.h = h;
+  dm.volume = vol;
+  dm.inradius = inr;
+  dm.mesh_of = mesh_of;
+  dm.period = period;
+  dm.nbr = nbr;
+  dm.fgeo = fgeo;
+  dm.fpts = fpts;
+  dm.fpts32 = fp32;
+  const int C = ctx->scheme.n_comp;
+  const int NP = (H.dim + 1) * H.nq;
+  if ((st = dalloc(ctx, &dm.A64, H.nnz * H.m)) || (st = dalloc(ctx, &dm.A32, H.nnz * H.m)) ||
+      (st = dalloc(ctx, &ctx->d_dt, H.n_meshes)) || (st = dalloc(ctx, &ctx->d_lmax, H.n_meshes)) ||
+      (st = dalloc(ctx, &ctx->d_counters, 4)) || (st = dalloc(ctx, &ctx->d_fvals, N * NP)) ||
+      (st = dalloc(ctx, &ctx->d_k1, C * N)) || (st = dalloc(ctx, &ctx->d_k2, C * N)))
+    return st;
+  cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
+  ctx->d_in = ctx->d_out = ctx->d_coef = ctx->d_fv_out = nullptr;
+  ctx->built = true;
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, WLSENO_ERR_STATE, "call wlseno_build_stencils first");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  KernelScope scope(ctx, WLSENO_KERNEL_MOMENTS, s);
+  cudaError_t e = launch_moments(ctx->dm, s);
+  scope.done(e == cudaSuccess ? 1 : 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "moments kernel");
+  ctx->moments_ready = true;
+  ctx->last_stream = s;
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* coeffs,
+                                 double* facet_values, void* stream) {
+  wlseno_status st = check_ready(ctx);
+  if (st != WLSENO_OK) return st;
+  if (!ubar) return fail(ctx, WLSENO_ERR_INVALID_ARG, "ubar is null");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = s;
+  const int64_t N = ctx->dm.N;
+  const int C = ctx->scheme.n_comp, m = ctx->dm.m, NP = points_per_cell(ctx);
+  bool host_io = false;
+  const double* u = ubar;
+  cudaError_t e;
+  if (!is_device_pointer(ubar)) {
+    if (!ctx->d_in && (st = dalloc(ctx, &ctx->d_in, C * N))) return st;
+    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * C * N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
+    u = ctx->d_in;
+    host_io = true;
+  }
+  const bool coef_host = coeffs && !is_device_pointer(coeffs);
+  const bool fv_host = facet_values && !is_device_pointer(facet_values);
+  if (coef_host && !ctx->d_coef && (st = dalloc(ctx, &ctx->d_coef, C * N * m))) return st;
+  if (fv_host && !ctx->d_fv_out && (st = dalloc(ctx, &ctx->d_fv_out, C * N * NP))) return st;
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset counters");
+  for (int c = 0; c < C; ++c) {
+    double* co = coeffs ? (coef_host ? ctx->d_coef : coeffs) + c * N * m : nullptr;
+    double* fv = facet_values ? (fv_host ? ctx->d_fv_out : facet_values) + c * N * NP : ctx->d_fvals;
+    e = reconstruct_one(ctx, u + c * N, co, fv, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruction kernel");
+  }
+  if (coef_host) {
+    e = cudaMemcpyAsync(coeffs, ctx->d_coef, sizeof(double) * C * N * m, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy coeffs");
+  }
+  if (fv_host) {
+    e = cudaMemcpyAsync(facet_values, ctx->d_fv_out, sizeof(double) * C * N * NP,
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy facet values");
+  }
+  if (host_io || coef_host || fv_host) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct");
+  }
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* residual,
+                                   void* stream) {
+  wlseno_status st = check_ready(ctx);
+  if (st != WLSENO_OK) return st;
+  if (!ubar || !residual) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null array");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = s;
+  const int64_t N = ctx->dm.N;
+  const int C = ctx->scheme.n_comp;
+  cudaError_t e;
+  const double* u = ubar;
+  const bool in_host = !is_device_pointer(ubar);
+  const bool out_host = !is_device_pointer(residual);
+  if (in_host) {
+    if (!ctx->d_in && (st = dalloc(ctx, &ctx->d_in, C * N))) return st;
+    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * C * N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
+    u = ctx->d_in;
+  }
+  if (out_host && !ctx->d_out && (st = dalloc(ctx, &ctx->d_out, C * N))) return st;
+  double* res = out_host ? ctx->d_out : residual;
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset counters");
+  for (int c = 0; c < C; ++c) {
+    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruction kernel");
+    e = flux_one(ctx, ctx->d_fvals, u + c * N, nullptr, 0.0, 1.0, true, res + c * N, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "flux kernel");
+  }
+  if (out_host) {
+    e = cudaMemcpyAsync(residual, ctx->d_out, sizeof(double) * C * N, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy residual");
+  }
+  if (in_host || out_host) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "flux_residual");
+  }
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
+                             double* dt_out, void* stream) {
+  wlseno_status st = check_ready(ctx);
+  if (st != WLSENO_OK) return st;
+  if (!ubar || n_steps < 0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null ubar or n_steps < 0");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(ctx, WLSENO_ERR_INVALID_ARG, "need dt > 0 or cfl > 0");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = s;
+  const int64_t N = ctx->dm.N;
+  const int C = ctx->scheme.n_comp;
+  cudaError_t e;
+  const bool host = !is_device_pointer(ubar);
+  double* u = ubar;
+  if (host) {
+    if (!ctx->d_in && (st = dalloc(ctx, &ctx->d_in, C * N))) return st;
+    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * C * N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
+    u = ctx->d_in;
+  }
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset counters");
+  for (int step = 0; step < n_steps; ++step) {
+    int nl = 0;
+    KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
+    e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
+                           dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, s, &nl);
+    scope.done(nl);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "time step kernel");
+    for (int c = 0; c < C; ++c) {
+      double* u0 = u + c * N;
+      double* k1 = ctx->d_k1 + c * N;
+      double* k2 = ctx->d_k2 + c * N;
+      // k1 = u + dt L(u)
+      if ((e = reconstruct_one(ctx, u0, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
+          (e = flux_one(ctx, ctx->d_fvals, u0, u0, 0.0, 1.0, false, k1, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "RK stage 1");
+      // k2 = 3/4 u + 1/4 (k1 + dt L(k1))
+      if ((e = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
+          (e = flux_one(ctx, ctx->d_fvals, k1, u0, 0.75, 0.25, false, k2, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "RK stage 2");
+      // u <- 1/3 u + 2/3 (k2 + dt L(k2))
+      if ((e = reconstruct_one(ctx, k2, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
+          (e = flux_one(ctx, ctx->d_fvals, k2, u0, 1.0 / 3.0, 2.0 / 3.0, false, u0, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "RK stage 3");
+    }
+  }
+  if (host) {
+    e = cudaMemcpyAsync(ubar, ctx->d_in, sizeof(double) * C * N, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar back");
+  }
+  if (dt_out) {
+    double v = 0.0;
+    e = cudaMemcpyAsync(&v, ctx->d_dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read dt");
+    *dt_out = v;
+    ctx->last_dt = v;
+  } else if (host) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rk_step");
+  }
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, void* stream,
+                              double* best_us) {
+  wlseno_status st = check_ready(ctx);
+  if (st != WLSENO_OK) return st;
+  if (!ubar || reps <= 0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null ubar or reps <= 0");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = s;
+  const int64_t N = ctx->dm.N;
+  cudaError_t e;
+  const double* u = ubar;
+  if (!is_device_pointer(ubar)) {
+    if (!ctx->d_in && (st = dalloc(ctx, &ctx->d_in, ctx->scheme.n_comp * N))) return st;
+    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
+    u = ctx->d_in;
+  }
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, e, "event");
+  }
+  const int G0 = ctx->G, R0 = ctx->R;
+  int bestG = G0, bestR = R0;
+  float best = -1.0f;
+  for (auto& sh : kShapes) {
+    if (sh[0] * sh[1] < ctx->host.max_n) continue;
+    ctx->G = sh[0];
+    ctx->R = sh[1];
+    e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ctx->G = G0;
+      ctx->R = R0;
+      return cuda_fail(ctx, e, "autotune");
+    }
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      bestG = sh[0];
+      bestR = sh[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->G = bestG;
+  ctx->R = bestR;
+  if (best_us) *best_us = best < 0.0f ? 0.0 : 1e3 * best / reps;
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
+                                  const double* gbar_next, double* gbar_n, void* stream) {
+  (void)ubar_n;
+  (void)dt;
+  (void)gbar_next;
+  (void)gbar_n;
+  (void)stream;
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  return fail(ctx, WLSENO_ERR_STATE, "the adjoint is not available in this build");
+}
+
+wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out) {
+  if (!ctx || !out) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built) return WLSENO_ERR_STATE;
+  const HostSetup& H = ctx->host;
+  out->dim = H.dim;
+  out->order_p = H.p;
+  out->m = H.m;
+  out->n_comp = ctx->scheme.n_comp;
+  out->n_meshes = H.n_meshes;
+  out->n_cells = H.N;
+  out->stencil_nnz = H.nnz;
+  out->max_stencil = H.max_n;
+  out->min_stencil = H.min_n;
+  out->quad_per_facet = H.nq;
+  out->lanes_per_cell = ctx->G;
+  out->rows_per_lane = ctx->R;
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_get_stencils(const wlseno_ctx* ctx, int64_t* row_ptr, int64_t* cols) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built) return WLSENO_ERR_STATE;
+  if (row_ptr) std::memcpy(row_ptr, ctx->host.row_ptr.data(), sizeof(int64_t) * ctx->host.row_ptr.size());
+  if (cols) std::memcpy(cols, ctx->host.cols.data(), sizeof(int64_t) * ctx->host.cols.size());
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_get_geometry(const wlseno_ctx* ctx, double* centroid, double* volume,
+                                  double* h, double* inradius) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built) return WLSENO_ERR_STATE;
+  const HostSetup& H = ctx->host;
+  if (centroid) std::memcpy(centroid, H.centroid.data(), sizeof(double) * H.centroid.size());
+  if (volume) std::memcpy(volume, H.volume.data(), sizeof(double) * H.volume.size());
+  if (h) std::memcpy(h, H.h.data(), sizeof(double) * H.h.size());
+  if (inradius) std::memcpy(inradius, H.inradius.data(), sizeof(double) * H.inradius.size());
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out) {
+  if (!ctx || !out) return WLSENO_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->kernel_launches = ctx->launches;
+  out->last_dt = ctx->last_dt;
+  for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) out->launches_by_kind[k] = ctx->by_kind[k];
+  if (!ctx->built) return WLSENO_OK;
+  DeviceGuard guard(ctx->device);
+  unsigned long long c[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
+  if (e == cudaSuccess) e = cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read counters");
+  out->flagged_cells = static_cast<int64_t>(c[0]);
+  out->rank_deficient = static_cast<int64_t>(c[1]);
+  out->nonfinite = static_cast<int64_t>(c[2]);
+  for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) out->launches_by_kind[k] = ctx->by_kind[k];
+  for (const auto& t : ctx->timed) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) out->kernel_ms[t.kind] += ms;
+    else cudaGetLastError();
+  }
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_set_timing(wlseno_ctx* ctx, int enable) {
+  if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  reset_kind_stats(ctx);
+  return WLSENO_OK;
+}
+
+}  // extern "C"

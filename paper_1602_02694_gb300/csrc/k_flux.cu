@@ -1,0 +1,228 @@
+// Lax-Friedrichs facet flux (Sec. 1, Eq. (flux)), finite-volume residual
+// (Sec. 1, Eq. (fvm), divided by |tau_i|) and one TVD-RK3 stage
+// (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta)), fused in one thread-per-cell
+// kernel, plus the CFL time step.
+//
+// Each cell gathers the facet values of its d+1 facets from itself and from
+// its facet neighbours and computes every facet flux in the orientation of the
+// facet's lower-indexed cell with that cell's normal and area (stored
+// identically in both cells' facet records).  Both cells therefore compute the
+// bitwise-same flux and use it with opposite signs: no atomics, a fixed
+// summation order, and exact discrete conservation up to the final FP64 sums.
+#include <cmath>
+
+#include "wlseno_internal.h"
+
+namespace wlseno {
+namespace {
+
+// One facet's integrated LF flux in the orientation of its lower-indexed cell
+// L (normal nrm and area of L), from the traces uL (of L) and uR at its NQ
+// points.  FP64 mode evaluates it directly.  FP32-bulk mode splits it at the
+// reference state u_ref = uL[0]: F(u_ref).n in FP64 plus the FP32 flux of the
+// deviations u - u_ref, so the FP32 rounding is relative to the (small)
+// deviations and a constant state gives an exactly constant flux.
+template <typename T, int DIM, int NQ>
+__device__ __forceinline__ double facet_flux(const SchemeParams& sp, const double* geo,
+                                             const double (&uL)[NQ], const double (&uR)[NQ]) {
+  const T wq = T(1) / T(NQ);  // equal-weight rules on every facet
+  double n64[DIM];
+  double nsum64 = 0.0, vn64 = 0.0, speed2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    n64[a] = geo[a];
+    nsum64 += n64[a];
+    vn64 += sp.vel[a] * n64[a];
+    speed2 += sp.vel[a] * sp.vel[a];
+  }
+  const bool adv = sp.pde == WLSENO_ADVECTION;
+  if constexpr (sizeof(T) == 8) {
+    double alpha;
+    if (adv) {
+      alpha = sqrt(speed2);
+    } else {
+      double mx = 0.0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) mx = fmax(mx, fmax(fabs(uL[q]), fabs(uR[q])));
+      alpha = mx * fabs(nsum64);
+    }
+    double fsum = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double fl, fr;
+      if (adv) {
+        fl = vn64 * uL[q];
+        fr = vn64 * uR[q];
+      } else {
+        fl = 0.5 * uL[q] * uL[q] * nsum64;
+        fr = 0.5 * uR[q] * uR[q] * nsum64;
+      }
+      fsum += wq * (0.5 * ((fl + fr) - alpha * (uR[q] - uL[q])));
+    }
+    return geo[3] * fsum;
+  } else {
+    const double uref = uL[0];
+    const float ur = static_cast<float>(uref);
+    const float nsum = static_cast<float>(nsum64), vn = static_cast<float>(vn64);
+    float dL[NQ], dR[NQ];
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      dL[q] = static_cast<float>(uL[q] - uref);
+      dR[q] = static_cast<float>(uR[q] - uref);
+      mx = fmaxf(mx, fmaxf(fabsf(ur + dL[q]), fabsf(ur + dR[q])));
+    }
+    const float alpha = adv ? static_cast<float>(sqrt(speed2)) : mx * fabsf(nsum);
+    float fsum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float fl, fr;
+      if (adv) {
+        fl = vn * dL[q];
+        fr = vn * dR[q];
+      } else {  // (u^2 - u_ref^2)/2 = d (u_ref + d/2)
+        fl = nsum * dL[q] * (ur + 0.5f * dL[q]);
+        fr = nsum * dR[q] * (ur + 0.5f * dR[q]);
+      }
+      fsum += wq * (0.5f * ((fl + fr) - alpha * (dR[q] - dL[q])));
+    }
+    const double fref = adv ? vn64 * uref : 0.5 * uref * uref * nsum64;
+    return geo[3] * (fref + static_cast<double>(fsum));
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256)
+flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fvals,
+                  const double* __restrict__ u, const double* __restrict__ u0, double a, double b,
+                  const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
+                  unsigned long long* __restrict__ counters) {
+  constexpr int NF = DIM + 1;
+  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NP = NF * NQ;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= dm.N) return;
+  double acc = 0.0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int nb = dm.nbr[i * NF + f];
+    double uo[NQ], un[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) uo[q] = fvals[i * NP + f * NQ + q];
+    bool owner = true;
+    if (nb >= 0) {
+      const int64_t j = nb >> 2;
+      const int f2 = nb & 3;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) un[q] = fvals[j * NP + f2 * NQ + q];
+      owner = i < j;
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) un[q] = uo[q];
+    }
+    double uL[NQ], uR[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      uL[q] = owner ? uo[q] : un[q];
+      uR[q] = owner ? un[q] : uo[q];
+    }
+    const double flux = facet_flux<T, DIM, NQ>(sp, dm.fgeo + (i * NF + f) * 4, uL, uR);
+    acc += owner ? flux : -flux;
+  }
+  const double L = -acc / dm.volume[i];
+  double res;
+  if (residual_only) {
+    res = L;
+  } else {
+    const double dt = dt_mesh[dm.mesh_of[i]];
+    res = a * u0[i] + b * (u[i] + dt * L);
+  }
+  out[i] = res;
+  if (!isfinite(res)) atomicAdd(&counters[2], 1ull);
+}
+
+// Largest |ubar| per mesh, as the bits of a non-negative double (their
+// integer order is the numeric order, so atomicMax is exact and deterministic).
+__global__ void max_abs_kernel(int64_t N, const double* __restrict__ u,
+                               const int32_t* __restrict__ mesh_of,
+                               unsigned long long* __restrict__ lmax_bits) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const bool in = i < N;
+  const int mesh = in ? mesh_of[i] : -1;
+  unsigned long long bits = in ? static_cast<unsigned long long>(__double_as_longlong(fabs(u[i]))) : 0ull;
+  const int lane = threadIdx.x & 31;
+  const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
+  const bool same = __all_sync(0xffffffffu, mesh == m0 || mesh < 0);
+  if (same) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      unsigned long long o = __shfl_xor_sync(0xffffffffu, bits, off);
+      bits = o > bits ? o : bits;
+    }
+    if (lane == 0 && m0 >= 0) atomicMax(&lmax_bits[m0], bits);
+  } else if (in) {
+    atomicMax(&lmax_bits[mesh], bits);
+  }
+}
+
+__global__ void cfl_dt_kernel(int n_meshes, int pde, int dim, double adv_speed,
+                              const unsigned long long* __restrict__ lmax_bits,
+                              const double* __restrict__ rmin, double cfl, double dt_fixed,
+                              double* __restrict__ dt_mesh) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_meshes) return;
+  if (dt_fixed > 0.0) {
+    dt_mesh[k] = dt_fixed;
+    return;
+  }
+  double lam = adv_speed;
+  if (pde == WLSENO_BURGERS) lam = sqrt(static_cast<double>(dim)) * __longlong_as_double(static_cast<long long>(lmax_bits[k]));
+  dt_mesh[k] = lam > 0.0 ? cfl * rmin[k] / lam : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
+                                   const double* fvals, const double* u, const double* u0,
+                                   double a, double b, const double* dt_mesh, bool residual_only,
+                                   double* out, unsigned long long* counters, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
+  const int ro = residual_only ? 1 : 0;
+  if (dm.dim == 2) {
+    if (precision == WLSENO_FP32_BULK)
+      flux_stage_kernel<float, 2><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+    else
+      flux_stage_kernel<double, 2><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  } else {
+    if (precision == WLSENO_FP32_BULK)
+      flux_stage_kernel<float, 3><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+    else
+      flux_stage_kernel<double, 3><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
+                               const double* u, const double* rmin, double cfl, double dt_fixed,
+                               unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
+                               int* launches) {
+  double speed = 0.0;
+  for (int a = 0; a < dm.dim; ++a) speed += sp.vel[a] * sp.vel[a];
+  speed = std::sqrt(speed);
+  *launches = 0;
+  if (dt_fixed <= 0.0 && sp.pde == WLSENO_BURGERS) {
+    cudaError_t e = cudaMemsetAsync(lmax_bits, 0, sizeof(unsigned long long) * n_meshes, s);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
+    max_abs_kernel<<<blocks, threads, 0, s>>>(dm.N, u, dm.mesh_of, lmax_bits);
+    ++*launches;
+  }
+  cfl_dt_kernel<<<(n_meshes + 127) / 128, 128, 0, s>>>(n_meshes, sp.pde, dm.dim, speed, lmax_bits,
+                                                        rmin, cfl, dt_fixed, dt_mesh);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace wlseno

@@ -1,0 +1,111 @@
+// Internal declarations of libwlseno (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/wlseno.h"
+
+namespace wlseno {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxM = 10;        // Taylor coefficients the kernels are built for
+constexpr int kMaxQ = 3;         // quadrature points per facet
+constexpr int kMaxFacets = 4;    // facets per simplex
+
+// Host-side result of the mesh / stencil setup (host_mesh.cpp).
+struct HostSetup {
+  int dim = 0, p = 0, m = 0, nq = 0, n_meshes = 0;
+  int64_t N = 0, nnz = 0;
+  int max_n = 0, min_n = 0;
+  std::vector<int64_t> row_ptr;   // [N+1]
+  std::vector<int64_t> cols;      // [nnz], centre first, then increasing index
+  std::vector<double> coords;     // [N][dim+1][dim] unwrapped vertices
+  std::vector<double> centroid;   // [N][dim]
+  std::vector<double> volume;     // [N]
+  std::vector<double> h;          // [N] mean edge length
+  std::vector<double> inradius;   // [N]
+  std::vector<int32_t> mesh_of;   // [N]
+  std::vector<double> period;     // [n_meshes][3]
+  std::vector<double> rmin;       // [n_meshes] smallest inradius
+  std::vector<int32_t> nbr;       // [N][dim+1]: (j << 2) | f' or -1 (boundary)
+  std::vector<double> fgeo;       // [N][dim+1][4]: owner's unit normal (dim), area
+  std::vector<double> fpts;       // [N][dim+1][nq][dim]: (x_q - x_i) / h_i
+};
+
+wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
+                               const wlseno_stencil_opts* opts, HostSetup* out,
+                               std::string* err);
+
+// ---------------------------------------------------------------------------
+// device-side views handed to the kernel launchers
+// ---------------------------------------------------------------------------
+struct DeviceMesh {
+  int dim, p, m, nq;
+  int64_t N, nnz;
+  const int32_t* st_ptr;    // [N+1]
+  const int32_t* st_idx;    // [nnz]
+  const double* coords;     // [N][dim+1][dim]
+  const double* centroid;   // [N][dim]
+  const double* h;          // [N]
+  const double* volume;     // [N]
+  const double* inradius;   // [N]
+  const int32_t* mesh_of;   // [N]
+  const double* period;     // [n_meshes][3]
+  const int32_t* nbr;       // [N][dim+1]
+  const double* fgeo;       // [N][dim+1][4]
+  const double* fpts;       // [N][dim+1][nq][dim]
+  const float* fpts32;      // same, FP32
+  double* A64;              // [nnz][m]
+  float* A32;               // [nnz][m]
+};
+
+struct SchemeParams {
+  int pde;
+  double vel[3];
+  double eps, alpha_c, rank_tol, kappa_flag;
+};
+
+struct ReconOut {
+  double* coeffs;           // [N][m] or null
+  double* fvals;            // [N][dim+1][nq] (always written)
+  unsigned long long* counters;  // [4]: flagged, rank deficient, nonfinite, spare
+};
+
+// Launchers (return the CUDA error of the launch).
+cudaError_t launch_moments(const DeviceMesh& dm, cudaStream_t s);
+
+// Reconstruction for one component; one translation unit per (T, DIM, M).
+template <typename T, int DIM, int M>
+cudaError_t launch_reconstruct_inst(const DeviceMesh& dm, const SchemeParams& sp, int G, int R,
+                                    const double* ubar, const ReconOut& out, cudaStream_t s);
+#define WLSENO_DECLARE_RECON(T, D, M)                                                      \
+  template <>                                                                               \
+  cudaError_t launch_reconstruct_inst<T, D, M>(const DeviceMesh&, const SchemeParams&, int, \
+                                               int, const double*, const ReconOut&,        \
+                                               cudaStream_t);
+WLSENO_DECLARE_RECON(double, 2, 6)
+WLSENO_DECLARE_RECON(double, 2, 10)
+WLSENO_DECLARE_RECON(double, 3, 10)
+WLSENO_DECLARE_RECON(float, 2, 6)
+WLSENO_DECLARE_RECON(float, 2, 10)
+WLSENO_DECLARE_RECON(float, 3, 10)
+#undef WLSENO_DECLARE_RECON
+
+// Per-cell flux gather + RK stage: out = a*u0 + b*(u + dt*L(u)); with
+// residual_only the output is L(u) itself.
+cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
+                                   const double* fvals, const double* u, const double* u0,
+                                   double a, double b, const double* dt_mesh, bool residual_only,
+                                   double* out, unsigned long long* counters, cudaStream_t s);
+// dt_mesh[k] = cfl * rmin[k] / lambda_max(mesh k), or dt_fixed when > 0.
+cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
+                               const double* u, const double* rmin, double cfl, double dt_fixed,
+                               unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
+                               int* launches);
+
+}  // namespace wlseno

@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every entry
+point include/wlseno.h declares; calls that need no GPU behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1602_02694_gb300 import wlseno as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "wlseno.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wlseno_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(W.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return W.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in W.SIGNATURES, f"binding does not declare {name}"
+    assert set(W.SIGNATURES) == set(names)
+
+
+def test_status_strings(lib):
+    assert lib.wlseno_status_string(0) == b"ok"
+    assert lib.wlseno_status_string(-8) == b"calls made in the wrong order"
+    assert lib.wlseno_status_string(-3) == b"invalid stencil"
+
+
+def test_argument_errors_without_gpu(lib):
+    # null arguments are rejected before any CUDA call
+    assert lib.wlseno_create(None, 0, None) == -1
+    assert lib.wlseno_get_info(None, None) == -1
+    assert lib.wlseno_reconstruct(None, None, None, None, None) == -1
+    assert lib.wlseno_rk_step(None, None, 0.0, 0.0, 1, None, None) == -1
+    lib.wlseno_destroy(None)
+    sch = W.wlseno_scheme()
+    sch.pde, sch.n_comp, sch.eps, sch.alpha_c, sch.rank_tol = 7, 1, 1e-2, 1.5, 1e-10
+    h = ctypes.c_void_p()
+    assert lib.wlseno_create(ctypes.byref(h), 0, ctypes.byref(sch)) == -1  # unknown pde
+
+
+def test_create_reports_missing_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    sch = W.wlseno_scheme()
+    sch.pde, sch.n_comp, sch.eps, sch.alpha_c, sch.rank_tol = 0, 1, 1e-2, 1.5, 1e-10
+    h = ctypes.c_void_p()
+    assert lib.wlseno_create(ctypes.byref(h), 0, ctypes.byref(sch)) == -4

@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances: FP64 mode max-abs 1e-10 on h-normalised coefficients, facet
+values and states (residuals relative to max(1, |L|_inf)); integer work
+(stencils) bit-exact; FP32-bulk mode relative L1 <= 1e-5 of the state."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import wlseno_oracle as O
+from paper_1602_02694_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1602_02694_gb300.wlseno import load_library
+    load_library()
+    return torch.device("cuda:0")
+
+
+def Context(**kw):
+    from paper_1602_02694_gb300.wlseno import Context as C
+    return C(0, **kw)
+
+
+# (name, mesh factory, p, ring, min_rows): ragged tails (162, 98, 200 cells),
+# periodic and transmissive, 2-D p = 3 / 4 and 3-D p = 3.
+CASES = {
+    "tri9_p3_periodic": (lambda: synth.tri_mesh(9, seed=11), 3, 1.0, 0),
+    "tri7_p3_open": (lambda: synth.tri_mesh(7, periodic=False, seed=12), 3, 1.0, 9),
+    "tri10_p4_ring2": (lambda: synth.tri_mesh(10, seed=13), 4, 2.0, 0),
+    "tet3_p3_open": (lambda: synth.tet_mesh(3, periodic=False, seed=14), 3, 2.0 / 3.0, 15),
+    "tet4_p3_periodic": (lambda: synth.tet_mesh(4, seed=15), 3, 2.0 / 3.0, 0),
+}
+
+_cache = {}
+
+
+def case(name, pde=O.ADVECTION):
+    key = (name, pde)
+    if key not in _cache:
+        make, p, ring, min_rows = CASES[name]
+        mesh = make()
+        vel = (1.0, 0.5, 0.25) if mesh.dim == 3 else (1.0, 1.0, 0.0)
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=p, ring=ring, pde=pde,
+                         velocity=vel, min_rows=min_rows)
+        _cache[key] = (mesh, prob)
+    return _cache[key]
+
+
+def field(mesh):
+    """Smooth data plus a jump, so that the weights vary strongly."""
+    if mesh.dim == 2:
+        return synth.cell_averages(mesh, lambda P: np.sin(2 * np.pi * P[:, 0]) * np.cos(2 * np.pi * P[:, 1])
+                                   + (P[:, 0] + 0.3 * P[:, 1] > 0.55))
+    return synth.cell_averages(mesh, lambda P: np.sin(2 * np.pi * (P[:, 0] + P[:, 2]))
+                               + (P[:, 1] > 0.5))
+
+
+def make_ctx(name, precision="fp64", pde="advection"):
+    mesh, prob = case(name, O.ADVECTION if pde == "advection" else O.BURGERS)
+    ctx = Context(pde=pde, velocity=prob.velocity, precision=precision)
+    ctx.build_stencils(mesh, order_p=prob.p, ring=prob.ring, min_rows=prob.min_rows)
+    ctx.precompute_moments()
+    return ctx, mesh, prob
+
+
+def facet_points(prob, mesh, i, f):
+    """Quadrature points of local facet f of cell i in the library's order
+    (facet vertices sorted by global index), in the cell's unwrapped frame."""
+    X = prob.geo.coords[i]
+    loc = sorted((v for v in range(prob.dim + 1) if v != f), key=lambda v: mesh.cells[i][v])
+    if prob.dim == 2:
+        g = math.sqrt(3.0) / 6.0
+        return [X[loc[0]] + t * (X[loc[1]] - X[loc[0]]) for t in (0.5 - g, 0.5 + g)]
+    return [sum((2 / 3 if a == q else 1 / 6) * X[loc[a]] for a in range(3)) for q in range(3)]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stencils_bit_exact(dev, name):
+    ctx, mesh, prob = make_ctx(name)
+    ptr, cols = ctx.stencils()
+    for i in range(prob.N):
+        assert list(cols[ptr[i]:ptr[i + 1]]) == prob.stencils[i], i
+    info = ctx.info()
+    assert info["max_stencil"] <= info["lanes_per_cell"] * info["rows_per_lane"]
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_geometry(dev, name):
+    ctx, mesh, prob = make_ctx(name)
+    g = ctx.geometry()
+    assert np.allclose(g["centroid"], prob.geo.centroid, rtol=0, atol=1e-15)
+    assert np.allclose(g["volume"], prob.geo.volume, rtol=1e-13, atol=0)
+    assert np.allclose(g["h"], prob.geo.h, rtol=1e-14, atol=0)
+    assert np.allclose(g["inradius"], prob.geo.inradius, rtol=1e-13, atol=0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_reconstruction_fp64(dev, name):
+    ctx, mesh, prob = make_ctx(name)
+    ubar = field(mesh)
+    m = prob.m
+    nq = 2 if prob.dim == 2 else 3
+    u = torch.tensor(ubar, device=dev)
+    coef = torch.empty(prob.N * m, dtype=torch.float64, device=dev)
+    fv = torch.empty(prob.N * (prob.dim + 1) * nq, dtype=torch.float64, device=dev)
+    ctx.reconstruct(u, coef, fv)
+    coef = coef.cpu().numpy().reshape(prob.N, m)
+    fv = fv.cpu().numpy().reshape(prob.N, prob.dim + 1, nq)
+    worst_c = worst_f = 0.0
+    for i in range(prob.N):
+        d, r = prob.reconstruct_cell(ubar, i)
+        assert r == m
+        worst_c = max(worst_c, float(np.max(np.abs(coef[i] - d))))
+        for f in range(prob.dim + 1):
+            for q, P in enumerate(facet_points(prob, mesh, i, f)):
+                worst_f = max(worst_f, abs(fv[i, f, q] - prob.eval_poly(d, i, P)))
+    assert worst_c <= TOL64, worst_c
+    assert worst_f <= TOL64, worst_f
+    assert ctx.diagnostics()["rank_deficient"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,pde", [("tri9_p3_periodic", "advection"), ("tri7_p3_open", "burgers"),
+                                      ("tri10_p4_ring2", "burgers"), ("tet3_p3_open", "advection"),
+                                      ("tet4_p3_periodic", "burgers")])
+def test_residual_fp64(dev, name, pde):
+    ctx, mesh, prob = make_ctx(name, pde=pde)
+    ubar = field(mesh) + 0.2
+    u = torch.tensor(ubar, device=dev)
+    L = torch.empty_like(u)
+    ctx.flux_residual(u, L)
+    ref = O.residual(prob, ubar)
+    err = float(np.max(np.abs(L.cpu().numpy() - ref)))
+    assert err <= TOL64 * max(1.0, float(np.max(np.abs(ref)))), err
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,pde,steps", [("tri9_p3_periodic", "advection", 3),
+                                            ("tri10_p4_ring2", "burgers", 2),
+                                            ("tet4_p3_periodic", "advection", 1)])
+def test_rk3_steps_fp64(dev, name, pde, steps):
+    ctx, mesh, prob = make_ctx(name, pde=pde)
+    ubar = field(mesh) + 0.2
+    u = torch.tensor(ubar, device=dev)
+    cfl = 0.3
+    dts = []
+    for _ in range(steps):
+        dts.append(ctx.rk_step(u, cfl=cfl, n_steps=1, want_dt=True))
+    ref, ref_dts = O.rk3_run(prob, ubar, steps, cfl=cfl)
+    assert np.allclose(dts, ref_dts, rtol=1e-14, atol=0)
+    err = float(np.max(np.abs(u.cpu().numpy() - ref)))
+    assert err <= TOL64, err
+    ctx.close()
+
+
+def test_rk3_fp32_bulk_matches_fp64_oracle(dev):
+    ctx, mesh, prob = make_ctx("tri10_p4_ring2", precision="fp32_bulk", pde="burgers")
+    ubar = synth.burgers_2d_initial(mesh)
+    u = torch.tensor(ubar, device=dev)
+    steps = 4
+    for _ in range(steps):
+        ctx.rk_step(u, cfl=0.3, n_steps=1)
+    ref, _ = O.rk3_run(prob, ubar, steps, cfl=0.3)
+    got = u.cpu().numpy()
+    rel_l1 = float(np.sum(np.abs(got - ref)) / np.sum(np.abs(ref)))
+    assert rel_l1 <= 1e-5, rel_l1
+    ctx.close()
+
+
+def test_conservation_and_constant_state(dev):
+    for precision in ("fp64", "fp32_bulk"):
+        ctx, mesh, prob = make_ctx("tri10_p4_ring2", precision=precision, pde="burgers")
+        vol = prob.geo.volume
+        ubar = synth.burgers_2d_initial(mesh)
+        u = torch.tensor(ubar, device=dev)
+        ctx.rk_step(u, cfl=0.3, n_steps=20)
+        got = u.cpu().numpy()
+        drift = abs(np.sum(vol * got) - np.sum(vol * ubar)) / np.sum(vol * np.abs(ubar))
+        assert drift <= 1e-13, (precision, drift)
+        c = torch.full((prob.N,), 0.625, dtype=torch.float64, device=dev)
+        ctx.rk_step(c, dt=1e-3, n_steps=3)
+        assert float(torch.max(torch.abs(c - 0.625))) <= 1e-13
+        ctx.close()
+
+
+def test_host_pointers_match_device(dev):
+    ctx, mesh, prob = make_ctx("tri10_p4_ring2", pde="burgers")
+    ubar = synth.burgers_2d_initial(mesh)
+    ud = torch.tensor(ubar, device=dev)
+    Ld = torch.empty_like(ud)
+    ctx.flux_residual(ud, Ld)
+    Lh = np.empty_like(ubar)
+    ctx.flux_residual(np.ascontiguousarray(ubar), Lh)
+    assert np.array_equal(Ld.cpu().numpy(), Lh)
+    uh = ubar.copy()
+    dt_h = ctx.rk_step(uh, cfl=0.3, n_steps=2, want_dt=True)
+    dt_d = ctx.rk_step(ud, cfl=0.3, n_steps=2, want_dt=True)
+    assert dt_h == dt_d
+    assert np.array_equal(ud.cpu().numpy(), uh)
+    ctx.close()
+
+
+def test_config1_advection_run(dev):
+    """2-D advection on the 32x32 jittered periodic mesh (2,048 cells), p = 3,
+    1-ring, CFL 0.4, initial sine product plus a square indicator: 3 steps."""
+    mesh = synth.tri_mesh(32, jitter=0.2, seed=1)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, velocity=(1.0, 1.0, 0.0))
+    ubar = synth.advection_2d_initial(mesh)
+    ctx = Context(pde="advection", velocity=(1.0, 1.0, 0.0))
+    ctx.build_stencils(mesh, order_p=3, ring=1.0)
+    ctx.precompute_moments()
+    u = torch.tensor(ubar, device=dev)
+    ctx.rk_step(u, cfl=0.4, n_steps=3)
+    ref, _ = O.rk3_run(prob, ubar, 3, cfl=0.4)
+    err = float(np.max(np.abs(u.cpu().numpy() - ref)))
+    assert err <= TOL64, err
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tri9_p3_periodic", "tri10_p4_ring2", "tet4_p3_periodic"])
+def test_every_kernel_shape_fp64(dev, name):
+    """Every compiled (lanes per cell, rows per lane) shape that holds the
+    stencil gives the oracle's coefficients; the autotuner picks one of them."""
+    mesh, prob = case(name)
+    ubar = field(mesh)
+    m = prob.m
+    ref = np.array([prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)])
+    u = torch.tensor(ubar, device=dev)
+    for G, R in [(8, 2), (8, 3), (8, 5), (16, 3), (16, 4)]:
+        if G * R < max(len(prob.stencils[i]) for i in range(prob.N)):
+            continue
+        ctx = Context(velocity=prob.velocity)
+        ctx.build_stencils(mesh, order_p=prob.p, ring=prob.ring, lanes_per_cell=G, rows_per_lane=R)
+        ctx.precompute_moments()
+        coef = torch.empty(prob.N * m, dtype=torch.float64, device=dev)
+        ctx.reconstruct(u, coef)
+        err = float(np.max(np.abs(coef.cpu().numpy().reshape(prob.N, m) - ref)))
+        assert err <= TOL64, (G, R, err)
+        G2, R2, us = ctx.autotune(u, reps=2)
+        assert G2 * R2 >= ctx.info()["max_stencil"] and us > 0
+        ctx.close()
+
+
+def test_fp32_bulk_refinement_reaches_fp64_accuracy(dev):
+    """Flagging every cell, the FP64-residual refinement sweep improves the
+    FP32 factorisation's coefficients (counted in the diagnostics)."""
+    mesh, prob = case("tri10_p4_ring2", O.BURGERS)
+    ubar = synth.burgers_2d_initial(mesh)
+    m = prob.m
+    ref = np.array([prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)])
+    u = torch.tensor(ubar, device=dev)
+    errs = {}
+    for kflag in (1e30, 0.0):
+        ctx = Context(pde="burgers", precision="fp32_bulk", kappa_flag=kflag if kflag > 0 else 1e-30)
+        ctx.build_stencils(mesh, order_p=4, ring=2.0)
+        ctx.precompute_moments()
+        coef = torch.empty(prob.N * m, dtype=torch.float64, device=dev)
+        ctx.reconstruct(u, coef)
+        flagged = ctx.diagnostics()["flagged_cells"]
+        errs[kflag] = float(np.max(np.abs(coef.cpu().numpy().reshape(prob.N, m) - ref)))
+        assert flagged == (0 if kflag > 0 else prob.N)
+        ctx.close()
+    # on this coarse mesh the least-squares residuals are large, which bounds
+    # what one plain refinement step can gain (kappa^2 eps |r|): it must help
+    assert errs[0.0] < 0.5 * errs[1e30], errs
+
+
+def test_full_size_sampled_parity(dev):
+    """The benchmark workload itself (131,072 cells, p = 4, 2-ring, Burgers):
+    FP64 coefficients and residual at sampled cells, FP32-bulk residual at the
+    same cells, and exact conservation of one full RK3 step in both modes."""
+    mesh = synth.tri_mesh(256, jitter=0.2, seed=1)
+    ubar = synth.burgers_2d_initial(mesh)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
+    rng = np.random.default_rng(7)
+    cells = sorted(set(rng.choice(prob.N, 24, replace=False).tolist()) | {0, prob.N - 1})
+    u = torch.tensor(ubar, device=dev)
+    res = {}
+    for precision, kflag in (("fp64", 1e3), ("fp32_bulk", 1e3), ("fp32_all", 1e-30), ("fp32_none", 1e30)):
+        ctx = Context(pde="burgers", precision=precision[:4] + ("_bulk" if precision != "fp64" else ""),
+                      kappa_flag=kflag)
+        ctx.build_stencils(mesh, order_p=4, ring=2.0)
+        ctx.precompute_moments()
+        coef = torch.empty(prob.N * 10, dtype=torch.float64, device=dev)
+        ctx.reconstruct(u, coef)
+        L = torch.empty_like(u)
+        ctx.flux_residual(u, L)
+        res[precision] = (coef.cpu().numpy().reshape(prob.N, 10), L.cpu().numpy())
+        v = u.clone()
+        ctx.rk_step(v, cfl=0.3, n_steps=1)
+        vol = prob.geo.volume
+        drift = abs(np.sum(vol * v.cpu().numpy()) - np.sum(vol * ubar)) / np.sum(vol * np.abs(ubar))
+        assert drift <= 1e-13, (precision, drift)
+        ctx.close()
+    coeffs = {}
+    worst = {k: 0.0 for k in res}
+    for i in cells:
+        coeffs[i] = prob.reconstruct_cell(ubar, i)[0]
+        for k in res:
+            worst[k] = max(worst[k], float(np.max(np.abs(res[k][0][i] - coeffs[i]))))
+    assert worst["fp64"] <= TOL64, worst
+    # FP32-bulk: one FP64-residual refinement sweep recovers near-FP64 coefficients
+    assert worst["fp32_all"] <= 1e-8 and worst["fp32_all"] <= 0.1 * worst["fp32_none"], worst
+    assert worst["fp32_bulk"] <= worst["fp32_none"] * 1.0000001, worst
+    # residual at the sampled cells from their facets
+    need = set(cells)
+    for i in cells:
+        need.update(prob.face_nbrs[i])
+    for j in need:
+        if j not in coeffs:
+            coeffs[j] = prob.reconstruct_cell(ubar, j)[0]
+    scale = 0.0
+    for i in cells:
+        acc = 0.0
+        for f in range(3):
+            c2, f2 = prob.sib[i, f]
+            if i < c2:
+                acc += O.facet_flux(prob, coeffs, i, f, int(c2))
+            else:
+                acc -= O.facet_flux(prob, coeffs, int(c2), int(f2), i)
+        Li = -acc / prob.geo.volume[i]
+        scale = max(scale, abs(Li))
+        assert abs(res["fp64"][1][i] - Li) <= TOL64 * max(1.0, abs(Li)), i
+        assert abs(res["fp32_bulk"][1][i] - Li) <= 1e-5 * max(1.0, abs(Li)), i
