@@ -212,6 +212,27 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
 wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
                              double* dt_out, void* stream);
 
+/* The operator of wlseno_flux_residual for callers that cannot allocate
+ * device memory when they call it (no paper counterpart: a deployment
+ * variant).  Code running inside a stream capture, real-time loops that
+ * forbid allocation after start-up and hosts that own all device memory
+ * through their own pool cannot call cudaMalloc; this call makes no
+ * allocation of any kind.  Its facet-value scratch is a fixed array inside
+ * the library (8 MiB of device memory on every GPU that loads the library,
+ * held until the process exits), so n_cells * (dim+1) * quad_per_facet may
+ * not exceed 1,048,576 (174,762 triangles, 87,381 tetrahedra): larger meshes
+ * get WLSENO_ERR_INVALID_ARG and a message.
+ * ubar, residual: [n_comp][n_cells] DEVICE arrays (host pointers are rejected
+ * with WLSENO_ERR_INVALID_ARG: staging them would allocate).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array and fully overwrites the part it reads, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (other streams, other
+ * contexts on the same device) race on it: order them on one stream.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+wlseno_status wlseno_flux_residual_static(wlseno_ctx* ctx, const double* ubar, double* residual,
+                                          void* stream);
+
 /* Adjoint of one fixed-dt TVD-RK3 step of wlseno_rk_step:
  * gbar_n = (d ubar^{n+1} / d ubar^n)^T gbar_next, including the derivative
  * through the solution-dependent weights omega_j and the per-facet LF alpha.

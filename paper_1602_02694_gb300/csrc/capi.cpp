@@ -217,6 +217,38 @@ wlseno_status check_ready(wlseno_ctx* ctx) {
 
 }  // namespace
 
+namespace wlseno {
+
+bool ctx_view(const wlseno_ctx* ctx, CtxView* out) {
+  if (!ctx || !out) return false;
+  out->device = ctx->device;
+  out->precision = ctx->scheme.precision;
+  out->n_comp = ctx->scheme.n_comp;
+  out->ready = ctx->built && ctx->moments_ready;
+  out->dm = ctx->dm;
+  out->sp = ctx->sp;
+  out->counters = ctx->d_counters;
+  out->dt = ctx->d_dt;
+  return true;
+}
+
+void ctx_set_error(wlseno_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->error = msg;
+}
+
+cudaError_t ctx_launch_reconstruct(wlseno_ctx* ctx, const double* ubar, const ReconOut& out,
+                                   cudaStream_t s) {
+  ctx->last_stream = s;
+  return reconstruct_one(ctx, ubar, out.coeffs, out.fvals, s);
+}
+
+cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const double* ubar,
+                                     double* residual, cudaStream_t s) {
+  return flux_one(ctx, fvals, ubar, nullptr, 0.0, 1.0, true, residual, s);
+}
+
+}  // namespace wlseno
+
 extern "C" {
 
 const char* wlseno_status_string(wlseno_status s) {

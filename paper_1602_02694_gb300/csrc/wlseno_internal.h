@@ -108,4 +108,23 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
                                int* launches);
 
+// Read-only view of a context and launch helpers for entry points that live
+// outside capi.cpp (they count launches like the context's own calls).
+struct CtxView {
+  int device;
+  int precision;
+  int n_comp;
+  bool ready;              // stencils built and moments precomputed
+  DeviceMesh dm;
+  SchemeParams sp;
+  unsigned long long* counters;
+  const double* dt;
+};
+bool ctx_view(const wlseno_ctx* ctx, CtxView* out);
+void ctx_set_error(wlseno_ctx* ctx, const std::string& msg);
+cudaError_t ctx_launch_reconstruct(wlseno_ctx* ctx, const double* ubar, const ReconOut& out,
+                                   cudaStream_t s);
+cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const double* ubar,
+                                     double* residual, cudaStream_t s);
+
 }  // namespace wlseno

@@ -83,6 +83,7 @@ SIGNATURES = {
     "wlseno_get_diagnostics": (_I, [_P, ctypes.POINTER(wlseno_diagnostics)]),
     "wlseno_set_timing": (_I, [_P, _I]),
     "wlseno_autotune": (_I, [_P, _P, _I, _P, _P]),
+    "wlseno_flux_residual_static": (_I, [_P, _P, _P, _P]),
     "wlseno_status_string": (ctypes.c_char_p, [_I]),
     "wlseno_last_error_message": (ctypes.c_char_p, [_P]),
 }
@@ -232,6 +233,15 @@ class Context:
         pr, _ = _ptr(residual, writable=True)
         s = stream if stream is not None else _stream_of(ubar, residual)
         self._check(self.lib.wlseno_flux_residual(self.h, pu, pr, s), "wlseno_flux_residual")
+
+    def flux_residual_static(self, ubar, residual, stream=None):
+        """wlseno_flux_residual_static: L(ubar) with no device allocation
+        (fixed library scratch; device arrays only)."""
+        pu, _ = _ptr(ubar)
+        pr, _ = _ptr(residual, writable=True)
+        s = stream if stream is not None else _stream_of(ubar, residual)
+        self._check(self.lib.wlseno_flux_residual_static(self.h, pu, pr, s),
+                    "wlseno_flux_residual_static")
 
     def rk_step(self, ubar, dt=0.0, cfl=0.0, n_steps=1, want_dt=False, stream=None):
         """TVD-RK3 steps in place; returns the last dt when want_dt."""
