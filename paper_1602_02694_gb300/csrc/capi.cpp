@@ -34,6 +34,8 @@ struct wlseno_ctx {
   double* d_out = nullptr;       // [C][N] staging for host outputs
   double* d_coef = nullptr;      // [C][N][m] staging for host coefficient output
   double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
+  int* d_wl = nullptr;           // [N] cells flagged for refinement (FP32-bulk)
+  int* d_wl_count = nullptr;     // [1]
   int64_t launches = 0;
   int64_t by_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
   // timing mode: event pairs recorded around launches, summed on demand
@@ -108,8 +110,10 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Shapes compiled into the reconstruction kernel (lanes per cell, rows per lane).
-const int kShapes[][2] = {{8, 2}, {8, 3}, {8, 5}, {16, 3}, {16, 4}};
+// Shapes compiled into the reconstruction (lanes per cell, rows per lane):
+// (1, 0) is the thread-per-cell kernel (any stencil size), the others the
+// lane-group kernel holding at most lanes x rows stencil rows.
+const int kShapes[][2] = {{1, 0}, {8, 2}, {8, 3}, {8, 5}, {16, 3}, {16, 4}};
 
 bool shape_ok(int G, int R) {
   for (auto& s : kShapes)
@@ -117,19 +121,14 @@ bool shape_ok(int G, int R) {
   return false;
 }
 
+// The thread-per-cell kernel hands ill-conditioned cells to the lane-group
+// kernel, whose largest compiled shape holds 64 rows.
+bool shape_fits(int G, int R, int max_n) { return G == 1 ? max_n <= 64 : G * R >= max_n; }
+
 void choose_shape(int max_n, int* G, int* R) {
-  int best = -1;
-  for (int k = 0; k < 5; ++k) {
-    int cap = kShapes[k][0] * kShapes[k][1];
-    if (cap < max_n) continue;
-    if (best < 0 || cap < kShapes[best][0] * kShapes[best][1]) best = k;
-  }
-  if (best < 0) {
-    *G = *R = 0;
-    return;
-  }
-  *G = kShapes[best][0];
-  *R = kShapes[best][1];
+  (void)max_n;
+  *G = 1;  // thread per cell: fastest on GB300 for every compiled (dim, m)
+  *R = 0;
 }
 
 int points_per_cell(const wlseno_ctx* ctx) { return (ctx->dm.dim + 1) * ctx->dm.nq; }
@@ -186,6 +185,21 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
   const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
   cudaError_t e = cudaErrorInvalidValue;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
+  if (ctx->G == 1) {
+    int nl = 0;
+    int* wl = ctx->d_wl;
+    if (dm.dim == 2 && dm.m == 6)
+      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
+              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+    else if (dm.dim == 2 && dm.m == 10)
+      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
+              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+    else if (dm.dim == 3 && dm.m == 10)
+      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
+              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+    scope.done(e == cudaSuccess ? nl : 0);
+    return e;
+  }
   if (dm.dim == 2 && dm.m == 6)
     e = f32 ? launch_reconstruct_inst<float, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
             : launch_reconstruct_inst<double, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
@@ -327,7 +341,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   } else if (!shape_ok(G, R)) {
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "lanes_per_cell/rows_per_lane not compiled");
   }
-  if (G * R < H.max_n || G == 0)
+  if (G == 0 || !shape_fits(G, R, H.max_n))
     return fail(ctx, WLSENO_ERR_STENCIL, "largest stencil (" + std::to_string(H.max_n) +
                                              " cells) exceeds the kernel's rows");
   ctx->G = G;
@@ -376,6 +390,12 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (st = dalloc(ctx, &ctx->d_counters, 4)) || (st = dalloc(ctx, &ctx->d_fvals, N * NP)) ||
       (st = dalloc(ctx, &ctx->d_k1, C * N)) || (st = dalloc(ctx, &ctx->d_k2, C * N)))
     return st;
+  dm.nmax = H.max_n;
+  const size_t ell = static_cast<size_t>(H.max_n) * N;
+  if ((st = dalloc(ctx, &dm.st_ell, ell)) || (st = dalloc(ctx, &dm.A64e, ell * H.m)) ||
+      (st = dalloc(ctx, &dm.A32e, ell * H.m)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
+      (st = dalloc(ctx, &ctx->d_wl_count, 1)))
+    return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
   ctx->d_in = ctx->d_out = ctx->d_coef = ctx->d_fv_out = nullptr;
@@ -390,7 +410,8 @@ wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   KernelScope scope(ctx, WLSENO_KERNEL_MOMENTS, s);
   cudaError_t e = launch_moments(ctx->dm, s);
-  scope.done(e == cudaSuccess ? 1 : 0);
+  if (e == cudaSuccess) e = launch_ell_copy(ctx->dm, s);
+  scope.done(e == cudaSuccess ? 2 : 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "moments kernel");
   ctx->moments_ready = true;
   ctx->last_stream = s;
@@ -578,7 +599,7 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
   int bestG = G0, bestR = R0;
   float best = -1.0f;
   for (auto& sh : kShapes) {
-    if (sh[0] * sh[1] < ctx->host.max_n) continue;
+    if (!shape_fits(sh[0], sh[1], ctx->host.max_n)) continue;
     ctx->G = sh[0];
     ctx->R = sh[1];
     e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);

@@ -1,0 +1,181 @@
+// Thread-per-cell reconstruction kernels (see k_recon_tpc.cuh).
+//
+// Main kernel: fold the stencil rows into R by Givens rotations (W A = Q R),
+// solve R d = Q^T W (ubar_S - ubar_i) by back substitution, and estimate the
+// conditioning of W A S from the column-scaled diagonal |R_kk| s_k.  For a
+// full-rank system this d is the least-squares solution the paper's QR with
+// column pivoting returns (Sec. 3.3.2).  Cells whose estimate exceeds the
+// flag threshold -- where pivoting and rank truncation could matter, and in
+// FP32-bulk mode where a refinement is due -- go to a work list.
+//
+// Work-listed cells are then redone by the lane-group kernel (rows spread over
+// the lanes of a group, so their loads run in parallel): the paper's path in
+// full -- column scaling, QR with column pivoting, numerical rank, basic
+// solution -- and, in FP32-bulk mode, one refinement sweep with the FP64
+// residual (FP64 weights and moments).  It overwrites the main kernel's
+// outputs for those cells.  (tpc_pivoted below is the same pivoted solve on
+// the small factor R S, kept for single-thread use.)
+#pragma once
+
+#include "k_recon_tpc.cuh"
+#include "k_reconstruct.cuh"
+
+namespace wlseno {
+
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* __restrict__ ubar,
+                                         int64_t i, double ui, int n, T eh2, T w_centre,
+                                         T (&R)[M][M + 1]) {
+  const int64_t N = dm.N;
+  const T* Ae = ell_moments<T>(dm);
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+#pragma unroll
+    for (int j = k; j <= M; ++j) R[k][j] = T(0);
+  // row t+1 is fetched while row t is folded (hides the index -> ubar chain)
+  double u_next = ubar[dm.st_ell[i]];
+  T a_next[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) a_next[c] = Ae[static_cast<int64_t>(c) * N + i];
+  for (int t = 0; t < n; ++t) {
+    const T dev = static_cast<T>(u_next - ui);
+    T a[M + 1];
+#pragma unroll
+    for (int c = 0; c < M; ++c) a[c] = a_next[c];
+    if (t + 1 < n) {
+      u_next = ubar[dm.st_ell[(t + 1) * N + i]];
+#pragma unroll
+      for (int c = 0; c < M; ++c) a_next[c] = Ae[(static_cast<int64_t>(t + 1) * M + c) * N + i];
+    }
+    const T w = t == 0 ? w_centre : eh2 / (dev * dev + eh2);
+#pragma unroll
+    for (int c = 0; c < M; ++c) a[c] *= w;
+    a[M] = w * dev;
+    givens_fold<T, M>(R, a);
+  }
+}
+
+// Column scaling from R's column norms and the pivoted QR of R S.
+template <typename T, int M>
+__device__ __forceinline__ void tpc_pivoted(const T (&R)[M][M + 1], T rank_tol, SmallQR<T, M>& q) {
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    T nrm2 = T(0);
+#pragma unroll
+    for (int k = 0; k <= c; ++k) nrm2 += R[k][c] * R[k][c];
+    const T s = nrm2 > T(0) ? rsqrt_t<T>(nrm2) : T(0);
+    q.s[c] = s;
+    q.col[c] = c;
+#pragma unroll
+    for (int k = 0; k < M; ++k) q.F[k][c] = k <= c ? R[k][c] * s : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < M; ++k) q.z[k] = R[k][M];
+  q.rank = M;
+  q.r00 = T(0);
+  q.rlast = T(0);
+  const T tau_piv = sizeof(T) == 8 ? T(1e-6) : T(1e-4);
+  small_qr_solve<T, M>(q, tau_piv, rank_tol, std::make_integer_sequence<int, M>{});
+}
+
+// Coefficients (original column order) and facet values of cell i.
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui,
+                                          const T (&hi)[M], const double (&lo)[M],
+                                          double* __restrict__ coeffs, double* __restrict__ fvals) {
+  constexpr int NP = (DIM + 1) * (DIM == 2 ? 2 : 3);
+  if (coeffs) {
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      coeffs[i * M + c] = static_cast<double>(hi[c]) + lo[c] + (c == 0 ? ui : 0.0);
+  }
+  const T* P = tpc_points<T>(dm) + i * NP * DIM;
+#pragma unroll
+  for (int pt = 0; pt < NP; ++pt) {
+    T yy[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) yy[a] = P[pt * DIM + a];
+    T mono[M];
+    eval_monomials<T, DIM, M>(yy, mono);
+    T sh = T(0);
+    double sl = 0.0;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      sh += hi[c] * mono[c];
+      sl += lo[c] * static_cast<double>(mono[c]);
+    }
+    fvals[i * NP + pt] = ui + static_cast<double>(sh) + sl;
+  }
+}
+
+template <typename T, int DIM, int M>
+__global__ void __launch_bounds__(128)
+recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
+                 double* __restrict__ coeffs, double* __restrict__ fvals,
+                 unsigned long long* __restrict__ counters, int* __restrict__ worklist,
+                 int* __restrict__ wl_count, T flag_threshold) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= dm.N) return;
+  const int n = dm.st_ptr[i + 1] - dm.st_ptr[i];
+  const double ui = ubar[i];
+  T eh2, wc;
+  tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
+  T R[M][M + 1];
+  tpc_fold<T, DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
+  // conditioning estimate of W A S from its scaled diagonal
+  T dmax = T(0), dmin = T(INFINITY);
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    T nrm2 = T(0);
+#pragma unroll
+    for (int k = 0; k <= c; ++k) nrm2 += R[k][c] * R[k][c];
+    const T dk = nrm2 > T(0) ? fabs(R[c][c]) * rsqrt_t<T>(nrm2) : T(0);
+    dmax = dk > dmax ? dk : dmax;
+    dmin = dk < dmin ? dk : dmin;
+  }
+  const bool flagged = !(dmax <= flag_threshold * dmin);  // also catches dmin == 0 and NaN
+  // R d = Q^T b
+  T d[M];
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    T t = R[k][M];
+#pragma unroll
+    for (int c = k + 1; c < M; ++c) t -= R[k][c] * d[c];
+    d[k] = R[k][k] != T(0) ? t / R[k][k] : T(0);
+  }
+  double lo[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) lo[c] = 0.0;
+  tpc_write<T, DIM, M>(dm, i, ui, d, lo, coeffs, fvals);
+  if (flagged) {
+    if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
+    worklist[atomicAdd(wl_count, 1)] = static_cast<int>(i);
+  }
+}
+
+template <typename T, int DIM, int M>
+cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                             const ReconOut& out, int* worklist, int* wl_count, cudaStream_t s,
+                             int* launches) {
+  constexpr int threads = 128;
+  const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
+  // FP32-bulk: refine above kappa_flag; FP64: take the pivoted path above 1e6
+  const T threshold = sizeof(T) == 4 ? static_cast<T>(sp.kappa_flag) : T(1e6);
+  *launches = 0;
+  cudaError_t e = cudaMemsetAsync(wl_count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
+                                                        out.counters, worklist, wl_count, threshold);
+  ++*launches;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the listed cells, one lane group each: rows spread over the lanes
+  if (dm.nmax <= 40)
+    e = launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, worklist, wl_count, s);
+  else
+    e = launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, worklist, wl_count, s);
+  ++*launches;
+  return e;
+}
+
+}  // namespace wlseno

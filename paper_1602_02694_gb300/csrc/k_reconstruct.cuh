@@ -206,23 +206,20 @@ constexpr size_t recon_smem_per_cell() {
   return static_cast<size_t>(G * R) * ((M + 1) * sizeof(T) + sizeof(int));
 }
 
+// One cell on the lanes of one group.  `listed`: the cell came from the work
+// list of the thread-per-cell kernel; in FP32-bulk it is always refined.
 template <typename T, int DIM, int M, int G, int R>
-__global__ void __launch_bounds__(128)
-reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                   double* __restrict__ coeffs, double* __restrict__ fvals,
-                   unsigned long long* __restrict__ counters) {
+__device__ __forceinline__ void group_reconstruct_cell(
+    const DeviceMesh& dm, const SchemeParams& sp, const double* __restrict__ ubar,
+    double* __restrict__ coeffs, double* __restrict__ fvals,
+    unsigned long long* __restrict__ counters, unsigned char* smem_raw, int g, int gib,
+    int64_t cell, bool valid, bool listed) {
   constexpr int NF = DIM + 1;
   constexpr int NQ = DIM == 2 ? 2 : 3;
   constexpr int NP = NF * NQ;
   constexpr int NR = G * R;
   constexpr bool kF32 = sizeof(T) == 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const T tau_piv = kF32 ? T(1e-4) : T(1e-6);
-
-  const int g = threadIdx.x % G;
-  const int gib = threadIdx.x / G;  // group in block
-  const int64_t cell = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
-  const bool valid = cell < dm.N;
   const int64_t ci = valid ? cell : 0;
   const int beg = dm.st_ptr[ci];
   const int n = valid ? dm.st_ptr[ci + 1] - beg : 0;
@@ -338,7 +335,7 @@ reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ub
     }
     st.rlast = rl;
   }
-  const bool flagged = valid && st.rank > 0 && st.r00 > static_cast<T>(sp.kappa_flag) * st.rlast;
+  const bool flagged = valid && (listed ? kF32 : (st.rank > 0 && st.r00 > static_cast<T>(sp.kappa_flag) * st.rlast));
 
   // FP32-bulk: one refinement sweep with the FP64 residual on flagged cells
   T dy[M];
@@ -432,8 +429,63 @@ reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ub
   if (!finite) atomicAdd(&counters[2], 1ull);
   if (g == 0) {
     if (st.rank < M) atomicAdd(&counters[1], 1ull);
-    if (flagged) atomicAdd(&counters[0], 1ull);
+    if (flagged && !listed) atomicAdd(&counters[0], 1ull);
   }
+}
+
+template <typename T, int DIM, int M, int G, int R>
+__global__ void __launch_bounds__(128)
+reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
+                   double* __restrict__ coeffs, double* __restrict__ fvals,
+                   unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t cell = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
+  group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, counters, smem_raw,
+                                          threadIdx.x % G, threadIdx.x / G, cell < dm.N ? cell : 0,
+                                          cell < dm.N, false);
+}
+
+// The work-listed cells of the thread-per-cell kernel (pivoted path, and in
+// FP32-bulk the refinement sweep), grid-stride over the list.
+template <typename T, int DIM, int M, int G, int R>
+__global__ void __launch_bounds__(128)
+reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
+                        double* __restrict__ coeffs, double* __restrict__ fvals,
+                        unsigned long long* __restrict__ counters, const int* __restrict__ worklist,
+                        const int* __restrict__ wl_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int count = *wl_count;
+  const int gpb = blockDim.x / G;
+  const int gib = threadIdx.x / G;
+  for (int base = blockIdx.x * gpb; base < count; base += gridDim.x * gpb) {
+    __syncwarp();
+    const int idx = base + gib;
+    const bool valid = idx < count;
+    const int64_t cell = valid ? worklist[idx] : 0;
+    group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, counters, smem_raw,
+                                            threadIdx.x % G, gib, cell, valid, true);
+  }
+}
+
+template <typename T, int DIM, int M, int G, int R>
+cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp,
+                                    const double* ubar, const ReconOut& out, const int* worklist,
+                                    const int* wl_count, cudaStream_t s) {
+  constexpr int threads = 128;
+  const size_t smem = recon_smem_per_cell<T, M, G, R>() * (threads / G);
+  static bool attr_set = false;  // per instantiation; set once per process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(reconstruct_list_kernel<T, DIM, M, G, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t groups = (dm.N * G + threads - 1) / threads;
+  const unsigned blocks = static_cast<unsigned>(groups < 152 * 8 ? groups : 152 * 8);
+  reconstruct_list_kernel<T, DIM, M, G, R><<<blocks, threads, smem, s>>>(
+      dm, sp, ubar, out.coeffs, out.fvals, out.counters, worklist, wl_count);
+  return cudaGetLastError();
 }
 
 template <typename T, int DIM, int M, int G, int R>

@@ -1,4 +1,5 @@
-// Instantiation of the reconstruction kernel for T = double, 2-D, m = 10.
+// Instantiations of the reconstruction kernels for T = double, 2-D, m = 10.
+#include "k_recon_tpc_kernels.cuh"
 #include "k_reconstruct.cuh"
 
 namespace wlseno {
@@ -7,5 +8,13 @@ cudaError_t launch_reconstruct_inst<double, 2, 10>(const DeviceMesh& dm, const S
                                                    int G, int R, const double* ubar,
                                                    const ReconOut& out, cudaStream_t s) {
   return launch_reconstruct_tm<double, 2, 10>(dm, sp, G, R, ubar, out, s);
+}
+
+template <>
+cudaError_t launch_recon_tpc_inst<double, 2, 10>(const DeviceMesh& dm, const SchemeParams& sp,
+                                                 const double* ubar, const ReconOut& out,
+                                                 int* worklist, int* wl_count, cudaStream_t s,
+                                                 int* launches) {
+  return launch_recon_tpc<double, 2, 10>(dm, sp, ubar, out, worklist, wl_count, s, launches);
 }
 }  // namespace wlseno

@@ -62,6 +62,11 @@ struct DeviceMesh {
   const float* fpts32;      // same, FP32
   double* A64;              // [nnz][m]
   float* A32;               // [nnz][m]
+  // ELL copies for the thread-per-cell kernel: row t of cell i at t*N + i
+  int nmax;                 // largest stencil
+  int32_t* st_ell;          // [nmax][N]
+  double* A64e;             // [nmax][m][N]
+  float* A32e;              // [nmax][m][N]
 };
 
 struct SchemeParams {
@@ -78,6 +83,27 @@ struct ReconOut {
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_moments(const DeviceMesh& dm, cudaStream_t s);
+// Copies the CSR stencil and moments into the ELL arrays.
+cudaError_t launch_ell_copy(const DeviceMesh& dm, cudaStream_t s);
+
+// Thread-per-cell reconstruction (and, in FP32-bulk with a work list, the
+// refinement sweep); *launches receives the number of kernels launched.
+template <typename T, int DIM, int M>
+cudaError_t launch_recon_tpc_inst(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                                  const ReconOut& out, int* worklist, int* wl_count, cudaStream_t s,
+                                  int* launches);
+#define WLSENO_DECLARE_TPC(T, D, M)                                                            \
+  template <>                                                                                   \
+  cudaError_t launch_recon_tpc_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,            \
+                                             const double*, const ReconOut&, int*, int*,        \
+                                             cudaStream_t, int*);
+WLSENO_DECLARE_TPC(double, 2, 6)
+WLSENO_DECLARE_TPC(double, 2, 10)
+WLSENO_DECLARE_TPC(double, 3, 10)
+WLSENO_DECLARE_TPC(float, 2, 6)
+WLSENO_DECLARE_TPC(float, 2, 10)
+WLSENO_DECLARE_TPC(float, 3, 10)
+#undef WLSENO_DECLARE_TPC
 
 // Reconstruction for one component; one translation unit per (T, DIM, M).
 template <typename T, int DIM, int M>

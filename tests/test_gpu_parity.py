@@ -92,7 +92,7 @@ def test_stencils_bit_exact(dev, name):
     for i in range(prob.N):
         assert list(cols[ptr[i]:ptr[i + 1]]) == prob.stencils[i], i
     info = ctx.info()
-    assert info["max_stencil"] <= info["lanes_per_cell"] * info["rows_per_lane"]
+    assert info["lanes_per_cell"] == 1 or info["max_stencil"] <= info["lanes_per_cell"] * info["rows_per_lane"]
     ctx.close()
 
 
@@ -239,8 +239,8 @@ def test_every_kernel_shape_fp64(dev, name):
     m = prob.m
     ref = np.array([prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)])
     u = torch.tensor(ubar, device=dev)
-    for G, R in [(8, 2), (8, 3), (8, 5), (16, 3), (16, 4)]:
-        if G * R < max(len(prob.stencils[i]) for i in range(prob.N)):
+    for G, R in [(1, 0), (8, 2), (8, 3), (8, 5), (16, 3), (16, 4)]:
+        if G > 1 and G * R < max(len(prob.stencils[i]) for i in range(prob.N)):
             continue
         ctx = Context(velocity=prob.velocity)
         ctx.build_stencils(mesh, order_p=prob.p, ring=prob.ring, lanes_per_cell=G, rows_per_lane=R)
@@ -250,7 +250,7 @@ def test_every_kernel_shape_fp64(dev, name):
         err = float(np.max(np.abs(coef.cpu().numpy().reshape(prob.N, m) - ref)))
         assert err <= TOL64, (G, R, err)
         G2, R2, us = ctx.autotune(u, reps=2)
-        assert G2 * R2 >= ctx.info()["max_stencil"] and us > 0
+        assert (G2 == 1 or G2 * R2 >= ctx.info()["max_stencil"]) and us > 0
         ctx.close()
 
 
