@@ -202,7 +202,8 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
 
 /* n_steps steps of TVD-RK3 (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta)) in place.
  * ubar:   [n_comp][n_cells], host or device; overwritten with the result.
- * dt:     > 0: fixed step;  <= 0: each step uses
+ * dt:     > 0: the same fixed step for every mesh;  < 0: the per-mesh fixed
+ *         steps given to wlseno_set_mesh_dt;  == 0: each step uses
  *         dt = cfl * min_i r_i / lambda_max with r_i = dim |tau_i| / |d tau_i|
  *         and lambda_max the largest wave speed over the cells (advection |a|,
  *         Burgers sqrt(dim) max |ubar|), computed on the device per mesh.
@@ -233,12 +234,24 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
 wlseno_status wlseno_flux_residual_static(wlseno_ctx* ctx, const double* ubar, double* residual,
                                           void* stream);
 
-/* Adjoint of one fixed-dt TVD-RK3 step of wlseno_rk_step:
+/* Per-mesh fixed time steps dt_host[n_meshes] (host, all > 0) for
+ * wlseno_rk_step and wlseno_step_adjoint called with dt < 0 (a batch of
+ * problems each stepping at its own dt).  Errors: STATE, INVALID_ARG, CUDA. */
+wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host);
+
+/* Adjoint of one fixed-dt TVD-RK3 step of wlseno_rk_step (the paper has no
+ * adjoint; this differentiates its scheme):
  * gbar_n = (d ubar^{n+1} / d ubar^n)^T gbar_next, including the derivative
- * through the solution-dependent weights omega_j and the per-facet LF alpha.
- * ubar_n: the step's input state (checkpoint); the stages are recomputed.
- * All arrays [n_comp][n_cells], host or device.
- * Errors: STATE, INVALID_ARG, CUDA. */
+ * through the solution-dependent weights omega_j (and the centre's minimum
+ * over its facet neighbours) and through the per-facet LF alpha (at its
+ * first maximiser); the derivative of the weighted least squares uses its
+ * full-rank normal form.  Computed in FP64 kernels with a deterministic
+ * transposed-stencil gather (no atomics).
+ * ubar_n: the step's input state (checkpoint); the two inner stages are
+ * recomputed.  dt: > 0 fixed for every mesh, < 0 the per-mesh steps of
+ * wlseno_set_mesh_dt (0 is rejected: a CFL step is not differentiated).
+ * All arrays [n_cells] (n_comp = 1), host or device; the first call
+ * allocates the adjoint's work arrays.  Errors: STATE, INVALID_ARG, CUDA. */
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
                                   const double* gbar_next, double* gbar_n, void* stream);
 

@@ -36,6 +36,10 @@ struct wlseno_ctx {
   double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
   int* d_wl = nullptr;           // [N] cells flagged for refinement (FP32-bulk)
   int* d_wl_count = nullptr;     // [1]
+  bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
+  // adjoint work (allocated on the first wlseno_step_adjoint)
+  AdjointWork adj{};
+  double* d_gbar[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int64_t by_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
   // timing mode: event pairs recorded around launches, summed on demand
@@ -512,7 +516,9 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   wlseno_status st = check_ready(ctx);
   if (st != WLSENO_OK) return st;
   if (!ubar || n_steps < 0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null ubar or n_steps < 0");
-  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(ctx, WLSENO_ERR_INVALID_ARG, "need dt > 0 or cfl > 0");
+  if (dt < 0.0 && !ctx->mesh_dt_set)
+    return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
+  if (dt == 0.0 && !(cfl > 0.0)) return fail(ctx, WLSENO_ERR_INVALID_ARG, "need dt != 0 or cfl > 0");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ctx->last_stream = s;
@@ -531,10 +537,13 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     return cuda_fail(ctx, e, "reset counters");
   for (int step = 0; step < n_steps; ++step) {
     int nl = 0;
-    KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
-    e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
-                           dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, s, &nl);
-    scope.done(nl);
+    if (dt >= 0.0) {  // dt < 0: the per-mesh steps already in d_dt
+      KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
+      e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
+                             dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, s, &nl);
+      scope.done(nl);
+      if (dt > 0.0) ctx->mesh_dt_set = false;
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "time step kernel");
     for (int c = 0; c < C; ++c) {
       double* u0 = u + c * N;
@@ -630,15 +639,121 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
   return WLSENO_OK;
 }
 
+wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host) {
+  if (!ctx || !dt_host) return WLSENO_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, WLSENO_ERR_STATE, "call wlseno_build_stencils first");
+  for (int k = 0; k < ctx->host.n_meshes; ++k)
+    if (!(dt_host[k] > 0.0)) return fail(ctx, WLSENO_ERR_INVALID_ARG, "per-mesh dt must be > 0");
+  DeviceGuard guard(ctx->device);
+  cudaError_t e = cudaMemcpy(ctx->d_dt, dt_host, sizeof(double) * ctx->host.n_meshes,
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "set mesh dt");
+  ctx->mesh_dt_set = true;
+  return WLSENO_OK;
+}
+
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
                                   const double* gbar_next, double* gbar_n, void* stream) {
-  (void)ubar_n;
-  (void)dt;
-  (void)gbar_next;
-  (void)gbar_n;
-  (void)stream;
-  if (!ctx) return WLSENO_ERR_INVALID_ARG;
-  return fail(ctx, WLSENO_ERR_STATE, "the adjoint is not available in this build");
+  wlseno_status st = check_ready(ctx);
+  if (st != WLSENO_OK) return st;
+  if (!ubar_n || !gbar_next || !gbar_n) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null array");
+  if (dt == 0.0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint needs a fixed dt (> 0, or < 0 for per-mesh steps)");
+  if (dt < 0.0 && !ctx->mesh_dt_set)
+    return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->last_stream = s;
+  const int64_t N = ctx->dm.N;
+  const int NP = points_per_cell(ctx);
+  cudaError_t e;
+  // work arrays on first use
+  if (!ctx->adj.gfv) {
+    AdjointWork& w = ctx->adj;
+    double* tp = nullptr;
+    int64_t* tr_ptr = nullptr;
+    int64_t* tr_slot = nullptr;
+    if ((st = dalloc(ctx, &w.gfv, N * NP)) || (st = dalloc(ctx, &w.contrib, ctx->dm.nmax * N)) ||
+        (st = dalloc(ctx, &w.selfbar, N)) || (st = dalloc(ctx, &w.amin_cell, N)) ||
+        (st = dalloc(ctx, &w.amin_val, N)) || (st = upload(ctx, &tr_ptr, ctx->host.tr_ptr)) ||
+        (st = upload(ctx, &tr_slot, ctx->host.tr_slot)) || (st = dalloc(ctx, &tp, 6 * N)))
+      return st;
+    w.tr_ptr = tr_ptr;
+    w.tr_slot = tr_slot;
+    for (int k = 0; k < 6; ++k) ctx->d_gbar[k] = tp + k * N;
+  }
+  double* t = ctx->d_gbar[0];    // J_L^T products
+  double* gk2 = ctx->d_gbar[1];
+  double* gk1 = ctx->d_gbar[2];
+  double* u = ctx->d_gbar[3];    // staged inputs / output
+  double* gnext = ctx->d_gbar[4];
+  double* gout = ctx->d_gbar[5];
+  const bool in_host = !is_device_pointer(ubar_n), g_host = !is_device_pointer(gbar_next);
+  const bool out_host = !is_device_pointer(gbar_n);
+  if (in_host) {
+    if ((e = cudaMemcpyAsync(u, ubar_n, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy ubar_n");
+  } else {
+    u = const_cast<double*>(ubar_n);
+  }
+  if (g_host) {
+    if ((e = cudaMemcpyAsync(gnext, gbar_next, sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy gbar_next");
+  } else {
+    gnext = const_cast<double*>(gbar_next);
+  }
+  double* gres = out_host ? gout : gbar_n;
+  if (dt > 0.0) {
+    int nl = 0;
+    KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
+    e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, 0.0, dt,
+                           ctx->d_lmax, ctx->d_dt, s, &nl);
+    scope.done(nl);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dt");
+    ctx->mesh_dt_set = false;
+  }
+  // recompute the stages k1, k2 of the step from the checkpoint u
+  double* k1 = ctx->d_k1;
+  double* k2 = ctx->d_k2;
+  if ((e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
+      (e = flux_one(ctx, ctx->d_fvals, u, u, 0.0, 1.0, false, k1, s)) != cudaSuccess ||
+      (e = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
+      (e = flux_one(ctx, ctx->d_fvals, k1, u, 0.75, 0.25, false, k2, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "adjoint: forward stages");
+  auto vjp = [&](const double* state, const double* lam, double* out) -> cudaError_t {
+    cudaError_t err = reconstruct_one(ctx, state, nullptr, ctx->d_fvals, s);
+    if (err != cudaSuccess) return err;
+    int nl = 0;
+    KernelScope scope(ctx, WLSENO_KERNEL_ADJOINT, s);
+    err = launch_operator_vjp(ctx->dm, ctx->sp, state, ctx->d_fvals, lam, ctx->adj, out, s, &nl);
+    scope.done(nl);
+    return err;
+  };
+  auto combine = [&](const double* x, double ca, const double* y, double cb, const double* w,
+                     double cc, const double* z, double cz, double* out) -> cudaError_t {
+    KernelScope scope(ctx, WLSENO_KERNEL_ADJOINT, s);
+    cudaError_t err = launch_adj_combine(ctx->dm, ctx->d_dt, x, ca, y, cb, w, cc, z, cz, out, s);
+    scope.done(1);
+    return err;
+  };
+  // u' = u/3 + 2/3 (k2 + dt L(k2)):  gk2 = 2/3 (g' + dt J(k2)^T g')
+  // k2 = 3/4 u + 1/4 (k1 + dt L(k1)): gk1 = 1/4 (gk2 + dt J(k1)^T gk2)
+  // k1 = u + dt L(u):                 g = g'/3 + 3/4 gk2 + gk1 + dt J(u)^T gk1
+  if ((e = vjp(k2, gnext, t)) != cudaSuccess ||
+      (e = combine(gnext, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0, t, 2.0 / 3.0, gk2)) != cudaSuccess ||
+      (e = vjp(k1, gk2, t)) != cudaSuccess ||
+      (e = combine(gk2, 0.25, nullptr, 0.0, nullptr, 0.0, t, 0.25, gk1)) != cudaSuccess ||
+      (e = vjp(u, gk1, t)) != cudaSuccess ||
+      (e = combine(gnext, 1.0 / 3.0, gk2, 0.75, gk1, 1.0, t, 1.0, gres)) != cudaSuccess)
+    return cuda_fail(ctx, e, "adjoint");
+  if (out_host) {
+    e = cudaMemcpyAsync(gbar_n, gout, sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy gbar_n");
+  }
+  if (in_host || g_host || out_host) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint");
+  }
+  return WLSENO_OK;
 }
 
 wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out) {

@@ -445,6 +445,18 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
     S.max_n = std::max(S.max_n, n);
     S.min_n = std::min(S.min_n, n);
   }
+  // transposed stencils for the adjoint's deterministic gather
+  S.tr_ptr.assign(N + 1, 0);
+  for (int64_t c = 0; c < N; ++c)
+    for (int64_t e = S.row_ptr[c] + 1; e < S.row_ptr[c + 1]; ++e) S.tr_ptr[S.cols[e] + 1]++;
+  for (int64_t j = 0; j < N; ++j) S.tr_ptr[j + 1] += S.tr_ptr[j];
+  S.tr_slot.assign(S.tr_ptr[N], 0);
+  {
+    std::vector<int64_t> fill(S.tr_ptr.begin(), S.tr_ptr.end() - 1);
+    for (int64_t c = 0; c < N; ++c)
+      for (int64_t e = S.row_ptr[c] + 1; e < S.row_ptr[c + 1]; ++e)
+        S.tr_slot[fill[S.cols[e]]++] = (e - S.row_ptr[c]) * N + c;  // ascending c, then t
+  }
   if (S.nnz >= (int64_t(1) << 31)) {
     *err = "stencil storage exceeds 32-bit offsets";
     return WLSENO_ERR_STENCIL;

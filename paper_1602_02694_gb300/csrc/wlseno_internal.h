@@ -35,6 +35,10 @@ struct HostSetup {
   std::vector<int32_t> nbr;       // [N][dim+1]: (j << 2) | f' or -1 (boundary)
   std::vector<double> fgeo;       // [N][dim+1][4]: owner's unit normal (dim), area
   std::vector<double> fpts;       // [N][dim+1][nq][dim]: (x_q - x_i) / h_i
+  // transposed stencils (adjoint gather): for cell j, the ELL slots t*N + c
+  // with stencil row t >= 1 of cell c equal to j, ordered by (c, t)
+  std::vector<int64_t> tr_ptr;    // [N+1]
+  std::vector<int64_t> tr_slot;   // [nnz - N]
 };
 
 wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
@@ -133,6 +137,25 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
                                const double* u, const double* rmin, double cfl, double dt_fixed,
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
                                int* launches);
+
+// Work arrays of the adjoint (k_adjoint.cu).
+struct AdjointWork {
+  double* gfv;             // [N][dim+1][nq] cotangents of each cell's facet traces
+  double* contrib;         // [nmax][N] per-(row, cell) cotangents for stencil cells
+  double* selfbar;         // [N]
+  int* amin_cell;          // [N] facet neighbour giving the centre's beta
+  double* amin_val;        // [N]
+  const int64_t* tr_ptr;   // [N+1] transposed stencils
+  const int64_t* tr_slot;  // [nnz-N]
+};
+// out = J_L(state)^T lambda (fvals: the facet traces of `state`).
+cudaError_t launch_operator_vjp(const DeviceMesh& dm, const SchemeParams& sp, const double* state,
+                                const double* fvals, const double* lambda, const AdjointWork& w,
+                                double* out, cudaStream_t s, int* launches);
+// out = ca x + cb y + cc w + cz dt_mesh z (null inputs skipped).
+cudaError_t launch_adj_combine(const DeviceMesh& dm, const double* dt_mesh, const double* x,
+                               double ca, const double* y, double cb, const double* w, double cc,
+                               const double* z, double cz, double* out, cudaStream_t s);
 
 // Read-only view of a context and launch helpers for entry points that live
 // outside capi.cpp (they count launches like the context's own calls).

@@ -84,6 +84,7 @@ SIGNATURES = {
     "wlseno_set_timing": (_I, [_P, _I]),
     "wlseno_autotune": (_I, [_P, _P, _I, _P, _P]),
     "wlseno_flux_residual_static": (_I, [_P, _P, _P, _P]),
+    "wlseno_set_mesh_dt": (_I, [_P, _P]),
     "wlseno_status_string": (ctypes.c_char_p, [_I]),
     "wlseno_last_error_message": (ctypes.c_char_p, [_P]),
 }
@@ -263,6 +264,11 @@ class Context:
                     "wlseno_autotune")
         inf = self.info()
         return inf["lanes_per_cell"], inf["rows_per_lane"], best.value
+
+    def set_mesh_dt(self, dts):
+        """Per-mesh fixed steps, used by rk_step / step_adjoint with dt < 0."""
+        a = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self.lib.wlseno_set_mesh_dt(self.h, a.ctypes.data), "wlseno_set_mesh_dt")
 
     def step_adjoint(self, ubar_n, dt, gbar_next, gbar_n, stream=None):
         pu, _ = _ptr(ubar_n)
