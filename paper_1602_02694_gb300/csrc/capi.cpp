@@ -37,6 +37,14 @@ struct wlseno_ctx {
   int* d_wl = nullptr;           // [N] cells flagged for refinement (FP32-bulk)
   int* d_wl_count = nullptr;     // [1]
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
+  // one captured RK step, replayed for multi-step calls
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  const double* graph_u = nullptr;
+  double graph_dt = 0.0, graph_cfl = 0.0;
+  int graph_G = 0;
+  int64_t graph_launches = 0;
+  int64_t graph_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
   // adjoint work (allocated on the first wlseno_step_adjoint)
   AdjointWork adj{};
   double* d_gbar[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -321,6 +329,8 @@ void wlseno_destroy(wlseno_ctx* ctx) {
   if (!ctx) return;
   {
     DeviceGuard g(ctx->device);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     free_all(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   }
@@ -331,8 +341,12 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
                                     const wlseno_stencil_opts* opts) {
   if (!ctx) return WLSENO_ERR_INVALID_ARG;
   DeviceGuard guard(ctx->device);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);  // it captured the old buffers
+  ctx->graph_exec = nullptr;
   free_all(ctx);
   ctx->built = ctx->moments_ready = false;
+  ctx->mesh_dt_set = false;
+  ctx->adj = AdjointWork{};
   std::string err;
   HostSetup& H = ctx->host;
   wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err);
@@ -535,34 +549,89 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   }
   if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
-  for (int step = 0; step < n_steps; ++step) {
-    int nl = 0;
+  // one TVD-RK3 step on stream `st` (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta))
+  auto enqueue_step = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t err = cudaSuccess;
     if (dt >= 0.0) {  // dt < 0: the per-mesh steps already in d_dt
-      KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
-      e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
-                             dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, s, &nl);
+      int nl = 0;
+      KernelScope scope(ctx, WLSENO_KERNEL_DT, st);
+      err = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
+                               dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl);
       scope.done(nl);
-      if (dt > 0.0) ctx->mesh_dt_set = false;
+      if (err != cudaSuccess) return err;
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "time step kernel");
     for (int c = 0; c < C; ++c) {
       double* u0 = u + c * N;
       double* k1 = ctx->d_k1 + c * N;
       double* k2 = ctx->d_k2 + c * N;
-      // k1 = u + dt L(u)
-      if ((e = reconstruct_one(ctx, u0, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
-          (e = flux_one(ctx, ctx->d_fvals, u0, u0, 0.0, 1.0, false, k1, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "RK stage 1");
-      // k2 = 3/4 u + 1/4 (k1 + dt L(k1))
-      if ((e = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
-          (e = flux_one(ctx, ctx->d_fvals, k1, u0, 0.75, 0.25, false, k2, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "RK stage 2");
-      // u <- 1/3 u + 2/3 (k2 + dt L(k2))
-      if ((e = reconstruct_one(ctx, k2, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
-          (e = flux_one(ctx, ctx->d_fvals, k2, u0, 1.0 / 3.0, 2.0 / 3.0, false, u0, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "RK stage 3");
+      // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
+      if ((err = reconstruct_one(ctx, u0, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
+          (err = flux_one(ctx, ctx->d_fvals, u0, u0, 0.0, 1.0, false, k1, st)) != cudaSuccess ||
+          (err = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
+          (err = flux_one(ctx, ctx->d_fvals, k1, u0, 0.75, 0.25, false, k2, st)) != cudaSuccess ||
+          (err = reconstruct_one(ctx, k2, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
+          (err = flux_one(ctx, ctx->d_fvals, k2, u0, 1.0 / 3.0, 2.0 / 3.0, false, u0, st)) != cudaSuccess)
+        return err;
     }
+    return cudaSuccess;
+  };
+  // Several steps: capture one step as a CUDA graph (on the context's own
+  // stream) and launch it n_steps times on `s`.  Not when timing, and not when
+  // `s` is itself being captured (then the launches join the caller's graph).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
   }
+  const bool use_graph = n_steps >= 2 && !ctx->timing && cap == cudaStreamCaptureStatusNone;
+  if (use_graph) {
+    const bool same = ctx->graph_exec && ctx->graph_u == u && ctx->graph_dt == dt &&
+                      ctx->graph_cfl == cfl && ctx->graph_G == ctx->G;
+    if (!same) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      if (!ctx->cap_stream &&
+          (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(ctx, e, "capture stream");
+      const int64_t l0 = ctx->launches;
+      int64_t k0[WLSENO_N_KERNEL_KINDS];
+      for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) k0[k] = ctx->by_kind[k];
+      cudaGraph_t graph = nullptr;
+      if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(ctx, e, "begin capture");
+      cudaError_t ecap = enqueue_step(ctx->cap_stream);
+      e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      if (ecap != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, ecap != cudaSuccess ? ecap : e, "capture step");
+      }
+      e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return cuda_fail(ctx, e, "instantiate step graph");
+      }
+      ctx->graph_launches = ctx->launches - l0;
+      ctx->launches = l0;
+      for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) {
+        ctx->graph_kind[k] = ctx->by_kind[k] - k0[k];
+        ctx->by_kind[k] = k0[k];
+      }
+      ctx->graph_u = u;
+      ctx->graph_dt = dt;
+      ctx->graph_cfl = cfl;
+      ctx->graph_G = ctx->G;
+    }
+    for (int step = 0; step < n_steps; ++step) {
+      if ((e = cudaGraphLaunch(ctx->graph_exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+      ctx->launches += ctx->graph_launches;
+      for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) ctx->by_kind[k] += ctx->graph_kind[k];
+    }
+  } else {
+    for (int step = 0; step < n_steps; ++step)
+      if ((e = enqueue_step(s)) != cudaSuccess) return cuda_fail(ctx, e, "RK step");
+  }
+  if (dt > 0.0) ctx->mesh_dt_set = false;
   if (host) {
     e = cudaMemcpyAsync(ubar, ctx->d_in, sizeof(double) * C * N, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar back");

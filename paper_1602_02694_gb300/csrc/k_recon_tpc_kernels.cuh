@@ -79,7 +79,9 @@ __device__ __forceinline__ void tpc_pivoted(const T (&R)[M][M + 1], T rank_tol, 
 }
 
 // Coefficients (original column order) and facet values of cell i.
-template <typename T, int DIM, int M>
+// Without the FP64 low part (kLo = false) no FP64 multiply-add is issued:
+// on GB300 the FP64 pipe runs at 1/64 of the FP32 rate.
+template <typename T, int DIM, int M, bool kLo = true>
 __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui,
                                           const T (&hi)[M], const double (&lo)[M],
                                           double* __restrict__ coeffs, double* __restrict__ fvals) {
@@ -87,7 +89,7 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
   if (coeffs) {
 #pragma unroll
     for (int c = 0; c < M; ++c)
-      coeffs[i * M + c] = static_cast<double>(hi[c]) + lo[c] + (c == 0 ? ui : 0.0);
+      coeffs[i * M + c] = static_cast<double>(hi[c]) + (kLo ? lo[c] : 0.0) + (c == 0 ? ui : 0.0);
   }
   const T* P = tpc_points<T>(dm) + i * NP * DIM;
 #pragma unroll
@@ -102,14 +104,14 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       sh += hi[c] * mono[c];
-      sl += lo[c] * static_cast<double>(mono[c]);
+      if (kLo) sl += lo[c] * static_cast<double>(mono[c]);
     }
     fvals[i * NP + pt] = ui + static_cast<double>(sh) + sl;
   }
 }
 
 template <typename T, int DIM, int M>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
                  double* __restrict__ coeffs, double* __restrict__ fvals,
                  unsigned long long* __restrict__ counters, int* __restrict__ worklist,
@@ -146,7 +148,7 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   double lo[M];
 #pragma unroll
   for (int c = 0; c < M; ++c) lo[c] = 0.0;
-  tpc_write<T, DIM, M>(dm, i, ui, d, lo, coeffs, fvals);
+  tpc_write<T, DIM, M, false>(dm, i, ui, d, lo, coeffs, fvals);
   if (flagged) {
     if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
     worklist[atomicAdd(wl_count, 1)] = static_cast<int>(i);

@@ -1,0 +1,183 @@
+"""The workloads beside the benchmark's, through the C ABI on the GPU:
+
+* 2-D advection on the 32x32 jittered periodic mesh (2,048 cells), p = 3,
+  1-ring, CFL 0.4, sine product plus square indicator, 100 steps, FP64,
+  against the oracle's 100 steps;
+* 3-D advection on Kuhn tetrahedra, p = 3, 2/3-ring plus the 1-ring cells
+  within 0.95 h_i (= 1.2 lattice spacings: 29-52 cells), Gaussian plus ball:
+  parity with the oracle on a 6^3 mesh, and on the full 64^3 mesh
+  (1,572,864 cells) conservation, FP32-bulk vs FP64 and finiteness;
+* 48 batched periodic Burgers problems n in {16, 24, ..., 256} (seeded),
+  p = 3, 1-ring, per-problem dt: batched vs separate contexts, and the
+  gradient of sum w u(T)^2 after 50 steps from the checkpointed adjoint
+  against central differences (1e-6, FP64) on 64 random directions."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import wlseno_oracle as O
+from paper_1602_02694_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+RADIUS_CUT_3D = 0.95
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return torch.device("cuda:0")
+
+
+def Context(**kw):
+    from paper_1602_02694_gb300.wlseno import Context as C
+    return C(0, **kw)
+
+
+def test_config1_full_run_matches_oracle(dev):
+    mesh = synth.tri_mesh(32, jitter=0.2, seed=1)
+    ubar = synth.advection_2d_initial(mesh)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, velocity=(1.0, 1.0, 0.0))
+    ref, ref_dts = O.rk3_run(prob, ubar, 100, cfl=0.4)
+    ctx = Context(pde="advection", velocity=(1.0, 1.0, 0.0))
+    ctx.build_stencils(mesh, order_p=3, ring=1.0)
+    ctx.precompute_moments()
+    u = torch.tensor(ubar, device=dev)
+    dt = ctx.rk_step(u, cfl=0.4, n_steps=100, want_dt=True)
+    assert abs(dt - ref_dts[-1]) <= 1e-15 * dt
+    err = float(np.max(np.abs(u.cpu().numpy() - ref)))
+    assert err <= TOL64, err
+    ctx.close()
+
+
+def tet_initial(mesh, k=3):
+    c = np.array([0.5, 0.5, 0.5])
+
+    def f(P):
+        d = P - c
+        d -= np.round(d)
+        r2 = np.sum(d * d, axis=1)
+        return np.exp(-50.0 * r2) + (r2 <= 0.15 ** 2)
+
+    return synth.cell_averages(mesh, f, k=k)
+
+
+def test_config4_parity_small(dev):
+    mesh = synth.tet_mesh(6, jitter=0.15, seed=1)
+    ubar = tet_initial(mesh)
+    vel = (1.0, 0.5, 0.25)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0 / 3.0, velocity=vel,
+                     radius_cut=RADIUS_CUT_3D)
+    ctx = Context(pde="advection", velocity=vel)
+    ctx.build_stencils(mesh, order_p=3, ring=2.0 / 3.0, radius_cut=RADIUS_CUT_3D)
+    ctx.precompute_moments()
+    info = ctx.info()
+    assert 25 <= info["min_stencil"] and info["max_stencil"] <= 64
+    ptr, cols = ctx.stencils()
+    rng = np.random.default_rng(3)
+    cells = sorted(rng.choice(prob.N, 40, replace=False).tolist())
+    for i in cells:
+        assert list(cols[ptr[i]:ptr[i + 1]]) == prob.stencils[i]
+    u = torch.tensor(ubar, device=dev)
+    coef = torch.empty(prob.N * 10, dtype=torch.float64, device=dev)
+    ctx.reconstruct(u, coef)
+    coef = coef.cpu().numpy().reshape(prob.N, 10)
+    for i in cells:
+        d, r = prob.reconstruct_cell(ubar, i)
+        assert np.max(np.abs(coef[i] - d)) <= TOL64, i
+    ctx.close()
+
+
+def test_config4_full_size_properties(dev):
+    mesh = synth.tet_mesh(64, jitter=0.15, seed=1)
+    assert mesh.n_cells == 1572864
+    ubar = tet_initial(mesh, k=2)
+    vel = (1.0, 0.5, 0.25)
+    states = {}
+    vol = None
+    for precision in ("fp64", "fp32_bulk"):
+        ctx = Context(pde="advection", velocity=vel, precision=precision)
+        ctx.build_stencils(mesh, order_p=3, ring=2.0 / 3.0, radius_cut=RADIUS_CUT_3D)
+        ctx.precompute_moments()
+        vol = ctx.geometry()["volume"]
+        u = torch.tensor(ubar, device=dev)
+        ctx.rk_step(u, cfl=0.3, n_steps=3)
+        diag = ctx.diagnostics()
+        assert diag["nonfinite"] == 0 and diag["rank_deficient"] == 0
+        states[precision] = u.cpu().numpy()
+        drift = abs(np.sum(vol * states[precision]) - np.sum(vol * ubar)) / np.sum(vol * np.abs(ubar))
+        assert drift <= 1e-13, (precision, drift)
+        ctx.close()
+    a, b = states["fp32_bulk"], states["fp64"]
+    assert np.sum(np.abs(a - b)) / np.sum(np.abs(b)) <= 1e-5
+
+
+def config5_meshes():
+    rng = np.random.default_rng(5)
+    sizes = rng.choice(np.arange(16, 257, 8), size=48)
+    meshes = [synth.tri_mesh(int(n), jitter=0.2, seed=100 + k) for k, n in enumerate(sizes)]
+    u0 = [synth.smooth_random_initial(m, seed=200 + k) for k, m in enumerate(meshes)]
+    return meshes, u0
+
+
+def mesh_dts(meshes, inr, u0):
+    dts, off = [], 0
+    for m, u in zip(meshes, u0):
+        dts.append(0.3 * float(np.min(inr[off:off + m.n_cells])) / (math.sqrt(2.0) * float(np.max(np.abs(u)))))
+        off += m.n_cells
+    return dts
+
+
+def test_config5_batched_equals_separate_and_adjoint(dev):
+    from paper_1602_02694_gb300.autograd import rollout
+    meshes, u0s = config5_meshes()
+    N = sum(m.n_cells for m in meshes)
+    assert 500_000 <= N <= 3_500_000
+    ctx = Context(pde="burgers")
+    ctx.build_stencils(meshes, order_p=3, ring=1.0)
+    ctx.precompute_moments()
+    inr = ctx.geometry()["inradius"]
+    dts = mesh_dts(meshes, inr, u0s)
+    ctx.set_mesh_dt(dts)
+    u0 = torch.tensor(np.concatenate(u0s), device=dev)
+    # batched vs separate contexts (three of the problems), 5 steps
+    ub = u0.clone()
+    ctx.rk_step(ub, dt=-1.0, n_steps=5)
+    offs = np.concatenate([[0], np.cumsum([m.n_cells for m in meshes])])
+    for k in (0, 17, 47):
+        c1 = Context(pde="burgers")
+        c1.build_stencils(meshes[k], order_p=3, ring=1.0)
+        c1.precompute_moments()
+        c1.set_mesh_dt([dts[k]])
+        us = torch.tensor(u0s[k], device=dev)
+        c1.rk_step(us, dt=-1.0, n_steps=5)
+        assert torch.equal(us, ub[offs[k]:offs[k + 1]])
+        c1.close()
+    # adjoint with checkpoints vs central differences: 64 directions over a
+    # 5-step horizon, 8 directions over the full 50 steps
+    w = torch.tensor(synth.loss_weights(N, 3), device=dev)
+    dirs = synth.random_unit_directions(N, 64, 4)
+    for steps, every, ndir in ((5, 2, 64), (50, 7, 8)):
+        x = u0.clone().requires_grad_(True)
+        uT = rollout(ctx, x, steps, -1.0, checkpoint_every=every)
+        torch.sum(w * uT * uT).backward()
+        g = x.grad.detach()
+        gnorm = float(torch.linalg.norm(g))
+
+        def J(u):
+            v = u.clone()
+            ctx.rk_step(v, dt=-1.0, n_steps=steps)
+            return float(torch.sum(w * v * v))
+
+        h = 1e-6
+        worst = 0.0
+        for d in dirs[:ndir]:
+            v = torch.tensor(d, device=dev)
+            fd = (J(u0 + h * v) - J(u0 - h * v)) / (2 * h)
+            ad = float(torch.dot(g, v))
+            worst = max(worst, abs(fd - ad) / gnorm)
+        assert worst <= 1e-4, (steps, worst)
+    ctx.close()

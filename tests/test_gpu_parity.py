@@ -335,3 +335,25 @@ def test_full_size_sampled_parity(dev):
         scale = max(scale, abs(Li))
         assert abs(res["fp64"][1][i] - Li) <= TOL64 * max(1.0, abs(Li)), i
         assert abs(res["fp32_bulk"][1][i] - Li) <= 1e-5 * max(1.0, abs(Li)), i
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_graph_replayed_steps_equal_single_steps(dev, precision):
+    """n_steps > 1 replays one captured step as a CUDA graph; it must give the
+    bits of n separate one-step calls (CFL dt recomputed every step)."""
+    mesh, prob = case("tri10_p4_ring2", O.BURGERS)
+    ctx = Context(pde="burgers", precision=precision)
+    ctx.build_stencils(mesh, order_p=4, ring=2.0)
+    ctx.precompute_moments()
+    u0 = torch.tensor(synth.burgers_2d_initial(mesh), device=dev)
+    a = u0.clone()
+    ctx.rk_step(a, cfl=0.3, n_steps=6)
+    b = u0.clone()
+    for _ in range(6):
+        ctx.rk_step(b, cfl=0.3, n_steps=1)
+    assert torch.equal(a, b)
+    launches = ctx.diagnostics()["kernel_launches"]
+    c = u0.clone()
+    ctx.rk_step(c, cfl=0.3, n_steps=6)  # another array: the step is captured again
+    assert ctx.diagnostics()["kernel_launches"] > launches
+    ctx.close()
