@@ -548,6 +548,8 @@ def facet_flux(prob, coeffs, L, fL, R):
 def residual(prob, ubar, coeffs=None):
     """L(ubar)_i = -(1/|tau_i|) * sum over facets of the integrated numerical
     flux out of tau_i (Eq. (fvm), divided by |tau_i|)."""
+    if prob.pde == EULER:
+        return residual_euler(prob, ubar)
     if coeffs is None:
         coeffs = reconstruct_all(prob, ubar)
     flux_out = np.zeros(prob.N)
@@ -564,7 +566,109 @@ def max_wave_speed(prob, ubar):
         return float(np.linalg.norm(prob.velocity[:prob.dim]))
     if prob.pde == BURGERS:
         return math.sqrt(prob.dim) * float(np.max(np.abs(ubar)))
+    if prob.pde == EULER:
+        rho, vel, p = euler_primitive(np.asarray(ubar), prob.gamma)
+        return float(np.max(np.linalg.norm(vel, axis=0) + np.sqrt(prob.gamma * p / rho)))
     raise ValueError(prob.pde)
+
+
+# ----------------------------------------------------------------------------
+# compressible Euler, componentwise WLS-ENO (Sec. 5.2.3 and 5.2.4 use the 2-D
+# Euler equations; the reconstruction is applied to each conserved variable)
+# ----------------------------------------------------------------------------
+
+POSITIVITY_FLOOR = 1e-12
+
+
+def euler_primitive(U, gamma):
+    """Density, velocity [d][...] and pressure from conserved U = (rho, rho v, E)."""
+    rho = U[0]
+    vel = U[1:-1] / rho
+    p = (gamma - 1.0) * (U[-1] - 0.5 * rho * np.sum(vel * vel, axis=0))
+    return rho, vel, p
+
+
+def euler_normal_flux(U, n, gamma):
+    """F(U).n for conserved U (shape [d+2])."""
+    rho, vel, p = euler_primitive(np.asarray(U, dtype=np.float64), gamma)
+    un = float(np.dot(vel, n))
+    out = np.empty(len(U))
+    out[0] = rho * un
+    out[1:-1] = rho * un * vel + p * np.asarray(n)
+    out[-1] = (U[-1] + p) * un
+    return out
+
+
+def euler_wave_speed(U, n, gamma):
+    rho, vel, p = euler_primitive(np.asarray(U, dtype=np.float64), gamma)
+    return abs(float(np.dot(vel, n))) + math.sqrt(gamma * p / rho)
+
+
+def euler_coeffs(prob, ubar):
+    """Componentwise reconstructions: coeffs[c][i] (each with its own weights)."""
+    C = ubar.shape[0]
+    return [[prob.reconstruct_cell(ubar[c], i)[0] for i in range(prob.N)] for c in range(C)]
+
+
+def euler_positive(prob, ubar, coeffs):
+    """Reading of the positivity fallback (the paper is silent): a cell whose
+    traces give density or pressure <= 1e-12 at any facet quadrature point
+    uses its cell averages at all its facets."""
+    C = ubar.shape[0]
+    ok = np.ones(prob.N, dtype=bool)
+    for i in range(prob.N):
+        X = prob.geo.coords[i]
+        for f in range(prob.dim + 1):
+            pts, _ = facet_rule(np.delete(X, f, axis=0))
+            for x in pts:
+                U = np.array([prob.eval_poly(coeffs[c][i], i, x) for c in range(C)])
+                rho, _, p = euler_primitive(U, prob.gamma)
+                if not (rho > POSITIVITY_FLOOR and p > POSITIVITY_FLOOR):
+                    ok[i] = False
+    return ok
+
+
+def euler_traces(prob, ubar, coeffs, ok, c_cell, pts_in_cell_frame):
+    C = ubar.shape[0]
+    out = np.empty((len(pts_in_cell_frame), C))
+    for q, x in enumerate(pts_in_cell_frame):
+        for c in range(C):
+            out[q, c] = prob.eval_poly(coeffs[c][c_cell], c_cell, x) if ok[c_cell] else ubar[c, c_cell]
+    return out
+
+
+def residual_euler(prob, ubar):
+    """Componentwise WLS-ENO traces, LF flux with alpha = max over the facet's
+    points and sides of |u.n| + c (Eq. (flux)), FV residual per component."""
+    ubar = np.asarray(ubar, dtype=np.float64)
+    C = ubar.shape[0]
+    coeffs = euler_coeffs(prob, ubar)
+    ok = euler_positive(prob, ubar, coeffs)
+    flux_out = np.zeros((C, prob.N))
+    for L, fL, R in facets(prob):
+        X = prob.geo.coords[L]
+        F = np.delete(X, fL, axis=0)
+        pts, w = facet_rule(F)
+        area = facet_measure(F)
+        n = outward_normal(X, fL)
+        UL = euler_traces(prob, ubar, coeffs, ok, L, pts)
+        if R < 0:
+            UR = UL.copy()
+        else:
+            shift = min_image(prob.geo.centroid[R] - prob.geo.centroid[L], prob.period) - \
+                (prob.geo.centroid[R] - prob.geo.centroid[L])
+            UR = euler_traces(prob, ubar, coeffs, ok, R, [x - shift for x in pts])
+        alpha = max(max(euler_wave_speed(UL[q], n, prob.gamma), euler_wave_speed(UR[q], n, prob.gamma))
+                    for q in range(len(w)))
+        g = np.zeros(C)
+        for q in range(len(w)):
+            g += w[q] * 0.5 * (euler_normal_flux(UL[q], n, prob.gamma) + euler_normal_flux(UR[q], n, prob.gamma)
+                               - alpha * (UR[q] - UL[q]))
+        g *= area
+        flux_out[:, L] += g
+        if R >= 0:
+            flux_out[:, R] -= g
+    return -flux_out / prob.geo.volume[None, :]
 
 
 def cfl_dt(prob, ubar, cfl):

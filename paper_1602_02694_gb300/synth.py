@@ -284,6 +284,46 @@ def gaussian_ball_3d_initial(mesh: Mesh, sub: int = 2) -> np.ndarray:
     return smooth + ind @ wq
 
 
+def quadrant_fractions(mesh: Mesh, x0: float = 0.5, y0: float = 0.5) -> np.ndarray:
+    """Exact area fraction of each triangle in the four quadrants around
+    (x0, y0), ordered (x<x0,y<y0), (x>x0,y<y0), (x<x0,y>y0), (x>x0,y>y0);
+    only cells straddling x = x0 or y = y0 are clipped."""
+    X = mesh.cell_coords
+    lo = X.min(axis=1)
+    hi = X.max(axis=1)
+    qx = (lo[:, 0] >= x0).astype(int)
+    qy = (lo[:, 1] >= y0).astype(int)
+    out = np.zeros((mesh.n_cells, 4))
+    out[np.arange(mesh.n_cells), qx + 2 * qy] = 1.0
+    straddle = np.nonzero((lo[:, 0] < x0) & (hi[:, 0] > x0) | (lo[:, 1] < y0) & (hi[:, 1] > y0))[0]
+    big = 1e9
+    boxes = [((-big, -big), (x0, y0)), ((x0, -big), (big, y0)), ((-big, y0), (x0, big)), ((x0, y0), (big, big))]
+    for c in straddle:
+        tri = [np.asarray(p) for p in X[c]]
+        area = _polygon_area(tri)
+        for k, (blo, bhi) in enumerate(boxes):
+            poly = tri
+            for axis in range(2):
+                poly = _clip_polygon(poly, axis, blo[axis], True) if poly else poly
+                poly = _clip_polygon(poly, axis, bhi[axis], False) if poly else poly
+            out[c, k] = _polygon_area(poly) / area if poly else 0.0
+    return out
+
+
+def euler_quadrant_initial(mesh: Mesh, seed: int, gamma: float = 1.4):
+    """Four piecewise-constant states around (1/2, 1/2): density U[0.1, 1.5],
+    velocity components U[-0.8, 0.8], pressure U[0.03, 1.5], drawn per
+    quadrant from ``default_rng(seed)``.  Returns conserved cell averages
+    [4][n_cells] (rho, rho u, rho v, E) and the primitive states [4][4]."""
+    rng = np.random.default_rng(seed)
+    prim = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-0.8, 0.8, 4), rng.uniform(-0.8, 0.8, 4),
+                     rng.uniform(0.03, 1.5, 4)], axis=1)  # [quadrant][rho, u, v, p]
+    rho, u, v, p = prim.T
+    cons = np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)], axis=0)
+    frac = quadrant_fractions(mesh)
+    return cons @ frac.T, prim
+
+
 def random_unit_directions(n_cells: int, count: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     d = rng.normal(size=(count, n_cells))

@@ -1,0 +1,80 @@
+"""Pins of the oracle's componentwise Euler path: properties the Euler
+equations and the Lax-Friedrichs flux fix (rotational invariance of the
+normal flux, consistency on constant states, exact conservation, the
+quadrant initial data), and the positivity fallback."""
+import math
+
+import numpy as np
+
+from oracle import wlseno_oracle as O
+from paper_1602_02694_gb300 import synth
+
+GAMMA = 1.4
+
+
+def cons(rho, u, v, p):
+    return np.array([rho, rho * u, rho * v, p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def test_normal_flux_rotational_invariance():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho, p = rng.uniform(0.2, 2.0, 2)
+        u, v = rng.uniform(-1, 1, 2)
+        th = rng.uniform(0, 2 * math.pi)
+        Rm = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        n = np.array([math.cos(0.3), math.sin(0.3)])
+        F = O.euler_normal_flux(cons(rho, u, v, p), n, GAMMA)
+        ur, vr = Rm @ np.array([u, v])
+        Fr = O.euler_normal_flux(cons(rho, ur, vr, p), Rm @ n, GAMMA)
+        assert abs(Fr[0] - F[0]) < 1e-13 and abs(Fr[3] - F[3]) < 1e-13
+        assert np.allclose(Fr[1:3], Rm @ F[1:3], atol=1e-13)
+        # a state at rest only pushes with its pressure
+        F0 = O.euler_normal_flux(cons(rho, 0.0, 0.0, p), n, GAMMA)
+        assert np.allclose(F0, [0.0, p * n[0], p * n[1], 0.0], atol=1e-15)
+
+
+def test_constant_state_and_conservation():
+    mesh = synth.tri_mesh(6, seed=7)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER)
+    U = np.repeat(cons(0.8, 0.3, -0.2, 0.9)[:, None], prob.N, axis=1)
+    L = O.residual(prob, U)
+    assert np.max(np.abs(L)) < 1e-11
+    rng = np.random.default_rng(3)
+    U = np.stack([cons(rng.uniform(0.5, 1.5), rng.uniform(-.5, .5), rng.uniform(-.5, .5), rng.uniform(0.5, 1.5))
+                  for _ in range(prob.N)], axis=1)
+    L = O.residual(prob, U)
+    vol = prob.geo.volume
+    for c in range(4):
+        assert abs(np.sum(vol * L[c])) < 1e-13 * np.sum(vol * np.abs(L[c]))
+
+
+def test_quadrant_initial_data_is_exact():
+    mesh = synth.tri_mesh(16, periodic=False, seed=2)
+    U, prim = synth.euler_quadrant_initial(mesh, seed=3)
+    vol = np.abs(np.linalg.det(mesh.cell_coords[:, 1:] - mesh.cell_coords[:, :1])) / 2
+    # every quadrant has area 1/4: the total of each conserved variable is exact
+    rho, u, v, p = prim.T
+    E = p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)
+    for c, q in enumerate([rho, rho * u, rho * v, E]):
+        assert abs(np.sum(vol * U[c]) - 0.25 * np.sum(q)) < 1e-13
+    assert np.all((0.1 <= prim[:, 0]) & (prim[:, 0] <= 1.5) & (prim[:, 3] >= 0.03))
+
+
+def test_positivity_fallback_uses_cell_averages():
+    mesh = synth.tri_mesh(6, periodic=False, seed=4)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, min_rows=9)
+    # unit density, momentum 2x (linear: reconstructed exactly), energy flat
+    # at 1/2 m_i^2 + 1e-4: the pressure is 4e-5 at cell i's average but goes
+    # negative at the facet points where |m| exceeds m_i
+    i = 20
+    U = np.zeros((4, prob.N))
+    U[0] = 1.0
+    U[1] = 2.0 * prob.geo.centroid[:, 0]
+    U[3] = 0.5 * U[1, i] ** 2 + 1e-4
+    coeffs = O.euler_coeffs(prob, U)
+    ok = O.euler_positive(prob, U, coeffs)
+    assert not ok[i]
+    X = prob.geo.coords[i]
+    tr = O.euler_traces(prob, U, coeffs, ok, i, list(X))
+    assert np.allclose(tr, np.repeat(U[:, i][None, :], len(X), axis=0))
