@@ -92,8 +92,10 @@ typedef struct {
 } wlseno_stencil_opts;
 
 /* Scheme parameters.
- * pde:        WLSENO_ADVECTION (F = a u), WLSENO_BURGERS (F = u^2/2 (1,..,1)).
- * n_comp:     number of conserved components (1 for the scalar equations).
+ * pde:        WLSENO_ADVECTION (F = a u), WLSENO_BURGERS (F = u^2/2 (1,..,1)),
+ *             WLSENO_EULER (2-D compressible Euler, see below).
+ * n_comp:     number of conserved components (1 for the scalar equations,
+ *             4 for 2-D Euler).
  * velocity:   advection velocity a (first dim entries used).
  * eps:        epsilon of the non-smoothness indicator, Eq. (smoothness
  *             indicator), e.g. 1e-2; h is the centre cell's mean edge length.
@@ -102,7 +104,14 @@ typedef struct {
  * kappa_flag: FP32-bulk mode: cells whose |R_11|/|R_rr| exceeds this get one
  *             FP64-residual refinement sweep (e.g. 1e3).
  * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and flux
- *             in FP32; moments, residual accumulation and RK update in FP64). */
+ *             in FP32; moments, residual accumulation and RK update in FP64).
+ * gamma:      WLSENO_EULER only: ratio of specific heats (e.g. 1.4).
+ *
+ * WLSENO_EULER (2-D): n_comp = 4 conserved variables (rho, rho u, rho v, E),
+ * each reconstructed with its own weights (componentwise WLS-ENO); LF alpha
+ * per facet = max over its points and sides of |u.n| + c; a cell whose traces
+ * give density or pressure <= 1e-12 at a facet point uses its averages at all
+ * its facets (counted in wlseno_diagnostics.positivity_fallbacks). */
 typedef struct {
   int pde;
   int n_comp;
@@ -112,6 +121,7 @@ typedef struct {
   double rank_tol;
   double kappa_flag;
   int precision;
+  double gamma;
 } wlseno_scheme;
 
 typedef struct {
@@ -144,6 +154,7 @@ typedef struct {
                                                       each kind since
                                                       wlseno_set_timing (timing
                                                       mode only)                */
+  int64_t positivity_fallbacks; /* Euler cells on first order (last call)      */
 } wlseno_diagnostics;
 
 /* Create a context on CUDA device `device`; copies *scheme.

@@ -234,6 +234,37 @@ cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, cons
   return e;
 }
 
+// One RK stage (or the residual) over all components: out = a u0 + b (u + dt
+// L(u)), or L(u) itself.  Euler reconstructs every component, applies the
+// positivity fix-up and runs the coupled flux; scalar equations go component
+// by component.
+cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double a, double b,
+                      bool residual_only, double* out, cudaStream_t s) {
+  const int64_t N = ctx->dm.N;
+  const int C = ctx->scheme.n_comp;
+  const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
+  cudaError_t e = cudaSuccess;
+  if (ctx->scheme.pde == WLSENO_EULER) {
+    for (int c = 0; c < C && e == cudaSuccess; ++c)
+      e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals + c * N * NP, s);
+    if (e != cudaSuccess) return e;
+    KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
+    e = launch_euler_positivity(ctx->dm, ctx->sp.gamma, u, ctx->d_fvals, ctx->d_counters, s);
+    if (e == cudaSuccess)
+      e = launch_euler_flux_stage(ctx->dm, ctx->sp.gamma, ctx->scheme.precision, ctx->d_fvals, u, u0,
+                                  a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s);
+    scope.done(e == cudaSuccess ? 2 : 0);
+    return e;
+  }
+  for (int c = 0; c < C && e == cudaSuccess; ++c) {
+    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s);
+    if (e == cudaSuccess)
+      e = flux_one(ctx, ctx->d_fvals, u + c * N, u0 ? u0 + c * N : nullptr, a, b, residual_only,
+                   out + c * N, s);
+  }
+  return e;
+}
+
 wlseno_status check_ready(wlseno_ctx* ctx) {
   if (!ctx) return WLSENO_ERR_INVALID_ARG;
   if (!ctx->built || !ctx->moments_ready)
@@ -299,9 +330,10 @@ const char* wlseno_last_error_message(const wlseno_ctx* ctx) {
 wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* scheme) {
   if (!out || !scheme) return WLSENO_ERR_INVALID_ARG;
   *out = nullptr;
-  if (scheme->pde != WLSENO_ADVECTION && scheme->pde != WLSENO_BURGERS)
+  if (scheme->pde != WLSENO_ADVECTION && scheme->pde != WLSENO_BURGERS && scheme->pde != WLSENO_EULER)
     return WLSENO_ERR_INVALID_ARG;
-  if (scheme->n_comp != 1) return WLSENO_ERR_INVALID_ARG;
+  if (scheme->pde == WLSENO_EULER ? scheme->n_comp != 4 || !(scheme->gamma > 1.0) : scheme->n_comp != 1)
+    return WLSENO_ERR_INVALID_ARG;
   if (scheme->precision != WLSENO_FP64 && scheme->precision != WLSENO_FP32_BULK)
     return WLSENO_ERR_INVALID_ARG;
   if (!(scheme->eps > 0.0) || !(scheme->alpha_c > 0.0) || !(scheme->rank_tol >= 0.0))
@@ -321,6 +353,7 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   ctx->sp.alpha_c = scheme->alpha_c;
   ctx->sp.rank_tol = scheme->rank_tol;
   ctx->sp.kappa_flag = scheme->kappa_flag > 0.0 ? scheme->kappa_flag : 1e3;
+  ctx->sp.gamma = scheme->gamma;
   *out = ctx;
   return WLSENO_OK;
 }
@@ -351,6 +384,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   HostSetup& H = ctx->host;
   wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err);
   if (st != WLSENO_OK) return fail(ctx, st, err);
+  if (ctx->scheme.pde == WLSENO_EULER && H.dim != 2)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "the Euler path is built for 2-D meshes");
   if ((H.dim == 2 && H.m != 6 && H.m != 10) || (H.dim == 3 && H.m != 10))
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "order p not compiled for this dimension");
   int G = opts->lanes_per_cell, R = opts->rows_per_lane;
@@ -405,7 +440,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   const int NP = (H.dim + 1) * H.nq;
   if ((st = dalloc(ctx, &dm.A64, H.nnz * H.m)) || (st = dalloc(ctx, &dm.A32, H.nnz * H.m)) ||
       (st = dalloc(ctx, &ctx->d_dt, H.n_meshes)) || (st = dalloc(ctx, &ctx->d_lmax, H.n_meshes)) ||
-      (st = dalloc(ctx, &ctx->d_counters, 4)) || (st = dalloc(ctx, &ctx->d_fvals, N * NP)) ||
+      (st = dalloc(ctx, &ctx->d_counters, 4)) || (st = dalloc(ctx, &ctx->d_fvals, C * N * NP)) ||
       (st = dalloc(ctx, &ctx->d_k1, C * N)) || (st = dalloc(ctx, &ctx->d_k2, C * N)))
     return st;
   dm.nmax = H.max_n;
@@ -508,12 +543,8 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
   double* res = out_host ? ctx->d_out : residual;
   if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
-  for (int c = 0; c < C; ++c) {
-    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruction kernel");
-    e = flux_one(ctx, ctx->d_fvals, u + c * N, nullptr, 0.0, 1.0, true, res + c * N, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "flux kernel");
-  }
+  if ((e = stage_all(ctx, u, nullptr, 0.0, 1.0, true, res, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "residual kernels");
   if (out_host) {
     e = cudaMemcpyAsync(residual, ctx->d_out, sizeof(double) * C * N, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy residual");
@@ -560,19 +591,13 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       scope.done(nl);
       if (err != cudaSuccess) return err;
     }
-    for (int c = 0; c < C; ++c) {
-      double* u0 = u + c * N;
-      double* k1 = ctx->d_k1 + c * N;
-      double* k2 = ctx->d_k2 + c * N;
-      // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
-      if ((err = reconstruct_one(ctx, u0, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
-          (err = flux_one(ctx, ctx->d_fvals, u0, u0, 0.0, 1.0, false, k1, st)) != cudaSuccess ||
-          (err = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
-          (err = flux_one(ctx, ctx->d_fvals, k1, u0, 0.75, 0.25, false, k2, st)) != cudaSuccess ||
-          (err = reconstruct_one(ctx, k2, nullptr, ctx->d_fvals, st)) != cudaSuccess ||
-          (err = flux_one(ctx, ctx->d_fvals, k2, u0, 1.0 / 3.0, 2.0 / 3.0, false, u0, st)) != cudaSuccess)
-        return err;
-    }
+    // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
+    double* k1 = ctx->d_k1;
+    double* k2 = ctx->d_k2;
+    if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st)) != cudaSuccess ||
+        (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st)) != cudaSuccess ||
+        (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st)) != cudaSuccess)
+      return err;
     return cudaSuccess;
   };
   // Several steps: capture one step as a CUDA graph (on the context's own
@@ -727,6 +752,8 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   if (st != WLSENO_OK) return st;
   if (!ubar_n || !gbar_next || !gbar_n) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null array");
   if (dt == 0.0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint needs a fixed dt (> 0, or < 0 for per-mesh steps)");
+  if (ctx->scheme.pde == WLSENO_EULER)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for the scalar equations");
   if (dt < 0.0 && !ctx->mesh_dt_set)
     return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
   DeviceGuard guard(ctx->device);
@@ -879,6 +906,7 @@ wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out) {
   out->flagged_cells = static_cast<int64_t>(c[0]);
   out->rank_deficient = static_cast<int64_t>(c[1]);
   out->nonfinite = static_cast<int64_t>(c[2]);
+  out->positivity_fallbacks = static_cast<int64_t>(c[3]);
   for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) out->launches_by_kind[k] = ctx->by_kind[k];
   for (const auto& t : ctx->timed) {
     float ms = 0.0f;

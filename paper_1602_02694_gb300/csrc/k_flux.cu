@@ -177,6 +177,7 @@ __global__ void cfl_dt_kernel(int n_meshes, int pde, int dim, double adv_speed,
   }
   double lam = adv_speed;
   if (pde == WLSENO_BURGERS) lam = sqrt(static_cast<double>(dim)) * __longlong_as_double(static_cast<long long>(lmax_bits[k]));
+  if (pde == WLSENO_EULER) lam = __longlong_as_double(static_cast<long long>(lmax_bits[k]));  // max |u| + c
   dt_mesh[k] = lam > 0.0 ? cfl * rmin[k] / lam : 0.0;
 }
 
@@ -217,6 +218,10 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
     const int threads = 256;
     const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
     max_abs_kernel<<<blocks, threads, 0, s>>>(dm.N, u, dm.mesh_of, lmax_bits);
+    ++*launches;
+  } else if (dt_fixed <= 0.0 && sp.pde == WLSENO_EULER) {
+    cudaError_t e = launch_euler_speed(dm, sp.gamma, u, lmax_bits, n_meshes, s);
+    if (e != cudaSuccess) return e;
     ++*launches;
   }
   cfl_dt_kernel<<<(n_meshes + 127) / 128, 128, 0, s>>>(n_meshes, sp.pde, dm.dim, speed, lmax_bits,

@@ -58,6 +58,10 @@ extern "C" wlseno_status wlseno_flux_residual_static(wlseno_ctx* ctx, const doub
                                                      double* residual, void* stream) {
   CtxView v;
   if (!ctx || !ctx_view(ctx, &v)) return WLSENO_ERR_INVALID_ARG;
+  if (v.sp.pde == WLSENO_EULER) {
+    ctx_set_error(ctx, "wlseno_flux_residual_static covers the scalar equations");
+    return WLSENO_ERR_INVALID_ARG;
+  }
   if (!v.ready) {
     ctx_set_error(ctx, "call wlseno_build_stencils and wlseno_precompute_moments first");
     return WLSENO_ERR_STATE;

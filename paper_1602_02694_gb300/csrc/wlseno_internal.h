@@ -77,7 +77,18 @@ struct SchemeParams {
   int pde;
   double vel[3];
   double eps, alpha_c, rank_tol, kappa_flag;
+  double gamma;             // Euler: ratio of specific heats
 };
+
+// Euler (k_euler.cu): fvals/u/out are [4][N]-major per component.
+cudaError_t launch_euler_positivity(const DeviceMesh& dm, double gamma, const double* ubar,
+                                    double* fvals, unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_euler_flux_stage(const DeviceMesh& dm, double gamma, int precision,
+                                    const double* fvals, const double* u, const double* u0,
+                                    double a, double b, const double* dt_mesh, bool residual_only,
+                                    double* out, unsigned long long* counters, cudaStream_t s);
+cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
+                               unsigned long long* lmax_bits, int n_meshes, cudaStream_t s);
 
 struct ReconOut {
   double* coeffs;           // [N][m] or null

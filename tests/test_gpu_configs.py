@@ -181,3 +181,58 @@ def test_config5_batched_equals_separate_and_adjoint(dev):
             worst = max(worst, abs(fd - ad) / gnorm)
         assert worst <= 1e-4, (steps, worst)
     ctx.close()
+
+
+def euler_problem(n, seed=3):
+    mesh = synth.tri_mesh(n, jitter=0.2, seed=1, periodic=False)
+    U, _ = synth.euler_quadrant_initial(mesh, seed=seed)
+    return mesh, U
+
+
+def test_euler_parity_small(dev):
+    """2-D Euler, four-quadrant states, transmissive 12x12 mesh, p = 3:
+    residual, positivity decisions and two CFL-0.3 steps against the oracle."""
+    mesh, U = euler_problem(12)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, min_rows=9)
+    ctx = Context(pde="euler")
+    ctx.build_stencils(mesh, order_p=3, ring=1.0, min_rows=9)
+    ctx.precompute_moments()
+    u = torch.tensor(U, device=dev).contiguous()
+    L = torch.empty_like(u)
+    ctx.flux_residual(u, L)
+    ref = O.residual(prob, U)
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    assert float(np.max(np.abs(L.cpu().numpy() - ref))) <= TOL64 * scale
+    ok = O.euler_positive(prob, U, O.euler_coeffs(prob, U))
+    assert ctx.diagnostics()["positivity_fallbacks"] == int(np.sum(~ok))
+    ref2, dts = O.rk3_run(prob, U, 2, cfl=0.3)
+    dt = None
+    for _ in range(2):
+        dt = ctx.rk_step(u, cfl=0.3, n_steps=1, want_dt=True)
+    assert abs(dt - dts[-1]) <= 1e-14 * dt
+    assert float(np.max(np.abs(u.cpu().numpy() - ref2))) <= TOL64
+    ctx.close()
+
+
+def test_euler_config3_full_size(dev):
+    """The 1024x1024 transmissive mesh (2,097,152 triangles): 3 CFL-0.3 steps
+    in FP64 and FP32-bulk; finite, positive, and FP32-bulk within 1e-5."""
+    mesh, U = euler_problem(1024)
+    assert mesh.n_cells == 2097152
+    out = {}
+    for precision in ("fp64", "fp32_bulk"):
+        ctx = Context(pde="euler", precision=precision)
+        ctx.build_stencils(mesh, order_p=3, ring=1.0)
+        ctx.precompute_moments()
+        u = torch.tensor(U, device=dev).contiguous()
+        ctx.rk_step(u, cfl=0.3, n_steps=3)
+        d = ctx.diagnostics()
+        assert d["nonfinite"] == 0
+        a = u.cpu().numpy()
+        rho = a[0]
+        p = 0.4 * (a[3] - 0.5 * (a[1] ** 2 + a[2] ** 2) / rho)
+        assert np.all(rho > 0) and np.all(p > 0)
+        out[precision] = a
+        ctx.close()
+    a, b = out["fp32_bulk"], out["fp64"]
+    assert np.sum(np.abs(a - b)) / np.sum(np.abs(b)) <= 1e-5
