@@ -445,8 +445,9 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
     return st;
   dm.nmax = H.max_n;
   const size_t ell = static_cast<size_t>(H.max_n) * N;
+  dm.rec_width = rec32_width(H.m);
   if ((st = dalloc(ctx, &dm.st_ell, ell)) || (st = dalloc(ctx, &dm.A64e, ell * H.m)) ||
-      (st = dalloc(ctx, &dm.A32e, ell * H.m)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
+      (st = dalloc(ctx, &dm.rec32, ell * dm.rec_width)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
       (st = dalloc(ctx, &ctx->d_wl_count, 1)))
     return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));

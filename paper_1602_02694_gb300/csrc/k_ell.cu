@@ -1,6 +1,13 @@
-// Copies the CSR stencils and moment rows into the ELL layout of the
-// thread-per-cell kernel (row t of cell i at t*N + i), once after the
-// moment precompute.
+// Copies the CSR stencils and moment rows, once after the moment precompute,
+// into the layouts of the thread-per-cell kernels:
+//  * ELL (FP64 kernel, adjoint): row t of cell i at t*N + i, column c of it at
+//    (t*m + c)*N + i, so a warp's loads of one column are coalesced;
+//  * FP32 row records (staged FP32 kernel): record (t, i) at (t*N + i)*W
+//    floats, W = round_up(m + 1, 4): the m moments, the stencil index as int32
+//    bits, zeros.  A warp's records are one contiguous 16-byte-aligned span,
+//    moved into shared memory by 16-byte asynchronous copies.
+// Rows past a cell's stencil (t >= n) point at the cell itself with zero
+// moments; the kernels never read them.
 #include "wlseno_internal.h"
 
 namespace wlseno {
@@ -11,17 +18,22 @@ __global__ void ell_copy_kernel(DeviceMesh dm) {
   if (i >= dm.N) return;
   const int64_t N = dm.N;
   const int m = dm.m;
+  const int W = dm.rec_width;
   const int beg = dm.st_ptr[i];
   const int n = dm.st_ptr[i + 1] - beg;
   for (int t = 0; t < dm.nmax; ++t) {
     const bool in = t < n;
-    dm.st_ell[t * N + i] = in ? dm.st_idx[beg + t] : static_cast<int32_t>(i);
+    const int32_t j = in ? dm.st_idx[beg + t] : static_cast<int32_t>(i);
+    dm.st_ell[t * N + i] = j;
+    float* rec = dm.rec32 + (static_cast<int64_t>(t) * N + i) * W;
     for (int c = 0; c < m; ++c) {
       const int64_t src = static_cast<int64_t>(beg + t) * m + c;
       const int64_t dst = (static_cast<int64_t>(t) * m + c) * N + i;
       dm.A64e[dst] = in ? dm.A64[src] : 0.0;
-      dm.A32e[dst] = in ? dm.A32[src] : 0.0f;
+      rec[c] = in ? dm.A32[src] : 0.0f;
     }
+    rec[m] = __int_as_float(j);
+    for (int c = m + 1; c < W; ++c) rec[c] = 0.0f;
   }
 }
 

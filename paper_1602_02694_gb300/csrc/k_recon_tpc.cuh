@@ -153,12 +153,9 @@ __device__ __forceinline__ void small_qr_solve(SmallQR<T, M>& q, T tau_piv, T ra
   (small_backsub_step<M - 1 - Ks, T, M>(q), ...);
 }
 
+// ELL moments of the FP64 kernel (the FP32 kernel reads row records).
 template <typename T>
-__device__ __forceinline__ const T* ell_moments(const DeviceMesh& dm);
-template <>
-__device__ __forceinline__ const float* ell_moments<float>(const DeviceMesh& dm) { return dm.A32e; }
-template <>
-__device__ __forceinline__ const double* ell_moments<double>(const DeviceMesh& dm) { return dm.A64e; }
+__device__ __forceinline__ const T* ell_moments(const DeviceMesh& dm) { return dm.A64e; }
 
 template <typename T>
 __device__ __forceinline__ const T* tpc_points(const DeviceMesh& dm);

@@ -55,6 +55,94 @@ __device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* __r
   }
 }
 
+constexpr int kTpcThreads = 128;  // block size of the thread-per-cell kernels
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
+}
+
+// FP32 fold with the rows staged through shared memory.  Each thread copies
+// its own rows asynchronously: the row record (moments + stencil index) four
+// rows ahead, and ubar_j two rows ahead (its index read from the staged
+// record), so neither the HBM latency of the records nor the record -> index
+// -> ubar chain stalls the rotations, and no prefetched row occupies
+// registers.  Commit groups: one per iteration t, holding ubar of row t+2 and
+// the record of row t+4; waiting for all but the newest group therefore
+// guarantees the record and ubar of row t and the record of row t+2.  Record
+// slots cycle mod 5 and ubar slots mod 3, so a copy never lands in a slot
+// whose previous row is still to be read.  Threads touch only their own
+// slots: no block barrier.
+template <int DIM, int M>
+__device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const double* __restrict__ ubar,
+                                                int64_t i, double ui, int n, float eh2, float w_centre,
+                                                float (&R)[M][M + 1]) {
+  constexpr int W4 = rec32_width(M) / 4;
+  constexpr int kRec = 5, kU = 3;
+  __shared__ float4 srec[kRec][W4][kTpcThreads];
+  __shared__ double su[kU][kTpcThreads];
+  const int tid = threadIdx.x;
+  const int64_t N = dm.N;
+  const float4* rec = reinterpret_cast<const float4*>(dm.rec32);
+  auto fetch_rec = [&](int t, int slot) {
+    const float4* src = rec + (static_cast<int64_t>(t) * N + i) * W4;
+#pragma unroll
+    for (int k = 0; k < W4; ++k) cp_async16(&srec[slot][k][tid], src + k);
+  };
+  auto fetch_u = [&](int rec_slot, int u_slot) {
+    const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][tid])[M % 4]);
+    cp_async8(&su[u_slot][tid], ubar + j);
+  };
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+#pragma unroll
+    for (int j = k; j <= M; ++j) R[k][j] = 0.0f;
+  for (int t = 0; t < 4 && t < n; ++t) fetch_rec(t, t);
+  cp_async_commit();
+  cp_async_wait<0>();
+  for (int t = 0; t < 2 && t < n; ++t) fetch_u(t, t);
+  cp_async_commit();
+  cp_async_commit();  // empty: the first wait below then covers the ubar copies
+  int sr = 0, sv = 0;  // slots of row t
+  for (int t = 0; t < n; ++t) {
+    cp_async_wait<1>();
+    float a[M + 1];
+#pragma unroll
+    for (int k = 0; k < W4; ++k) {
+      const float4 v = srec[sr][k][tid];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * k + q < M) a[4 * k + q] = vv[q];
+    }
+    const double uj = su[sv][tid];
+    const int sr2 = sr + 2 < kRec ? sr + 2 : sr + 2 - kRec;
+    const int sr4 = sr + 4 < kRec ? sr + 4 : sr + 4 - kRec;
+    const int sv2 = sv + 2 < kU ? sv + 2 : sv + 2 - kU;
+    if (t + 2 < n) fetch_u(sr2, sv2);
+    if (t + 4 < n) fetch_rec(t + 4, sr4);
+    cp_async_commit();
+    const float dev = static_cast<float>(uj - ui);
+    const float w = t == 0 ? w_centre : eh2 / (dev * dev + eh2);
+#pragma unroll
+    for (int c = 0; c < M; ++c) a[c] *= w;
+    a[M] = w * dev;
+    givens_fold<float, M>(R, a);
+    sr = sr + 1 < kRec ? sr + 1 : 0;
+    sv = sv + 1 < kU ? sv + 1 : 0;
+  }
+  cp_async_wait<0>();
+}
+
 // Column scaling from R's column norms and the pivoted QR of R S.
 template <typename T, int M>
 __device__ __forceinline__ void tpc_pivoted(const T (&R)[M][M + 1], T rank_tol, SmallQR<T, M>& q) {
@@ -123,7 +211,10 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   T eh2, wc;
   tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
   T R[M][M + 1];
-  tpc_fold<T, DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
+  if constexpr (sizeof(T) == 4)
+    tpc_fold_staged<DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
+  else
+    tpc_fold<T, DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
   // conditioning estimate of W A S from its scaled diagonal
   T dmax = T(0), dmin = T(INFINITY);
 #pragma unroll
@@ -159,7 +250,7 @@ template <typename T, int DIM, int M>
 cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
                              const ReconOut& out, int* worklist, int* wl_count, cudaStream_t s,
                              int* launches) {
-  constexpr int threads = 128;
+  constexpr int threads = kTpcThreads;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   // FP32-bulk: refine above kappa_flag; FP64: take the pivoted path above 1e6
   const T threshold = sizeof(T) == 4 ? static_cast<T>(sp.kappa_flag) : T(1e6);

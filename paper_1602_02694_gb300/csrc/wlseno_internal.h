@@ -70,8 +70,15 @@ struct DeviceMesh {
   int nmax;                 // largest stencil
   int32_t* st_ell;          // [nmax][N]
   double* A64e;             // [nmax][m][N]
-  float* A32e;              // [nmax][m][N]
+  // FP32 row records of the staged thread-per-cell kernel: record (t, i) at
+  // (t*N + i)*rec_width floats holds the m moments of row t of cell i, then
+  // the stencil index (int32 bits), then zero padding to a 16-byte multiple
+  float* rec32;             // [nmax][N][rec_width]
+  int rec_width;            // round_up(m + 1, 4)
 };
+
+// Width in floats of one FP32 row record (moments + index, 16-byte padded).
+__host__ __device__ constexpr int rec32_width(int m) { return (m + 1 + 3) / 4 * 4; }
 
 struct SchemeParams {
   int pde;
