@@ -130,16 +130,10 @@ adj_recon_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
     }
   }
   const double wc = sp.alpha_c * e / bmin;
-  double R[M][M + 1];
-  tpc_fold<double, DIM, M>(dm, ubar, c, uc, n, e, wc, R);
+  SqrtFreeQR<double, M> f;  // W A = Q D^(1/2) U
+  tpc_fold<DIM, M>(dm, ubar, c, uc, n, e, wc, f);
   double d[M];
-#pragma unroll
-  for (int k = M - 1; k >= 0; --k) {
-    double t = R[k][M];
-#pragma unroll
-    for (int q = k + 1; q < M; ++q) t -= R[k][q] * d[q];
-    d[k] = R[k][k] != 0.0 ? t / R[k][k] : 0.0;
-  }
+  sqrt_free_solve(f, d);
   // dbar from the facet-trace cotangents
   double dbar[M];
 #pragma unroll
@@ -158,21 +152,23 @@ adj_recon_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
 #pragma unroll
     for (int k = 0; k < M; ++k) dbar[k] += g * mono[k];
   }
-  // lambda = (R^T R)^-1 dbar
+  // lambda = (R^T R)^-1 dbar = U^-1 D^-1 U^-T dbar
   double v[M], lam[M];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     double t = dbar[k];
 #pragma unroll
-    for (int q = 0; q < k; ++q) t -= R[q][k] * v[q];
-    v[k] = R[k][k] != 0.0 ? t / R[k][k] : 0.0;
+    for (int q = 0; q < k; ++q) t = fma(-f.U[q][k], v[q], t);
+    v[k] = t;
   }
+#pragma unroll
+  for (int k = 0; k < M; ++k) v[k] /= f.d[k];
 #pragma unroll
   for (int k = M - 1; k >= 0; --k) {
     double t = v[k];
 #pragma unroll
-    for (int q = k + 1; q < M; ++q) t -= R[k][q] * lam[q];
-    lam[k] = R[k][k] != 0.0 ? t / R[k][k] : 0.0;
+    for (int q = k + 1; q < M; ++q) t = fma(-f.U[k][q], lam[q], t);
+    lam[k] = t;
   }
   double self = direct;
   double aval = 0.0;

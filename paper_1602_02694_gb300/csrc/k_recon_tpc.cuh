@@ -1,23 +1,31 @@
 // WLS-ENO reconstruction, one thread per cell (Sec. 3.1.2, Sec. 3.2,
-// Sec. 3.3.2).
+// Sec. 3.3.2): the row fold and its helpers.
 //
-// The thread streams its stencil rows a_j = w_j [A_j | ubar_j - ubar_i] from
-// an ELL layout (row t of every cell contiguous across cells, so a warp's
-// loads are coalesced) and folds each into an m x m upper-triangular factor R
-// (plus the transformed right-hand side) with Givens rotations: W A = Q R.
-// Column norms of W A equal those of R, so S = diag(1/||col R||) and the
-// paper's QR with column pivoting of W A S is the pivoted QR of the small
-// R S: W A S E = Q (R S E) = Q Q2 R2.  The pivots, R2 and hence the numerical
-// rank and the basic solution are those of W A S E = Q R (Sec. 3.3.2); only
-// the order of the orthogonal transformations differs.  Everything lives in
-// registers: no shuffles, no shared memory.
+// The weighted least-squares problem of cell i is min sum_t delta_t
+// (x_t . d - b_t)^2 over its stencil rows, with x_t the moment row of cell t
+// (Sec. 3.2), b_t = ubar_t - ubar_i and delta_t = w_t^2 the squared weight of
+// Sec. 3.1.2 -- the problem whose rows are w_t [x_t | b_t].  The thread folds
+// its rows one at a time into the triangular factor of W A = Q R by Givens
+// rotations in the square-root-free form of Gentleman (1973, "Least squares
+// computations by Givens transformations without square roots"; Applied
+// Statistics algorithm AS 75): R = D^(1/2) U with U unit upper triangular and
+// D = diag(d_k), so an incoming row (z, delta) updates, for k = 0..m-1,
 //
-// FP32-bulk: the weights, W A, the factorisations and the polynomial run in
-// FP32; ubar_j - ubar_i and ubar_i + deviation in FP64.  Cells whose
-// |R2_00| / |R2_rr| exceeds kappa_flag are appended to a work list; a second
-// kernel recomputes them and applies one corrected-seminormal-equations
-// refinement, y += (R2^T R2)^-1 (B E)^T (b - B y), with the residual and
-// B^T r formed in FP64 from the FP64 weights and moments.
+//   d_k' = d_k + delta z_k^2,   cbar = d_k / d_k',   sbar = delta z_k / d_k',
+//   z_j <- z_j - z_k u_kj,       u_kj <- u_kj + sbar z_j      (j > k),
+//   delta <- delta cbar,
+//
+// which is the Givens rotation that annihilates the row against row k of R
+// (the same Q and R), written without square roots: two multiply-adds per
+// entry instead of four.  The right-hand side is column m of U, so
+// R d = Q^T W b reduces to the unit-triangular U d = u_{:,m}: no divisions.
+// Column k of R has squared norm n_k = sum_{i<=k} d_i u_ik^2, so the
+// column-scaled diagonal of W A S (S = diag(1/||col R||), Sec. 3.3.2) is
+// q_k = sqrt(d_k / n_k); its spread bounds the conditioning of W A S.
+//
+// d_k starts at a tiny tau instead of 0 (a prior tau u_k^2 far below the
+// rounding of any real row): the first row reaching column k then needs no
+// special case, and a zero row leaves D and U unchanged exactly.
 #pragma once
 
 #include <cmath>
@@ -28,134 +36,90 @@
 
 namespace wlseno {
 
+// Reciprocal for the fold: FP32 uses the hardware approximation (about 1 ulp,
+// inside the rounding the FP32 factorisation already carries); FP64 the
+// correctly rounded reciprocal.
 template <typename T>
-__device__ __forceinline__ T rsqrt_t(T x);
+__device__ __forceinline__ T recip_t(T x);
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float recip_t<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 template <>
-__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double recip_t<double>(double x) { return __drcp_rn(x); }
 
 template <typename T>
-__device__ __forceinline__ void cswap(bool c, T& a, T& b) {
-  const T ta = a;
-  a = c ? b : a;
-  b = c ? ta : b;
-}
+__device__ __forceinline__ constexpr T fold_tau() { return sizeof(T) == 4 ? T(1e-30) : T(1e-280); }
 
-// Fold row a (a[M] = right-hand side) into the triangular factor R.
+// The square-root-free factor: d[k] and U[k][j] for j > k (column m is the
+// transformed right-hand side).  Entries with j <= k are never touched.
 template <typename T, int M>
-__device__ __forceinline__ void givens_fold(T (&R)[M][M + 1], T (&a)[M + 1]) {
-#pragma unroll
-  for (int k = 0; k < M; ++k) {
-    const T rkk = R[k][k];
-    const T ak = a[k];
-    const T t2 = rkk * rkk + ak * ak;
-    const bool nz = t2 > T(0);
-    const T inv = nz ? rsqrt_t<T>(t2) : T(0);
-    const T c = nz ? rkk * inv : T(1);
-    const T s = ak * inv;
-    R[k][k] = t2 * inv;
-#pragma unroll
-    for (int j = k + 1; j <= M; ++j) {
-      const T rj = R[k][j];
-      const T aj = a[j];
-      R[k][j] = c * rj + s * aj;
-      a[j] = c * aj - s * rj;
-    }
-  }
-}
-
-// Pivoted QR of the small scaled factor and its solve.
-template <typename T, int M>
-struct SmallQR {
-  T F[M][M];     // R S E after pivoting; R2 in its upper triangle at the end
-  T z[M];        // (Q Q2)^T W (ubar_S - ubar_i), first M entries
-  T s[M];        // S in pivoted order
-  int col[M];    // original column of pivoted position k
-  T y[M];        // solution in pivoted order (S-scaled unknowns)
-  T r00, rlast;
-  int rank;
+struct SqrtFreeQR {
+  T d[M];
+  T U[M][M + 1];
 };
 
-template <int K, typename T, int M>
-__device__ __forceinline__ void small_qr_step(SmallQR<T, M>& q, T tau_piv, T rank_tol) {
-  T pn[M];
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_init(SqrtFreeQR<T, M>& f) {
 #pragma unroll
-  for (int c = K; c < M; ++c) {
-    T acc = T(0);
+  for (int k = 0; k < M; ++k) {
+    f.d[k] = fold_tau<T>();
 #pragma unroll
-    for (int k = K; k < M; ++k) acc += q.F[k][c] * q.F[k][c];
-    pn[c] = acc;
+    for (int j = k + 1; j <= M; ++j) f.U[k][j] = T(0);
   }
-  T mx = T(0);
+}
+
+// Fold the row z (z[M] = right-hand side) with weight delta into f.
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_fold(SqrtFreeQR<T, M>& f, T (&z)[M + 1], T delta) {
 #pragma unroll
-  for (int c = K; c < M; ++c) mx = pn[c] > mx ? pn[c] : mx;
-  int p = K;
-  T sigma = pn[K];
+  for (int k = 0; k < M; ++k) {
+    const T zk = z[k];
+    const T t = delta * zk;
+    const T dn = fma(t, zk, f.d[k]);
+    const T r = recip_t<T>(dn);
+    const T sbar = t * r;
+    delta *= f.d[k] * r;
+    f.d[k] = dn;
 #pragma unroll
-  for (int c = M - 1; c >= K; --c)
-    if (pn[c] >= (T(1) - tau_piv) * mx) {
-      p = c;
-      sigma = pn[c];
+    for (int j = k + 1; j <= M; ++j) {
+      z[j] = fma(-zk, f.U[k][j], z[j]);
+      f.U[k][j] = fma(sbar, z[j], f.U[k][j]);
     }
-#pragma unroll
-  for (int c = K + 1; c < M; ++c) {
-    const bool sw = c == p;
-#pragma unroll
-    for (int k = 0; k < M; ++k) cswap(sw, q.F[k][K], q.F[k][c]);
-    cswap(sw, q.s[K], q.s[c]);
-    cswap(sw, q.col[K], q.col[c]);
   }
-  const T xk = q.F[K][K];
-  const T nrm = sqrt(sigma);
-  const T alpha = xk >= T(0) ? -nrm : nrm;
-  const T vtv = T(2) * (sigma + fabs(xk) * nrm);
-  const T tau = vtv > T(0) ? T(2) / vtv : T(0);
-  T v[M];
-#pragma unroll
-  for (int k = K; k < M; ++k) v[k] = k == K ? xk - alpha : q.F[k][K];
-#pragma unroll
-  for (int c = K + 1; c < M; ++c) {
-    T d = T(0);
-#pragma unroll
-    for (int k = K; k < M; ++k) d += v[k] * q.F[k][c];
-    d *= tau;
-#pragma unroll
-    for (int k = K; k < M; ++k) q.F[k][c] -= d * v[k];
-  }
-  {
-    T d = T(0);
-#pragma unroll
-    for (int k = K; k < M; ++k) d += v[k] * q.z[k];
-    d *= tau;
-#pragma unroll
-    for (int k = K; k < M; ++k) q.z[k] -= d * v[k];
-  }
-  q.F[K][K] = alpha;
-  if (K == 0) q.r00 = fabs(alpha);
-  if (q.rank == M && !(fabs(alpha) > rank_tol * q.r00)) q.rank = K;
 }
 
-template <int K, typename T, int M>
-__device__ __forceinline__ void small_backsub_step(SmallQR<T, M>& q) {
-  T t = q.z[K];
+// Spread of the column-scaled diagonal: max_k q_k^2 / min_k q_k^2 compared
+// with threshold^2 (true when the cell needs the pivoted path / refinement;
+// also for a zero or non-finite diagonal).
+template <typename T, int M>
+__device__ __forceinline__ bool sqrt_free_ill_conditioned(const SqrtFreeQR<T, M>& f, T threshold) {
+  T qmax = T(0), qmin = T(INFINITY);
 #pragma unroll
-  for (int c = K + 1; c < M; ++c) t -= q.F[K][c] * q.y[c];
-  const T rkk = q.F[K][K];
-  q.y[K] = (K < q.rank && rkk != T(0)) ? t / rkk : T(0);
-  if (K == q.rank - 1) q.rlast = fabs(rkk);
+  for (int k = 0; k < M; ++k) {
+    T n = f.d[k];
+#pragma unroll
+    for (int i = 0; i < k; ++i) n = fma(f.d[i] * f.U[i][k], f.U[i][k], n);
+    const T q = f.d[k] / n;
+    qmax = q > qmax ? q : qmax;
+    qmin = q < qmin ? q : qmin;
+  }
+  return !(qmax <= threshold * threshold * qmin);
 }
 
-template <typename T, int M, int... Ks>
-__device__ __forceinline__ void small_qr_solve(SmallQR<T, M>& q, T tau_piv, T rank_tol,
-                                               std::integer_sequence<int, Ks...>) {
-  (small_qr_step<Ks, T, M>(q, tau_piv, rank_tol), ...);
-  (small_backsub_step<M - 1 - Ks, T, M>(q), ...);
+// U d = u_{:,m} by back substitution (unit diagonal).
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_solve(const SqrtFreeQR<T, M>& f, T (&x)[M]) {
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    T t = f.U[k][M];
+#pragma unroll
+    for (int c = k + 1; c < M; ++c) t = fma(-f.U[k][c], x[c], t);
+    x[k] = t;
+  }
 }
-
-// ELL moments of the FP64 kernel (the FP32 kernel reads row records).
-template <typename T>
-__device__ __forceinline__ const T* ell_moments(const DeviceMesh& dm) { return dm.A64e; }
 
 template <typename T>
 __device__ __forceinline__ const T* tpc_points(const DeviceMesh& dm);

@@ -1,8 +1,8 @@
-// Thread-per-cell reconstruction kernels (see k_recon_tpc.cuh).
+// Thread-per-cell reconstruction kernels (the fold is in k_recon_tpc.cuh).
 //
-// Main kernel: fold the stencil rows into R by Givens rotations (W A = Q R),
-// solve R d = Q^T W (ubar_S - ubar_i) by back substitution, and estimate the
-// conditioning of W A S from the column-scaled diagonal |R_kk| s_k.  For a
+// Main kernel: fold the stencil rows into the square-root-free factor of
+// W A = Q R, solve R d = Q^T W (ubar_S - ubar_i), and estimate the
+// conditioning of W A S from the column-scaled diagonal of R.  For a
 // full-rank system this d is the least-squares solution the paper's QR with
 // column pivoting returns (Sec. 3.3.2).  Cells whose estimate exceeds the
 // flag threshold -- where pivoting and rank truncation could matter, and in
@@ -13,8 +13,7 @@
 // full -- column scaling, QR with column pivoting, numerical rank, basic
 // solution -- and, in FP32-bulk mode, one refinement sweep with the FP64
 // residual (FP64 weights and moments).  It overwrites the main kernel's
-// outputs for those cells.  (tpc_pivoted below is the same pivoted solve on
-// the small factor R S, kept for single-thread use.)
+// outputs for those cells.
 #pragma once
 
 #include "k_recon_tpc.cuh"
@@ -22,36 +21,32 @@
 
 namespace wlseno {
 
-template <typename T, int DIM, int M>
+// FP64 fold: rows read from the ELL layout, row t+1 fetched while row t is
+// folded (hides the index -> ubar chain).
+template <int DIM, int M>
 __device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* __restrict__ ubar,
-                                         int64_t i, double ui, int n, T eh2, T w_centre,
-                                         T (&R)[M][M + 1]) {
+                                         int64_t i, double ui, int n, double eh2, double w_centre,
+                                         SqrtFreeQR<double, M>& f) {
   const int64_t N = dm.N;
-  const T* Ae = ell_moments<T>(dm);
-#pragma unroll
-  for (int k = 0; k < M; ++k)
-#pragma unroll
-    for (int j = k; j <= M; ++j) R[k][j] = T(0);
-  // row t+1 is fetched while row t is folded (hides the index -> ubar chain)
+  const double* Ae = dm.A64e;
+  sqrt_free_init(f);
   double u_next = ubar[dm.st_ell[i]];
-  T a_next[M];
+  double a_next[M];
 #pragma unroll
   for (int c = 0; c < M; ++c) a_next[c] = Ae[static_cast<int64_t>(c) * N + i];
   for (int t = 0; t < n; ++t) {
-    const T dev = static_cast<T>(u_next - ui);
-    T a[M + 1];
+    const double dev = u_next - ui;
+    double z[M + 1];
 #pragma unroll
-    for (int c = 0; c < M; ++c) a[c] = a_next[c];
+    for (int c = 0; c < M; ++c) z[c] = a_next[c];
     if (t + 1 < n) {
       u_next = ubar[dm.st_ell[(t + 1) * N + i]];
 #pragma unroll
       for (int c = 0; c < M; ++c) a_next[c] = Ae[(static_cast<int64_t>(t + 1) * M + c) * N + i];
     }
-    const T w = t == 0 ? w_centre : eh2 / (dev * dev + eh2);
-#pragma unroll
-    for (int c = 0; c < M; ++c) a[c] *= w;
-    a[M] = w * dev;
-    givens_fold<T, M>(R, a);
+    const double w = t == 0 ? w_centre : eh2 * recip_t(fma(dev, dev, eh2));
+    z[M] = dev;
+    sqrt_free_fold(f, z, w * w);
   }
 }
 
@@ -85,7 +80,7 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int DIM, int M>
 __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const double* __restrict__ ubar,
                                                 int64_t i, double ui, int n, float eh2, float w_centre,
-                                                float (&R)[M][M + 1]) {
+                                                SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
   constexpr int kRec = 5, kU = 3;
   __shared__ float4 srec[kRec][W4][kTpcThreads];
@@ -102,10 +97,7 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
     const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][tid])[M % 4]);
     cp_async8(&su[u_slot][tid], ubar + j);
   };
-#pragma unroll
-  for (int k = 0; k < M; ++k)
-#pragma unroll
-    for (int j = k; j <= M; ++j) R[k][j] = 0.0f;
+  sqrt_free_init(f);
   for (int t = 0; t < 4 && t < n; ++t) fetch_rec(t, t);
   cp_async_commit();
   cp_async_wait<0>();
@@ -115,14 +107,14 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
   int sr = 0, sv = 0;  // slots of row t
   for (int t = 0; t < n; ++t) {
     cp_async_wait<1>();
-    float a[M + 1];
+    float z[M + 1];
 #pragma unroll
     for (int k = 0; k < W4; ++k) {
       const float4 v = srec[sr][k][tid];
       const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (4 * k + q < M) a[4 * k + q] = vv[q];
+        if (4 * k + q < M) z[4 * k + q] = vv[q];
     }
     const double uj = su[sv][tid];
     const int sr2 = sr + 2 < kRec ? sr + 2 : sr + 2 - kRec;
@@ -132,52 +124,24 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
     if (t + 4 < n) fetch_rec(t + 4, sr4);
     cp_async_commit();
     const float dev = static_cast<float>(uj - ui);
-    const float w = t == 0 ? w_centre : eh2 / (dev * dev + eh2);
-#pragma unroll
-    for (int c = 0; c < M; ++c) a[c] *= w;
-    a[M] = w * dev;
-    givens_fold<float, M>(R, a);
+    const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
+    z[M] = dev;
+    sqrt_free_fold(f, z, w * w);
     sr = sr + 1 < kRec ? sr + 1 : 0;
     sv = sv + 1 < kU ? sv + 1 : 0;
   }
   cp_async_wait<0>();
 }
 
-// Column scaling from R's column norms and the pivoted QR of R S.
-template <typename T, int M>
-__device__ __forceinline__ void tpc_pivoted(const T (&R)[M][M + 1], T rank_tol, SmallQR<T, M>& q) {
-#pragma unroll
-  for (int c = 0; c < M; ++c) {
-    T nrm2 = T(0);
-#pragma unroll
-    for (int k = 0; k <= c; ++k) nrm2 += R[k][c] * R[k][c];
-    const T s = nrm2 > T(0) ? rsqrt_t<T>(nrm2) : T(0);
-    q.s[c] = s;
-    q.col[c] = c;
-#pragma unroll
-    for (int k = 0; k < M; ++k) q.F[k][c] = k <= c ? R[k][c] * s : T(0);
-  }
-#pragma unroll
-  for (int k = 0; k < M; ++k) q.z[k] = R[k][M];
-  q.rank = M;
-  q.r00 = T(0);
-  q.rlast = T(0);
-  const T tau_piv = sizeof(T) == 8 ? T(1e-6) : T(1e-4);
-  small_qr_solve<T, M>(q, tau_piv, rank_tol, std::make_integer_sequence<int, M>{});
-}
-
-// Coefficients (original column order) and facet values of cell i.
-// Without the FP64 low part (kLo = false) no FP64 multiply-add is issued:
-// on GB300 the FP64 pipe runs at 1/64 of the FP32 rate.
-template <typename T, int DIM, int M, bool kLo = true>
-__device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui,
-                                          const T (&hi)[M], const double (&lo)[M],
+// Coefficients and facet values of cell i (FP32-bulk: the polynomial in FP32,
+// ubar_i added in FP64).
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
                                           double* __restrict__ coeffs, double* __restrict__ fvals) {
   constexpr int NP = (DIM + 1) * (DIM == 2 ? 2 : 3);
   if (coeffs) {
 #pragma unroll
-    for (int c = 0; c < M; ++c)
-      coeffs[i * M + c] = static_cast<double>(hi[c]) + (kLo ? lo[c] : 0.0) + (c == 0 ? ui : 0.0);
+    for (int c = 0; c < M; ++c) coeffs[i * M + c] = static_cast<double>(x[c]) + (c == 0 ? ui : 0.0);
   }
   const T* P = tpc_points<T>(dm) + i * NP * DIM;
 #pragma unroll
@@ -188,13 +152,9 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
     T mono[M];
     eval_monomials<T, DIM, M>(yy, mono);
     T sh = T(0);
-    double sl = 0.0;
 #pragma unroll
-    for (int c = 0; c < M; ++c) {
-      sh += hi[c] * mono[c];
-      if (kLo) sl += lo[c] * static_cast<double>(mono[c]);
-    }
-    fvals[i * NP + pt] = ui + static_cast<double>(sh) + sl;
+    for (int c = 0; c < M; ++c) sh = fma(x[c], mono[c], sh);
+    fvals[i * NP + pt] = ui + static_cast<double>(sh);
   }
 }
 
@@ -210,36 +170,15 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   const double ui = ubar[i];
   T eh2, wc;
   tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
-  T R[M][M + 1];
+  SqrtFreeQR<T, M> f;
   if constexpr (sizeof(T) == 4)
-    tpc_fold_staged<DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
+    tpc_fold_staged<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
   else
-    tpc_fold<T, DIM, M>(dm, ubar, i, ui, n, eh2, wc, R);
-  // conditioning estimate of W A S from its scaled diagonal
-  T dmax = T(0), dmin = T(INFINITY);
-#pragma unroll
-  for (int c = 0; c < M; ++c) {
-    T nrm2 = T(0);
-#pragma unroll
-    for (int k = 0; k <= c; ++k) nrm2 += R[k][c] * R[k][c];
-    const T dk = nrm2 > T(0) ? fabs(R[c][c]) * rsqrt_t<T>(nrm2) : T(0);
-    dmax = dk > dmax ? dk : dmax;
-    dmin = dk < dmin ? dk : dmin;
-  }
-  const bool flagged = !(dmax <= flag_threshold * dmin);  // also catches dmin == 0 and NaN
-  // R d = Q^T b
+    tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
+  const bool flagged = sqrt_free_ill_conditioned(f, flag_threshold);
   T d[M];
-#pragma unroll
-  for (int k = M - 1; k >= 0; --k) {
-    T t = R[k][M];
-#pragma unroll
-    for (int c = k + 1; c < M; ++c) t -= R[k][c] * d[c];
-    d[k] = R[k][k] != T(0) ? t / R[k][k] : T(0);
-  }
-  double lo[M];
-#pragma unroll
-  for (int c = 0; c < M; ++c) lo[c] = 0.0;
-  tpc_write<T, DIM, M, false>(dm, i, ui, d, lo, coeffs, fvals);
+  sqrt_free_solve(f, d);
+  tpc_write<T, DIM, M>(dm, i, ui, d, coeffs, fvals);
   if (flagged) {
     if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
     worklist[atomicAdd(wl_count, 1)] = static_cast<int>(i);
