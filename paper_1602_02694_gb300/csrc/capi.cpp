@@ -34,8 +34,10 @@ struct wlseno_ctx {
   double* d_out = nullptr;       // [C][N] staging for host outputs
   double* d_coef = nullptr;      // [C][N][m] staging for host coefficient output
   double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
-  int* d_wl = nullptr;           // [N] cells flagged for refinement (FP32-bulk)
-  int* d_wl_count = nullptr;     // [1]
+  int* d_wl = nullptr;           // [N] cells for the pivoted lane-group path
+  int* d_wl_count = nullptr;     // [2] lengths of d_wl and d_rl
+  int* d_rl = nullptr;           // [N] cells for the FP64-residual refinement (FP32-bulk)
+  float* d_rbuf = nullptr;       // [refine_fields(m)][N] their FP32 factors
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
   cudaStream_t cap_stream = nullptr;
@@ -199,16 +201,16 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
     int nl = 0;
-    int* wl = ctx->d_wl;
+    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rl, ctx->d_rbuf};
     if (dm.dim == 2 && dm.m == 6)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
-              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl);
     else if (dm.dim == 2 && dm.m == 10)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
-              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
     else if (dm.dim == 3 && dm.m == 10)
-      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl)
-              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, ctx->d_wl_count, s, &nl);
+      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
     scope.done(e == cudaSuccess ? nl : 0);
     return e;
   }
@@ -448,7 +450,11 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.rec_width = rec32_width(H.m);
   if ((st = dalloc(ctx, &dm.st_ell, ell)) || (st = dalloc(ctx, &dm.A64e, ell * H.m)) ||
       (st = dalloc(ctx, &dm.rec32, ell * dm.rec_width)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
-      (st = dalloc(ctx, &ctx->d_wl_count, 1)))
+      (st = dalloc(ctx, &ctx->d_wl_count, 2)))
+    return st;
+  if (ctx->scheme.precision == WLSENO_FP32_BULK &&
+      ((st = dalloc(ctx, &ctx->d_rl, N)) ||
+       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_fields(H.m)) * N))))
     return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");

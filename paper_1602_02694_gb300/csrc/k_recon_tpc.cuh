@@ -91,11 +91,11 @@ __device__ __forceinline__ void sqrt_free_fold(SqrtFreeQR<T, M>& f, T (&z)[M + 1
   }
 }
 
-// Spread of the column-scaled diagonal: max_k q_k^2 / min_k q_k^2 compared
-// with threshold^2 (true when the cell needs the pivoted path / refinement;
-// also for a zero or non-finite diagonal).
+// Spread of the column-scaled diagonal: qmax = max_k q_k^2 and qmin =
+// min_k q_k^2.  A cell is ill-conditioned at threshold K when
+// !(qmax <= K^2 qmin), which also catches a zero or non-finite diagonal.
 template <typename T, int M>
-__device__ __forceinline__ bool sqrt_free_ill_conditioned(const SqrtFreeQR<T, M>& f, T threshold) {
+__device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, T* qmax_out, T* qmin_out) {
   T qmax = T(0), qmin = T(INFINITY);
 #pragma unroll
   for (int k = 0; k < M; ++k) {
@@ -106,7 +106,13 @@ __device__ __forceinline__ bool sqrt_free_ill_conditioned(const SqrtFreeQR<T, M>
     qmax = q > qmax ? q : qmax;
     qmin = q < qmin ? q : qmin;
   }
-  return !(qmax <= threshold * threshold * qmin);
+  *qmax_out = qmax;
+  *qmin_out = qmin;
+}
+
+// Packed position of U[k][j] (k < j < M) in a strict upper triangle.
+__host__ __device__ constexpr int strict_upper_index(int M, int k, int j) {
+  return k * M - k * (k + 1) / 2 + (j - k - 1);
 }
 
 // U d = u_{:,m} by back substitution (unit diagonal).

@@ -162,8 +162,8 @@ template <typename T, int DIM, int M>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
                  double* __restrict__ coeffs, double* __restrict__ fvals,
-                 unsigned long long* __restrict__ counters, int* __restrict__ worklist,
-                 int* __restrict__ wl_count, T flag_threshold) {
+                 unsigned long long* __restrict__ counters, TpcWork work, T flag_threshold,
+                 T pivot_threshold) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= dm.N) return;
   const int n = dm.st_ptr[i + 1] - dm.st_ptr[i];
@@ -175,37 +175,212 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
     tpc_fold_staged<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
   else
     tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
-  const bool flagged = sqrt_free_ill_conditioned(f, flag_threshold);
-  T d[M];
-  sqrt_free_solve(f, d);
-  tpc_write<T, DIM, M>(dm, i, ui, d, coeffs, fvals);
-  if (flagged) {
-    if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
-    worklist[atomicAdd(wl_count, 1)] = static_cast<int>(i);
+  T qmax, qmin;
+  sqrt_free_spread(f, &qmax, &qmin);
+  T x[M];
+  sqrt_free_solve(f, x);
+  tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals);
+  if (qmax <= flag_threshold * flag_threshold * qmin) return;
+  if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
+  if (sizeof(T) == 4 && work.refine_list && qmax <= pivot_threshold * pivot_threshold * qmin) {
+    // keep the FP32 factor for the refinement kernel
+    const int slot = atomicAdd(&work.counts[1], 1);
+    work.refine_list[slot] = static_cast<int>(i);
+    float* buf = work.refine_buf + slot;
+    const int64_t N = dm.N;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      buf[c * N] = static_cast<float>(x[c]);
+      buf[(M + c) * N] = static_cast<float>(f.d[c]);
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+#pragma unroll
+      for (int j = k + 1; j < M; ++j)
+        buf[(2 * M + strict_upper_index(M, k, j)) * N] = static_cast<float>(f.U[k][j]);
+  } else {
+    work.group_list[atomicAdd(&work.counts[0], 1)] = static_cast<int>(i);
   }
 }
 
+// One corrected-seminormal-equations sweep on the refine-listed cells
+// (FP32-bulk): with the FP32 factor W A = Q D^(1/2) U of the main kernel and
+// its solution x, x += (U^T D U)^-1 A^T W^2 (b - A x), with the residual
+// b - A x formed in FP64 from the FP64 moments and deviations (the FP32
+// factor only preconditions the correction).  L lanes share a
+// cell, lane l taking rows l, l+L, ..., l+(RPL-1)L (the thread-per-cell path
+// serves stencils of at most L*RPL rows); every load of those rows is issued
+// before any arithmetic, so a cell costs about one memory round trip.  The
+// partial sums are combined by shuffles.  It overwrites the main kernel's
+// outputs for those cells.
+template <int DIM, int M, int L, int RPL>
+__global__ void __launch_bounds__(64)
+refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
+              double* __restrict__ coeffs, double* __restrict__ fvals, TpcWork work) {
+  constexpr int NF = DIM + 1;
+  constexpr int NP = NF * (DIM == 2 ? 2 : 3);
+  constexpr int kPerWarp = 32 / L;
+  const int count = work.counts[1];
+  const int64_t N = dm.N;
+  const int lane = threadIdx.x % L;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / 32;
+  const int64_t warps = gridDim.x * static_cast<int64_t>(blockDim.x) / 32;
+  for (int64_t base = warp * kPerWarp; base < count; base += warps * kPerWarp) {
+    const int64_t slot = base + (threadIdx.x % 32) / L;
+    const bool valid = slot < count;
+    const int64_t i = valid ? work.refine_list[slot] : 0;
+    const int beg = dm.st_ptr[i];
+    const int n = valid ? dm.st_ptr[i + 1] - beg : 0;
+    // all loads of this lane's rows first, from the CSR layout: a cell's rows
+    // are contiguous, so the group's loads of one row set share cache lines
+    int64_t jrow[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int t = lane + r * L;
+      jrow[r] = t < n ? dm.st_idx[beg + t] : i;
+    }
+    double a[RPL][M];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int t = lane + r * L;
+      const double* row = dm.A64 + static_cast<int64_t>(beg + t) * M;
+#pragma unroll
+      for (int c = 0; c < M; ++c) a[r][c] = t < n ? row[c] : 0.0;
+    }
+    const double ui = ubar[i];
+    double uj[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) uj[r] = ubar[jrow[r]];
+    const float* buf = work.refine_buf + (valid ? slot : 0);
+    double x[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) x[c] = static_cast<double>(buf[c * N]);
+    // weights of the FP64 problem (Sec. 3.1.2), to FP32 relative accuracy:
+    // only the residual needs FP64 (its cancellation), A^T W^2 r does not
+    const double hi = dm.h[i];
+    const float e = static_cast<float>(sp.eps * hi * hi);
+    float bmin = INFINITY;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int nb = dm.nbr[i * NF + f];
+      if (nb >= 0) {
+        const float dv = static_cast<float>(ubar[nb >> 2] - ui);
+        bmin = fminf(bmin, fmaf(dv, dv, e));
+      }
+    }
+    float g[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) g[c] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int t = lane + r * L;
+      const double dev = uj[r] - ui;
+      const float devf = static_cast<float>(dev);
+      const float beta = t == 0 ? bmin : fmaf(devf, devf, e);
+      const float w = (t == 0 ? static_cast<float>(sp.alpha_c) * e : e) / beta;
+      double fit0 = 0.0, fit1 = 0.0;
+#pragma unroll
+      for (int c = 0; c < M; c += 2) {
+        fit0 = fma(a[r][c], x[c], fit0);
+        if (c + 1 < M) fit1 = fma(a[r][c + 1], x[c + 1], fit1);
+      }
+      const float wr = t < n ? w * w * static_cast<float>(dev - (fit0 + fit1)) : 0.0f;
+#pragma unroll
+      for (int c = 0; c < M; ++c) g[c] = fmaf(wr, static_cast<float>(a[r][c]), g[c]);
+    }
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int c = 0; c < M; ++c) g[c] += __shfl_xor_sync(0xffffffffu, g[c], off);
+    if (!valid) continue;
+    // (U^T D U) delta = g with the FP32 factor
+    float dl[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      float v = g[k];
+#pragma unroll
+      for (int q = 0; q < k; ++q) v = fmaf(-buf[(2 * M + strict_upper_index(M, q, k)) * N], dl[q], v);
+      dl[k] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) dl[k] /= buf[(M + k) * N];
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+      float v = dl[k];
+#pragma unroll
+      for (int q = k + 1; q < M; ++q) v = fmaf(-buf[(2 * M + strict_upper_index(M, k, q)) * N], dl[q], v);
+      dl[k] = v;
+    }
+    float xh[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) xh[c] = buf[c * N];
+    if (coeffs) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        if (c % L == lane)
+          coeffs[i * M + c] = static_cast<double>(xh[c]) + static_cast<double>(dl[c]) + (c == 0 ? ui : 0.0);
+    }
+    const float* P = dm.fpts32 + i * NP * DIM;
+#pragma unroll
+    for (int pt = 0; pt < NP; ++pt) {
+      if (pt % L != lane) continue;
+      float yy[DIM];
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) yy[q] = P[pt * DIM + q];
+      float mono[M];
+      eval_monomials<float, DIM, M>(yy, mono);
+      float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        sh = fmaf(xh[c], mono[c], sh);
+        sl = fmaf(dl[c], mono[c], sl);
+      }
+      fvals[i * NP + pt] = ui + static_cast<double>(sh) + static_cast<double>(sl);
+    }
+  }
+}
+
+// Cells of the refinement sweep above this conditioning estimate take the
+// pivoted path instead (one FP32 sweep contracts the error by about
+// kappa * 2^-24).
+constexpr float kRefinePivotBound = 1e5f;
+
 template <typename T, int DIM, int M>
 cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
-                             const ReconOut& out, int* worklist, int* wl_count, cudaStream_t s,
+                             const ReconOut& out, const TpcWork& work, cudaStream_t s,
                              int* launches) {
   constexpr int threads = kTpcThreads;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
-  // FP32-bulk: refine above kappa_flag; FP64: take the pivoted path above 1e6
-  const T threshold = sizeof(T) == 4 ? static_cast<T>(sp.kappa_flag) : T(1e6);
+  // FP32-bulk: refine above kappa_flag (pivot above kRefinePivotBound);
+  // FP64: take the pivoted path above 1e6
+  const bool f32 = sizeof(T) == 4;
+  const T flag = f32 ? static_cast<T>(sp.kappa_flag) : T(1e6);
+  const T pivot = f32 ? static_cast<T>(kRefinePivotBound) : flag;
   *launches = 0;
-  cudaError_t e = cudaMemsetAsync(wl_count, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(work.counts, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
-                                                        out.counters, worklist, wl_count, threshold);
+                                                        out.counters, work, flag, pivot);
   ++*launches;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // the listed cells, one lane group each: rows spread over the lanes
+  if constexpr (sizeof(T) == 4) {
+    if (!work.refine_list) return cudaErrorInvalidValue;
+    // 16 lanes x 4 rows: every stencil the thread-per-cell path accepts (<= 64)
+    constexpr int L = 16, RPL = 4, kThreads = 64;
+    const int64_t want = (dm.N * L + kThreads - 1) / kThreads;
+    const unsigned rblocks = static_cast<unsigned>(want < 8 * 152 ? want : 8 * 152);
+    refine_kernel<DIM, M, L, RPL>
+        <<<rblocks, kThreads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals, work);
+    ++*launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // the pivoted cells, one lane group each: rows spread over the lanes
   if (dm.nmax <= 40)
-    e = launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, worklist, wl_count, s);
+    e = launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, work.group_list, work.counts, s);
   else
-    e = launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, worklist, wl_count, s);
+    e = launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, work.group_list, work.counts, s);
   ++*launches;
   return e;
 }

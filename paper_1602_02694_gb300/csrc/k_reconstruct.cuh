@@ -481,8 +481,9 @@ cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  // a few blocks per SM: the list is short (and usually empty)
   const int64_t groups = (dm.N * G + threads - 1) / threads;
-  const unsigned blocks = static_cast<unsigned>(groups < 152 * 8 ? groups : 152 * 8);
+  const unsigned blocks = static_cast<unsigned>(groups < 152 * 2 ? groups : 152 * 2);
   reconstruct_list_kernel<T, DIM, M, G, R><<<blocks, threads, smem, s>>>(
       dm, sp, ubar, out.coeffs, out.fvals, out.counters, worklist, wl_count);
   return cudaGetLastError();

@@ -13,8 +13,8 @@ cudaError_t launch_reconstruct_inst<float, 2, 10>(const DeviceMesh& dm, const Sc
 template <>
 cudaError_t launch_recon_tpc_inst<float, 2, 10>(const DeviceMesh& dm, const SchemeParams& sp,
                                                  const double* ubar, const ReconOut& out,
-                                                 int* worklist, int* wl_count, cudaStream_t s,
+                                                 const TpcWork& work, cudaStream_t s,
                                                  int* launches) {
-  return launch_recon_tpc<float, 2, 10>(dm, sp, ubar, out, worklist, wl_count, s, launches);
+  return launch_recon_tpc<float, 2, 10>(dm, sp, ubar, out, work, s, launches);
 }
 }  // namespace wlseno

@@ -108,16 +108,30 @@ cudaError_t launch_moments(const DeviceMesh& dm, cudaStream_t s);
 // Copies the CSR stencil and moments into the ELL arrays.
 cudaError_t launch_ell_copy(const DeviceMesh& dm, cudaStream_t s);
 
-// Thread-per-cell reconstruction (and, in FP32-bulk with a work list, the
-// refinement sweep); *launches receives the number of kernels launched.
+// Work lists of the thread-per-cell kernels.  Flagged cells go either to the
+// pivoted lane-group path (group_list) or, in FP32-bulk when only moderately
+// ill-conditioned, to the thread-level FP64-residual refinement (refine_list),
+// which reuses the FP32 factor the main kernel left in refine_buf.
+struct TpcWork {
+  int* group_list;          // [N]
+  int* counts;              // [2]: lengths of group_list and refine_list
+  int* refine_list;         // [N] (FP32-bulk contexts; else null)
+  float* refine_buf;        // [refine_fields(m)][N]: x, d, strict upper U
+};
+
+// Floats per refine-listed cell: solution x (m), D (m), strict upper U (m(m-1)/2).
+__host__ __device__ constexpr int refine_fields(int m) { return 2 * m + m * (m - 1) / 2; }
+
+// Thread-per-cell reconstruction and its follow-up kernels; *launches
+// receives the number of kernels launched.
 template <typename T, int DIM, int M>
 cudaError_t launch_recon_tpc_inst(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
-                                  const ReconOut& out, int* worklist, int* wl_count, cudaStream_t s,
+                                  const ReconOut& out, const TpcWork& work, cudaStream_t s,
                                   int* launches);
 #define WLSENO_DECLARE_TPC(T, D, M)                                                            \
   template <>                                                                                   \
   cudaError_t launch_recon_tpc_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,            \
-                                             const double*, const ReconOut&, int*, int*,        \
+                                             const double*, const ReconOut&, const TpcWork&,    \
                                              cudaStream_t, int*);
 WLSENO_DECLARE_TPC(double, 2, 6)
 WLSENO_DECLARE_TPC(double, 2, 10)
