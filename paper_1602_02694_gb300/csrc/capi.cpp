@@ -38,6 +38,7 @@ struct wlseno_ctx {
   int* d_wl_count = nullptr;     // [2] lengths of d_wl and d_rl
   int* d_rl = nullptr;           // [N] cells for the FP64-residual refinement (FP32-bulk)
   float* d_rbuf = nullptr;       // [refine_fields(m)][N] their FP32 factors
+  float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
   cudaStream_t cap_stream = nullptr;
@@ -192,9 +193,11 @@ void reset_kind_stats(wlseno_ctx* ctx) {
 }
 
 
+// fvals receives the facet values, or with fdev set (FP32-bulk) their FP32
+// deviations from the cell averages instead.
 cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
-                            cudaStream_t s) {
-  ReconOut out{coeffs, fvals, ctx->d_counters};
+                            cudaStream_t s, float* fdev = nullptr) {
+  ReconOut out{coeffs, fdev ? nullptr : fvals, ctx->d_counters, fdev};
   const DeviceMesh& dm = ctx->dm;
   const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
   cudaError_t e = cudaErrorInvalidValue;
@@ -228,9 +231,10 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
 }
 
 cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, const double* u0,
-                     double a, double b, bool residual_only, double* out, cudaStream_t s) {
+                     double a, double b, bool residual_only, double* out, cudaStream_t s,
+                     const float* fdev = nullptr) {
   KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
-  cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, u, u0,
+  cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, fdev, u, u0,
                                          a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s);
   scope.done(e == cudaSuccess ? 1 : 0);
   return e;
@@ -258,11 +262,13 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
     scope.done(e == cudaSuccess ? 2 : 0);
     return e;
   }
+  // FP32-bulk thread-per-cell: facet values travel as FP32 deviations
+  float* fdev = ctx->G == 1 ? ctx->d_fdev : nullptr;
   for (int c = 0; c < C && e == cudaSuccess; ++c) {
-    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s);
+    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s, fdev);
     if (e == cudaSuccess)
       e = flux_one(ctx, ctx->d_fvals, u + c * N, u0 ? u0 + c * N : nullptr, a, b, residual_only,
-                   out + c * N, s);
+                   out + c * N, s, fdev);
   }
   return e;
 }
@@ -288,6 +294,7 @@ bool ctx_view(const wlseno_ctx* ctx, CtxView* out) {
   out->sp = ctx->sp;
   out->counters = ctx->d_counters;
   out->dt = ctx->d_dt;
+  out->dev_facets = ctx->d_fdev != nullptr && ctx->G == 1;
   return true;
 }
 
@@ -298,12 +305,12 @@ void ctx_set_error(wlseno_ctx* ctx, const std::string& msg) {
 cudaError_t ctx_launch_reconstruct(wlseno_ctx* ctx, const double* ubar, const ReconOut& out,
                                    cudaStream_t s) {
   ctx->last_stream = s;
-  return reconstruct_one(ctx, ubar, out.coeffs, out.fvals, s);
+  return reconstruct_one(ctx, ubar, out.coeffs, out.fvals, s, out.fdev);
 }
 
-cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const double* ubar,
-                                     double* residual, cudaStream_t s) {
-  return flux_one(ctx, fvals, ubar, nullptr, 0.0, 1.0, true, residual, s);
+cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const float* fdev,
+                                     const double* ubar, double* residual, cudaStream_t s) {
+  return flux_one(ctx, fvals, ubar, nullptr, 0.0, 1.0, true, residual, s, fdev);
 }
 
 }  // namespace wlseno
@@ -414,12 +421,15 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.nq = H.nq;
   dm.N = N;
   dm.nnz = H.nnz;
-  double *coords, *centroid, *h, *vol, *inr, *period, *fgeo, *fpts;
+  double *coords, *centroid, *h, *vol, *ivol, *inr, *period, *fgeo, *fpts;
   int32_t *mesh_of, *nbr;
   float* fp32;
+  std::vector<double> inv_volume(H.volume.size());
+  for (size_t k = 0; k < inv_volume.size(); ++k) inv_volume[k] = 1.0 / H.volume[k];
   if ((st = upload(ctx, &ctx->d_st_ptr, ptr32)) || (st = upload(ctx, &ctx->d_st_idx, idx32)) ||
       (st = upload(ctx, &coords, H.coords)) || (st = upload(ctx, &centroid, H.centroid)) ||
       (st = upload(ctx, &h, H.h)) || (st = upload(ctx, &vol, H.volume)) ||
+      (st = upload(ctx, &ivol, inv_volume)) ||
       (st = upload(ctx, &inr, H.inradius)) || (st = upload(ctx, &mesh_of, H.mesh_of)) ||
       (st = upload(ctx, &period, H.period)) || (st = upload(ctx, &nbr, H.nbr)) ||
       (st = upload(ctx, &fgeo, H.fgeo)) || (st = upload(ctx, &fpts, H.fpts)) ||
@@ -431,6 +441,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.centroid = centroid;
   dm.h = h;
   dm.volume = vol;
+  dm.inv_volume = ivol;
   dm.inradius = inr;
   dm.mesh_of = mesh_of;
   dm.period = period;
@@ -453,7 +464,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (st = dalloc(ctx, &ctx->d_wl_count, 2)))
     return st;
   if (ctx->scheme.precision == WLSENO_FP32_BULK &&
-      ((st = dalloc(ctx, &ctx->d_rl, N)) ||
+      ((st = dalloc(ctx, &ctx->d_rl, N)) || (st = dalloc(ctx, &ctx->d_fdev, N * NP)) ||
        (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_fields(H.m)) * N))))
     return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
@@ -817,10 +828,9 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   // recompute the stages k1, k2 of the step from the checkpoint u
   double* k1 = ctx->d_k1;
   double* k2 = ctx->d_k2;
-  if ((e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
-      (e = flux_one(ctx, ctx->d_fvals, u, u, 0.0, 1.0, false, k1, s)) != cudaSuccess ||
-      (e = reconstruct_one(ctx, k1, nullptr, ctx->d_fvals, s)) != cudaSuccess ||
-      (e = flux_one(ctx, ctx->d_fvals, k1, u, 0.75, 0.25, false, k2, s)) != cudaSuccess)
+  // (the same launches as the forward step, so the stages match it bitwise)
+  if ((e = stage_all(ctx, u, u, 0.0, 1.0, false, k1, s)) != cudaSuccess ||
+      (e = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "adjoint: forward stages");
   auto vjp = [&](const double* state, const double* lam, double* out) -> cudaError_t {
     cudaError_t err = reconstruct_one(ctx, state, nullptr, ctx->d_fvals, s);

@@ -141,6 +141,108 @@ flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fva
   if (!isfinite(res)) atomicAdd(&counters[2], 1ull);
 }
 
+// FP32-bulk flux from facet deviations: the facet values arrive as FP32
+// deviations from their cell averages, value = ubar_c + dev.  Each facet is
+// split at its lower-indexed cell's average u_ref = ubar_L (the same for both
+// cells, so both compute the bitwise-same flux): F(u_ref).n in FP64 plus the
+// FP32 flux of the deviations from u_ref, where the other cell's deviations
+// are shifted by the FP32 rounding of ubar_R - ubar_L.  FP64 work is then one
+// subtraction, the reference flux and the accumulation per facet.
+template <int DIM, int NQ>
+__device__ __forceinline__ double facet_flux_dev(const SchemeParams& sp, const double* geo,
+                                                 float speed, double uref,
+                                                 const float (&dL)[NQ], const float (&dR)[NQ]) {
+  const float wq = 1.0f / NQ;
+  double nsum64 = 0.0, vn64 = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    nsum64 += geo[a];
+    vn64 = fma(sp.vel[a], geo[a], vn64);
+  }
+  float fsum = 0.0f;
+  double fref;
+  if (sp.pde == WLSENO_ADVECTION) {
+    const float vn = static_cast<float>(vn64);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) fsum += wq * (0.5f * (vn * (dL[q] + dR[q]) - speed * (dR[q] - dL[q])));
+    fref = vn64 * uref;
+  } else {
+    const float ur = static_cast<float>(uref);
+    const float nsum = static_cast<float>(nsum64);
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) mx = fmaxf(mx, fmaxf(fabsf(ur + dL[q]), fabsf(ur + dR[q])));
+    const float alpha = mx * fabsf(nsum);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {  // (u^2 - u_ref^2)/2 = d (u_ref + d/2)
+      const float fl = nsum * dL[q] * (ur + 0.5f * dL[q]);
+      const float fr = nsum * dR[q] * (ur + 0.5f * dR[q]);
+      fsum += wq * (0.5f * ((fl + fr) - alpha * (dR[q] - dL[q])));
+    }
+    fref = 0.5 * uref * uref * nsum64;
+  }
+  return geo[3] * (fref + static_cast<double>(fsum));
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ fdev,
+                      const double* __restrict__ u, const double* __restrict__ u0, double a, double b,
+                      const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
+                      unsigned long long* __restrict__ counters) {
+  constexpr int NF = DIM + 1;
+  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NP = NF * NQ;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= dm.N) return;
+  float speed2 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) speed2 += static_cast<float>(sp.vel[q] * sp.vel[q]);
+  const float speed = sqrtf(speed2);
+  const double ui = u[i];
+  double acc = 0.0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int nb = dm.nbr[i * NF + f];
+    float di[NQ], dj[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) di[q] = fdev[i * NP + f * NQ + q];
+    double uj = ui;
+    bool owner = true;
+    if (nb >= 0) {
+      const int64_t j = nb >> 2;
+      const int f2 = nb & 3;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dj[q] = fdev[j * NP + f2 * NQ + q];
+      uj = u[j];
+      owner = i < j;
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dj[q] = di[q];
+    }
+    const double uL = owner ? ui : uj;
+    const float jump = static_cast<float>((owner ? uj : ui) - uL);
+    float dL[NQ], dR[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      dL[q] = owner ? di[q] : dj[q];
+      dR[q] = (owner ? dj[q] : di[q]) + jump;
+    }
+    const double flux = facet_flux_dev<DIM, NQ>(sp, dm.fgeo + (i * NF + f) * 4, speed, uL, dL, dR);
+    acc += owner ? flux : -flux;
+  }
+  const double L = -acc * dm.inv_volume[i];
+  double res;
+  if (residual_only) {
+    res = L;
+  } else {
+    const double dt = dt_mesh[dm.mesh_of[i]];
+    res = a * u0[i] + b * (ui + dt * L);
+  }
+  out[i] = res;
+  if (!isfinite(res)) atomicAdd(&counters[2], 1ull);
+}
+
 // Largest |ubar| per mesh, as the bits of a non-negative double (their
 // integer order is the numeric order, so atomicMax is exact and deterministic).
 __global__ void max_abs_kernel(int64_t N, const double* __restrict__ u,
@@ -184,12 +286,20 @@ __global__ void cfl_dt_kernel(int n_meshes, int pde, int dim, double adv_speed,
 }  // namespace
 
 cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
-                                   const double* fvals, const double* u, const double* u0,
-                                   double a, double b, const double* dt_mesh, bool residual_only,
-                                   double* out, unsigned long long* counters, cudaStream_t s) {
+                                   const double* fvals, const float* fdev, const double* u,
+                                   const double* u0, double a, double b, const double* dt_mesh,
+                                   bool residual_only, double* out, unsigned long long* counters,
+                                   cudaStream_t s) {
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   const int ro = residual_only ? 1 : 0;
+  if (fdev) {
+    if (dm.dim == 2)
+      flux_stage_dev_kernel<2><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters);
+    else
+      flux_stage_dev_kernel<3><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters);
+    return cudaGetLastError();
+  }
   if (dm.dim == 2) {
     if (precision == WLSENO_FP32_BULK)
       flux_stage_kernel<float, 2><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);

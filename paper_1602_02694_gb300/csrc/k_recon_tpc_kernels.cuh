@@ -134,10 +134,11 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
 }
 
 // Coefficients and facet values of cell i (FP32-bulk: the polynomial in FP32,
-// ubar_i added in FP64).
+// ubar_i added in FP64), or with fdev set the FP32 deviations ubar - ubar_i.
 template <typename T, int DIM, int M>
 __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
-                                          double* __restrict__ coeffs, double* __restrict__ fvals) {
+                                          double* __restrict__ coeffs, double* __restrict__ fvals,
+                                          float* __restrict__ fdev) {
   constexpr int NP = (DIM + 1) * (DIM == 2 ? 2 : 3);
   if (coeffs) {
 #pragma unroll
@@ -154,14 +155,17 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
     T sh = T(0);
 #pragma unroll
     for (int c = 0; c < M; ++c) sh = fma(x[c], mono[c], sh);
-    fvals[i * NP + pt] = ui + static_cast<double>(sh);
+    if (fdev)
+      fdev[i * NP + pt] = static_cast<float>(sh);
+    else
+      fvals[i * NP + pt] = ui + static_cast<double>(sh);
   }
 }
 
 template <typename T, int DIM, int M>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                 double* __restrict__ coeffs, double* __restrict__ fvals,
+                 double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
                  unsigned long long* __restrict__ counters, TpcWork work, T flag_threshold,
                  T pivot_threshold) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -179,7 +183,7 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   sqrt_free_spread(f, &qmax, &qmin);
   T x[M];
   sqrt_free_solve(f, x);
-  tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals);
+  tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev);
   if (qmax <= flag_threshold * flag_threshold * qmin) return;
   if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
   if (sizeof(T) == 4 && work.refine_list && qmax <= pivot_threshold * pivot_threshold * qmin) {
@@ -216,7 +220,8 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
 template <int DIM, int M, int L, int RPL>
 __global__ void __launch_bounds__(64)
 refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-              double* __restrict__ coeffs, double* __restrict__ fvals, TpcWork work) {
+              double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
+              TpcWork work) {
   constexpr int NF = DIM + 1;
   constexpr int NP = NF * (DIM == 2 ? 2 : 3);
   constexpr int kPerWarp = 32 / L;
@@ -335,7 +340,10 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
         sh = fmaf(xh[c], mono[c], sh);
         sl = fmaf(dl[c], mono[c], sl);
       }
-      fvals[i * NP + pt] = ui + static_cast<double>(sh) + static_cast<double>(sl);
+      if (fdev)
+        fdev[i * NP + pt] = sh + sl;
+      else
+        fvals[i * NP + pt] = ui + static_cast<double>(sh) + static_cast<double>(sl);
     }
   }
 }
@@ -360,7 +368,7 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
   cudaError_t e = cudaMemsetAsync(work.counts, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
-                                                        out.counters, work, flag, pivot);
+                                                        out.fdev, out.counters, work, flag, pivot);
   ++*launches;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -371,7 +379,7 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
     const int64_t want = (dm.N * L + kThreads - 1) / kThreads;
     const unsigned rblocks = static_cast<unsigned>(want < 8 * 152 ? want : 8 * 152);
     refine_kernel<DIM, M, L, RPL>
-        <<<rblocks, kThreads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals, work);
+        <<<rblocks, kThreads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals, out.fdev, work);
     ++*launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -211,7 +211,7 @@ constexpr size_t recon_smem_per_cell() {
 template <typename T, int DIM, int M, int G, int R>
 __device__ __forceinline__ void group_reconstruct_cell(
     const DeviceMesh& dm, const SchemeParams& sp, const double* __restrict__ ubar,
-    double* __restrict__ coeffs, double* __restrict__ fvals,
+    double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
     unsigned long long* __restrict__ counters, unsigned char* smem_raw, int g, int gib,
     int64_t cell, bool valid, bool listed) {
   constexpr int NF = DIM + 1;
@@ -422,9 +422,15 @@ __device__ __forceinline__ void group_reconstruct_cell(
       sh += chi[c] * mono[c];
       sl += clo[c] * mono[c];
     }
-    const double val = ui + static_cast<double>(sh) + static_cast<double>(sl);
-    fvals[cell * NP + pt] = val;
-    finite = finite && isfinite(val);
+    if (fdev) {
+      const float dv = static_cast<float>(sh) + static_cast<float>(sl);
+      fdev[cell * NP + pt] = dv;
+      finite = finite && isfinite(dv);
+    } else {
+      const double val = ui + static_cast<double>(sh) + static_cast<double>(sl);
+      fvals[cell * NP + pt] = val;
+      finite = finite && isfinite(val);
+    }
   }
   if (!finite) atomicAdd(&counters[2], 1ull);
   if (g == 0) {
@@ -436,11 +442,11 @@ __device__ __forceinline__ void group_reconstruct_cell(
 template <typename T, int DIM, int M, int G, int R>
 __global__ void __launch_bounds__(128)
 reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                   double* __restrict__ coeffs, double* __restrict__ fvals,
+                   double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
                    unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t cell = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
-  group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, counters, smem_raw,
+  group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, smem_raw,
                                           threadIdx.x % G, threadIdx.x / G, cell < dm.N ? cell : 0,
                                           cell < dm.N, false);
 }
@@ -450,7 +456,7 @@ reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ub
 template <typename T, int DIM, int M, int G, int R>
 __global__ void __launch_bounds__(128)
 reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                        double* __restrict__ coeffs, double* __restrict__ fvals,
+                        double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
                         unsigned long long* __restrict__ counters, const int* __restrict__ worklist,
                         const int* __restrict__ wl_count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -462,7 +468,7 @@ reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict
     const int idx = base + gib;
     const bool valid = idx < count;
     const int64_t cell = valid ? worklist[idx] : 0;
-    group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, counters, smem_raw,
+    group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, smem_raw,
                                             threadIdx.x % G, gib, cell, valid, true);
   }
 }
@@ -485,7 +491,7 @@ cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp
   const int64_t groups = (dm.N * G + threads - 1) / threads;
   const unsigned blocks = static_cast<unsigned>(groups < 152 * 2 ? groups : 152 * 2);
   reconstruct_list_kernel<T, DIM, M, G, R><<<blocks, threads, smem, s>>>(
-      dm, sp, ubar, out.coeffs, out.fvals, out.counters, worklist, wl_count);
+      dm, sp, ubar, out.coeffs, out.fvals, out.fdev, out.counters, worklist, wl_count);
   return cudaGetLastError();
 }
 
@@ -505,7 +511,7 @@ cudaError_t launch_reconstruct_shape(const DeviceMesh& dm, const SchemeParams& s
   const int64_t total = dm.N * G;
   const unsigned blocks = static_cast<unsigned>((total + threads - 1) / threads);
   reconstruct_kernel<T, DIM, M, G, R>
-      <<<blocks, threads, smem, s>>>(dm, sp, ubar, out.coeffs, out.fvals, out.counters);
+      <<<blocks, threads, smem, s>>>(dm, sp, ubar, out.coeffs, out.fvals, out.fdev, out.counters);
   return cudaGetLastError();
 }
 

@@ -98,9 +98,13 @@ extern "C" wlseno_status wlseno_flux_residual_static(wlseno_ctx* ctx, const doub
     e = cudaMemsetAsync(v.counters, 0, 4 * sizeof(unsigned long long), s);
     for (int c = 0; c < v.n_comp && e == cudaSuccess; ++c) {
       const double* u = ubar + c * v.dm.N;
-      ReconOut out{nullptr, scratch, v.counters};
+      // the same facet-value format as wlseno_flux_residual (FP32 deviations
+      // in FP32-bulk thread-per-cell contexts; they take half the scratch)
+      float* dev = v.dev_facets ? reinterpret_cast<float*>(scratch) : nullptr;
+      ReconOut out{nullptr, dev ? nullptr : scratch, v.counters, dev};
       e = ctx_launch_reconstruct(ctx, u, out, s);
-      if (e == cudaSuccess) e = ctx_launch_flux_residual(ctx, scratch, u, residual + c * v.dm.N, s);
+      if (e == cudaSuccess)
+        e = ctx_launch_flux_residual(ctx, scratch, dev, u, residual + c * v.dm.N, s);
     }
     if (e != cudaSuccess) {
       ctx_set_error(ctx, std::string("wlseno_flux_residual_static: ") + cudaGetErrorString(e));

@@ -57,6 +57,7 @@ struct DeviceMesh {
   const double* centroid;   // [N][dim]
   const double* h;          // [N]
   const double* volume;     // [N]
+  const double* inv_volume; // [N] 1 / volume
   const double* inradius;   // [N]
   const int32_t* mesh_of;   // [N]
   const double* period;     // [n_meshes][3]
@@ -99,8 +100,11 @@ cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double*
 
 struct ReconOut {
   double* coeffs;           // [N][m] or null
-  double* fvals;            // [N][dim+1][nq] (always written)
+  double* fvals;            // [N][dim+1][nq] facet values, or null when fdev is set
   unsigned long long* counters;  // [4]: flagged, rank deficient, nonfinite, spare
+  // FP32-bulk flux path: the facet values as FP32 deviations from the cell
+  // average, value = ubar_i + fdev (written instead of fvals when set)
+  float* fdev = nullptr;    // [N][dim+1][nq]
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -160,8 +164,9 @@ WLSENO_DECLARE_RECON(float, 3, 10)
 
 // Per-cell flux gather + RK stage: out = a*u0 + b*(u + dt*L(u)); with
 // residual_only the output is L(u) itself.
+// fdev (FP32-bulk, scalar equations) replaces fvals when set.
 cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
-                                   const double* fvals, const double* u, const double* u0,
+                                   const double* fvals, const float* fdev, const double* u, const double* u0,
                                    double a, double b, const double* dt_mesh, bool residual_only,
                                    double* out, unsigned long long* counters, cudaStream_t s);
 // dt_mesh[k] = cfl * rmin[k] / lambda_max(mesh k), or dt_fixed when > 0.
@@ -200,12 +205,13 @@ struct CtxView {
   SchemeParams sp;
   unsigned long long* counters;
   const double* dt;
+  bool dev_facets;         // scalar residuals pass facet values as FP32 deviations
 };
 bool ctx_view(const wlseno_ctx* ctx, CtxView* out);
 void ctx_set_error(wlseno_ctx* ctx, const std::string& msg);
 cudaError_t ctx_launch_reconstruct(wlseno_ctx* ctx, const double* ubar, const ReconOut& out,
                                    cudaStream_t s);
-cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const double* ubar,
-                                     double* residual, cudaStream_t s);
+cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const float* fdev,
+                                     const double* ubar, double* residual, cudaStream_t s);
 
 }  // namespace wlseno
