@@ -67,22 +67,27 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // FP32 fold with the rows staged through shared memory.  Each thread copies
-// its own rows asynchronously: the row record (moments + stencil index) four
-// rows ahead, and ubar_j two rows ahead (its index read from the staged
+// its own rows asynchronously: the row record (moments + stencil index) kLeadR
+// rows ahead, and ubar_j kLeadU rows ahead (its index read from the staged
 // record), so neither the HBM latency of the records nor the record -> index
 // -> ubar chain stalls the rotations, and no prefetched row occupies
-// registers.  Commit groups: one per iteration t, holding ubar of row t+2 and
-// the record of row t+4; waiting for all but the newest group therefore
-// guarantees the record and ubar of row t and the record of row t+2.  Record
-// slots cycle mod 5 and ubar slots mod 3, so a copy never lands in a slot
+// registers.  Commit groups: one per iteration t, holding ubar of row t+kLeadU
+// and the record of row t+kLeadR.  Iteration t needs the groups of iterations
+// t-kLeadU (ubar of row t) and t+kLeadU-kLeadR (record of row t+kLeadU), so
+// all but the newest kPending groups must be complete.  Record slots cycle
+// mod kLeadR+1 and ubar slots mod kLeadU+1, so a copy never lands in a slot
 // whose previous row is still to be read.  Threads touch only their own
 // slots: no block barrier.
+constexpr int kLeadR = 6, kLeadU = 3;
+constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (kLeadR - kLeadU - 1);
+static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");
+
 template <int DIM, int M>
 __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const double* __restrict__ ubar,
                                                 int64_t i, double ui, int n, float eh2, float w_centre,
                                                 SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
-  constexpr int kRec = 5, kU = 3;
+  constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
   __shared__ float4 srec[kRec][W4][kTpcThreads];
   __shared__ double su[kU][kTpcThreads];
   const int tid = threadIdx.x;
@@ -98,15 +103,17 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
     cp_async8(&su[u_slot][tid], ubar + j);
   };
   sqrt_free_init(f);
-  for (int t = 0; t < 4 && t < n; ++t) fetch_rec(t, t);
+  for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
   cp_async_commit();
   cp_async_wait<0>();
-  for (int t = 0; t < 2 && t < n; ++t) fetch_u(t, t);
+  for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
-  cp_async_commit();  // empty: the first wait below then covers the ubar copies
+  // empty groups: the first waits below then cover the ubar copies
+#pragma unroll
+  for (int k = 0; k < kPending; ++k) cp_async_commit();
   int sr = 0, sv = 0;  // slots of row t
   for (int t = 0; t < n; ++t) {
-    cp_async_wait<1>();
+    cp_async_wait<kPending>();
     float z[M + 1];
 #pragma unroll
     for (int k = 0; k < W4; ++k) {
@@ -117,11 +124,11 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
         if (4 * k + q < M) z[4 * k + q] = vv[q];
     }
     const double uj = su[sv][tid];
-    const int sr2 = sr + 2 < kRec ? sr + 2 : sr + 2 - kRec;
-    const int sr4 = sr + 4 < kRec ? sr + 4 : sr + 4 - kRec;
-    const int sv2 = sv + 2 < kU ? sv + 2 : sv + 2 - kU;
-    if (t + 2 < n) fetch_u(sr2, sv2);
-    if (t + 4 < n) fetch_rec(t + 4, sr4);
+    const int srU = sr + kLeadU < kRec ? sr + kLeadU : sr + kLeadU - kRec;
+    const int srR = sr + kLeadR < kRec ? sr + kLeadR : sr + kLeadR - kRec;
+    const int svU = sv + kLeadU < kU ? sv + kLeadU : sv + kLeadU - kU;
+    if (t + kLeadU < n) fetch_u(srU, svU);
+    if (t + kLeadR < n) fetch_rec(t + kLeadR, srR);
     cp_async_commit();
     const float dev = static_cast<float>(uj - ui);
     const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
