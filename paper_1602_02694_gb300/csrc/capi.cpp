@@ -449,6 +449,26 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.fgeo = fgeo;
   dm.fpts = fpts;
   dm.fpts32 = fp32;
+  dm.ff32 = nullptr;
+  if (ctx->scheme.precision == WLSENO_FP32_BULK && ctx->scheme.pde != WLSENO_EULER) {
+    const int nf = H.dim + 1;
+    std::vector<FacetF32> ff(static_cast<size_t>(N) * nf);
+    for (size_t k = 0; k < ff.size(); ++k) {
+      const double* G = &H.fgeo[k * 4];
+      double nsum = 0.0, vn = 0.0;
+      for (int a = 0; a < H.dim; ++a) {
+        nsum += G[a];
+        vn += ctx->sp.vel[a] * G[a];
+      }
+      const bool adv = ctx->scheme.pde == WLSENO_ADVECTION;
+      ff[k].pref = adv ? G[3] * vn : 0.5 * G[3] * nsum;
+      ff[k].coef = static_cast<float>(adv ? vn : nsum);
+      ff[k].area = static_cast<float>(G[3]);
+    }
+    FacetF32* d_ff = nullptr;
+    if ((st = upload(ctx, &d_ff, ff))) return st;
+    dm.ff32 = d_ff;
+  }
   const int C = ctx->scheme.n_comp;
   const int NP = (H.dim + 1) * H.nq;
   if ((st = dalloc(ctx, &dm.A64, H.nnz * H.m)) || (st = dalloc(ctx, &dm.A32, H.nnz * H.m)) ||

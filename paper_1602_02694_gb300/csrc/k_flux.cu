@@ -144,44 +144,33 @@ flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fva
 // FP32-bulk flux from facet deviations: the facet values arrive as FP32
 // deviations from their cell averages, value = ubar_c + dev.  Each facet is
 // split at its lower-indexed cell's average u_ref = ubar_L (the same for both
-// cells, so both compute the bitwise-same flux): F(u_ref).n in FP64 plus the
-// FP32 flux of the deviations from u_ref, where the other cell's deviations
-// are shifted by the FP32 rounding of ubar_R - ubar_L.  FP64 work is then one
-// subtraction, the reference flux and the accumulation per facet.
-template <int DIM, int NQ>
-__device__ __forceinline__ double facet_flux_dev(const SchemeParams& sp, const double* geo,
-                                                 float speed, double uref,
+// cells, so both compute the bitwise-same flux): F(u_ref).n |f| in FP64 from
+// the precomputed reference coefficient, plus the FP32 flux of the deviations
+// from u_ref, where the other cell's deviations are shifted by the FP32
+// rounding of ubar_R - ubar_L.  FP64 work per facet: that subtraction, the
+// reference flux and the accumulation.
+template <int NQ>
+__device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, float speed, double uref,
                                                  const float (&dL)[NQ], const float (&dR)[NQ]) {
   const float wq = 1.0f / NQ;
-  double nsum64 = 0.0, vn64 = 0.0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    nsum64 += geo[a];
-    vn64 = fma(sp.vel[a], geo[a], vn64);
-  }
   float fsum = 0.0f;
-  double fref;
-  if (sp.pde == WLSENO_ADVECTION) {
-    const float vn = static_cast<float>(vn64);
+  if (pde == WLSENO_ADVECTION) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) fsum += wq * (0.5f * (vn * (dL[q] + dR[q]) - speed * (dR[q] - dL[q])));
-    fref = vn64 * uref;
-  } else {
-    const float ur = static_cast<float>(uref);
-    const float nsum = static_cast<float>(nsum64);
-    float mx = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) mx = fmaxf(mx, fmaxf(fabsf(ur + dL[q]), fabsf(ur + dR[q])));
-    const float alpha = mx * fabsf(nsum);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {  // (u^2 - u_ref^2)/2 = d (u_ref + d/2)
-      const float fl = nsum * dL[q] * (ur + 0.5f * dL[q]);
-      const float fr = nsum * dR[q] * (ur + 0.5f * dR[q]);
-      fsum += wq * (0.5f * ((fl + fr) - alpha * (dR[q] - dL[q])));
-    }
-    fref = 0.5 * uref * uref * nsum64;
+    for (int q = 0; q < NQ; ++q) fsum += wq * (0.5f * (g.coef * (dL[q] + dR[q]) - speed * (dR[q] - dL[q])));
+    return fma(g.pref, uref, static_cast<double>(g.area * fsum));
   }
-  return geo[3] * (fref + static_cast<double>(fsum));
+  const float ur = static_cast<float>(uref);
+  float mx = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) mx = fmaxf(mx, fmaxf(fabsf(ur + dL[q]), fabsf(ur + dR[q])));
+  const float alpha = mx * fabsf(g.coef);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {  // (u^2 - u_ref^2)/2 = d (u_ref + d/2)
+    const float fl = g.coef * dL[q] * (ur + 0.5f * dL[q]);
+    const float fr = g.coef * dR[q] * (ur + 0.5f * dR[q]);
+    fsum += wq * (0.5f * ((fl + fr) - alpha * (dR[q] - dL[q])));
+  }
+  return fma(g.pref * uref, uref, static_cast<double>(g.area * fsum));
 }
 
 template <int DIM>
@@ -228,7 +217,7 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
       dL[q] = owner ? di[q] : dj[q];
       dR[q] = (owner ? dj[q] : di[q]) + jump;
     }
-    const double flux = facet_flux_dev<DIM, NQ>(sp, dm.fgeo + (i * NF + f) * 4, speed, uL, dL, dR);
+    const double flux = facet_flux_dev<NQ>(sp.pde, dm.ff32[i * NF + f], speed, uL, dL, dR);
     acc += owner ? flux : -flux;
   }
   const double L = -acc * dm.inv_volume[i];

@@ -48,6 +48,17 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
 // ---------------------------------------------------------------------------
 // device-side views handed to the kernel launchers
 // ---------------------------------------------------------------------------
+// Per-facet coefficients of the FP32-bulk scalar flux, in the orientation of
+// the facet's lower-indexed cell (identical in both cells' records): the FP64
+// reference coefficient (Burgers: |f| (n_1+..+n_d)/2, advection: |f| v.n),
+// the FP32 normal factor (Burgers: n_1+..+n_d, advection: v.n) and the FP32
+// facet measure |f|.
+struct FacetF32 {
+  double pref;
+  float coef;
+  float area;
+};
+
 struct DeviceMesh {
   int dim, p, m, nq;
   int64_t N, nnz;
@@ -75,6 +86,7 @@ struct DeviceMesh {
   // (t*N + i)*rec_width floats holds the m moments of row t of cell i, then
   // the stencil index (int32 bits), then zero padding to a 16-byte multiple
   float* rec32;             // [nmax][N][rec_width]
+  const FacetF32* ff32;     // [N][dim+1] FP32-bulk scalar flux coefficients (else null)
   int rec_width;            // round_up(m + 1, 4)
 };
 
