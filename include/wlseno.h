@@ -101,8 +101,11 @@ typedef struct {
  *             indicator), e.g. 1e-2; h is the centre cell's mean edge length.
  * alpha_c:    alpha > 1 of the centre weight, Eq. (weight), e.g. 1.5.
  * rank_tol:   numerical rank: #{k : |R_kk| > rank_tol |R_11|}, e.g. 1e-10.
- * kappa_flag: FP32-bulk mode: cells whose |R_11|/|R_rr| exceeds this get one
- *             FP64-residual refinement sweep (e.g. 1e3).
+ * kappa_flag: FP32-bulk mode: cells whose conditioning estimate (the spread
+ *             max_k/min_k of the column-scaled diagonal |R_kk| / ||R_:,k|| of
+ *             the factor of W A) exceeds this get one FP64-residual
+ *             refinement sweep (e.g. 1e3); above 1e5 they take the pivoted
+ *             path below.
  * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and flux
  *             in FP32; moments, residual accumulation and RK update in FP64).
  * gamma:      WLSENO_EULER only: ratio of specific heats (e.g. 1.4).
@@ -139,9 +142,12 @@ typedef struct {
   int rows_per_lane;
 } wlseno_info;
 
-/* Kernel kinds of the per-kind launch counts and timings. */
+/* Kernel kinds of the per-kind launch counts and timings.  RECONSTRUCT is
+ * the main reconstruction kernel; FIXUP the follow-ups that redo the cells it
+ * flags (refinement sweep, pivoted path). */
 enum { WLSENO_KERNEL_MOMENTS = 0, WLSENO_KERNEL_RECONSTRUCT = 1, WLSENO_KERNEL_FLUX = 2,
-       WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_N_KERNEL_KINDS = 5 };
+       WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_KERNEL_FIXUP = 5,
+       WLSENO_N_KERNEL_KINDS = 6 };
 
 typedef struct {
   int64_t flagged_cells;   /* cells flagged ill-conditioned (last call)         */
@@ -184,6 +190,13 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
 wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream);
 
 /* WLS-ENO reconstruction (Sec. 3.1, Sec. 3.2, Sec. 3.3.2).
+ * Solver: each cell's weighted rows are folded into a QR factor of W A
+ * without pivoting; when its conditioning estimate stays below the flag
+ * threshold (FP32-bulk: kappa_flag; FP64: 1e6) the system has full rank and
+ * this is the least-squares solution the paper's pivoted QR returns.  Other
+ * cells are redone by Householder QR with column pivoting of W A S, the rank
+ * rule of rank_tol and the basic solution (Sec. 3.3.2), or, in FP32-bulk
+ * between kappa_flag and 1e5, refined once with the FP64 residual.
  * ubar:   [n_comp][n_cells] cell averages, host or device.
  * coeffs: [n_comp][n_cells][m] output, host or device: h-normalised Taylor
  *         coefficients d_kappa = h_i^|kappa| d^kappa u(x_i) (kappa ordered by

