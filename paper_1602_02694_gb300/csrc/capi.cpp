@@ -35,9 +35,8 @@ struct wlseno_ctx {
   double* d_coef = nullptr;      // [C][N][m] staging for host coefficient output
   double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
   int* d_wl = nullptr;           // [N] cells for the pivoted lane-group path
-  int* d_wl_count = nullptr;     // [2] lengths of d_wl and d_rl
-  int* d_rl = nullptr;           // [N] cells for the FP64-residual refinement (FP32-bulk)
-  float* d_rbuf = nullptr;       // [refine_fields(m)][N] their FP32 factors
+  int* d_wl_count = nullptr;     // [2] lengths of d_wl and of the refine records
+  float* d_rbuf = nullptr;       // [N][refine_record_floats(m)] FP32-bulk refine records
   float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
@@ -206,7 +205,7 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
     return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rl, ctx->d_rbuf};
+    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf};
     const bool d2m6 = dm.dim == 2 && dm.m == 6, d2m10 = dm.dim == 2 && dm.m == 10,
                d3m10 = dm.dim == 3 && dm.m == 10;
     if (d2m6)
@@ -501,8 +500,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (st = dalloc(ctx, &ctx->d_wl_count, 2)))
     return st;
   if (ctx->scheme.precision == WLSENO_FP32_BULK &&
-      ((st = dalloc(ctx, &ctx->d_rl, N)) || (st = dalloc(ctx, &ctx->d_fdev, N * NP)) ||
-       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_fields(H.m)) * N))))
+      ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) ||
+       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N))))
     return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");

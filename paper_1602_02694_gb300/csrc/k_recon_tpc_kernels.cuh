@@ -193,22 +193,29 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev);
   if (qmax <= flag_threshold * flag_threshold * qmin) return;
   if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
-  if (sizeof(T) == 4 && work.refine_list && qmax <= pivot_threshold * pivot_threshold * qmin) {
-    // keep the FP32 factor for the refinement kernel
-    const int slot = atomicAdd(&work.counts[1], 1);
-    work.refine_list[slot] = static_cast<int>(i);
-    float* buf = work.refine_buf + slot;
-    const int64_t N = dm.N;
+  if (sizeof(T) == 4 && work.refine_buf && qmax <= pivot_threshold * pivot_threshold * qmin) {
+    // keep the FP32 factor for the refinement kernel: one contiguous record
+    constexpr int RW = refine_record_floats(M);
+    float v[RW];
+    v[0] = __int_as_float(static_cast<int>(i));
+    v[1] = __int_as_float(dm.st_ptr[i]);
+    v[2] = __int_as_float(n);
+    v[3] = 0.0f;
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-      buf[c * N] = static_cast<float>(x[c]);
-      buf[(M + c) * N] = static_cast<float>(f.d[c]);
+      v[4 + c] = static_cast<float>(x[c]);
+      v[4 + M + c] = static_cast<float>(f.d[c]);
     }
 #pragma unroll
     for (int k = 0; k < M; ++k)
 #pragma unroll
-      for (int j = k + 1; j < M; ++j)
-        buf[(2 * M + strict_upper_index(M, k, j)) * N] = static_cast<float>(f.U[k][j]);
+      for (int j = k + 1; j < M; ++j) v[4 + 2 * M + strict_upper_index(M, k, j)] = static_cast<float>(f.U[k][j]);
+#pragma unroll
+    for (int c = 4 + 2 * M + M * (M - 1) / 2; c < RW; ++c) v[c] = 0.0f;
+    const int slot = atomicAdd(&work.counts[1], 1);
+    float4* rec = reinterpret_cast<float4*>(work.refine_buf + static_cast<int64_t>(slot) * RW);
+#pragma unroll
+    for (int q = 0; q < RW / 4; ++q) rec[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else {
     work.group_list[atomicAdd(&work.counts[0], 1)] = static_cast<int>(i);
   }
@@ -233,40 +240,56 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
   constexpr int NP = NF * (DIM == 2 ? 2 : 3);
   constexpr int kPerWarp = 32 / L;
   const int count = work.counts[1];
-  const int64_t N = dm.N;
   const int lane = threadIdx.x % L;
   const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / 32;
   const int64_t warps = gridDim.x * static_cast<int64_t>(blockDim.x) / 32;
+  constexpr int RW = refine_record_floats(M);
   for (int64_t base = warp * kPerWarp; base < count; base += warps * kPerWarp) {
     const int64_t slot = base + (threadIdx.x % 32) / L;
     const bool valid = slot < count;
-    const int64_t i = valid ? work.refine_list[slot] : 0;
-    const int beg = dm.st_ptr[i];
-    const int n = valid ? dm.st_ptr[i + 1] - beg : 0;
-    // all loads of this lane's rows first, from the CSR layout: a cell's rows
-    // are contiguous, so the group's loads of one row set share cache lines
+    // the cell's record (the same address for all L lanes: broadcast loads)
+    float r[RW];
+    {
+      const float4* rec = reinterpret_cast<const float4*>(work.refine_buf + (valid ? slot : 0) * RW);
+#pragma unroll
+      for (int q = 0; q < RW / 4; ++q) {
+        const float4 v = rec[q];
+        r[4 * q] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
+      }
+    }
+    const int64_t i = valid ? __float_as_int(r[0]) : 0;
+    const int beg = __float_as_int(r[1]);
+    const int n = valid ? __float_as_int(r[2]) : 0;
+    // all loads of this lane's rows next, from the CSR layout: a cell's rows
+    // are contiguous (16-byte aligned), so the group's loads share cache lines
     int64_t jrow[RPL];
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      const int t = lane + r * L;
-      jrow[r] = t < n ? dm.st_idx[beg + t] : i;
+    for (int q = 0; q < RPL; ++q) {
+      const int t = lane + q * L;
+      jrow[q] = t < n ? dm.st_idx[beg + t] : i;
     }
     double a[RPL][M];
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      const int t = lane + r * L;
-      const double* row = dm.A64 + static_cast<int64_t>(beg + t) * M;
+    for (int q = 0; q < RPL; ++q) {
+      const int t = lane + q * L;
+      const double2* row = reinterpret_cast<const double2*>(dm.A64 + static_cast<int64_t>(beg + t) * M);
 #pragma unroll
-      for (int c = 0; c < M; ++c) a[r][c] = t < n ? row[c] : 0.0;
+      for (int c = 0; c < M; c += 2) {
+        const double2 v = t < n ? row[c / 2] : make_double2(0.0, 0.0);
+        a[q][c] = v.x;
+        a[q][c + 1] = v.y;
+      }
     }
     const double ui = ubar[i];
     double uj[RPL];
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) uj[r] = ubar[jrow[r]];
-    const float* buf = work.refine_buf + (valid ? slot : 0);
+    for (int q = 0; q < RPL; ++q) uj[q] = ubar[jrow[q]];
     double x[M];
 #pragma unroll
-    for (int c = 0; c < M; ++c) x[c] = static_cast<double>(buf[c * N]);
+    for (int c = 0; c < M; ++c) x[c] = static_cast<double>(r[4 + c]);
     // weights of the FP64 problem (Sec. 3.1.2), to FP32 relative accuracy:
     // only the residual needs FP64 (its cancellation), A^T W^2 r does not
     const double hi = dm.h[i];
@@ -284,21 +307,21 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
 #pragma unroll
     for (int c = 0; c < M; ++c) g[c] = 0.0f;
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      const int t = lane + r * L;
-      const double dev = uj[r] - ui;
+    for (int q = 0; q < RPL; ++q) {
+      const int t = lane + q * L;
+      const double dev = uj[q] - ui;
       const float devf = static_cast<float>(dev);
       const float beta = t == 0 ? bmin : fmaf(devf, devf, e);
       const float w = (t == 0 ? static_cast<float>(sp.alpha_c) * e : e) / beta;
       double fit0 = 0.0, fit1 = 0.0;
 #pragma unroll
       for (int c = 0; c < M; c += 2) {
-        fit0 = fma(a[r][c], x[c], fit0);
-        if (c + 1 < M) fit1 = fma(a[r][c + 1], x[c + 1], fit1);
+        fit0 = fma(a[q][c], x[c], fit0);
+        if (c + 1 < M) fit1 = fma(a[q][c + 1], x[c + 1], fit1);
       }
       const float wr = t < n ? w * w * static_cast<float>(dev - (fit0 + fit1)) : 0.0f;
 #pragma unroll
-      for (int c = 0; c < M; ++c) g[c] = fmaf(wr, static_cast<float>(a[r][c]), g[c]);
+      for (int c = 0; c < M; ++c) g[c] = fmaf(wr, static_cast<float>(a[q][c]), g[c]);
     }
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1)
@@ -311,21 +334,21 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
     for (int k = 0; k < M; ++k) {
       float v = g[k];
 #pragma unroll
-      for (int q = 0; q < k; ++q) v = fmaf(-buf[(2 * M + strict_upper_index(M, q, k)) * N], dl[q], v);
+      for (int q = 0; q < k; ++q) v = fmaf(-r[4 + 2 * M + strict_upper_index(M, q, k)], dl[q], v);
       dl[k] = v;
     }
 #pragma unroll
-    for (int k = 0; k < M; ++k) dl[k] /= buf[(M + k) * N];
+    for (int k = 0; k < M; ++k) dl[k] /= r[4 + M + k];
 #pragma unroll
     for (int k = M - 1; k >= 0; --k) {
       float v = dl[k];
 #pragma unroll
-      for (int q = k + 1; q < M; ++q) v = fmaf(-buf[(2 * M + strict_upper_index(M, k, q)) * N], dl[q], v);
+      for (int q = k + 1; q < M; ++q) v = fmaf(-r[4 + 2 * M + strict_upper_index(M, k, q)], dl[q], v);
       dl[k] = v;
     }
     float xh[M];
 #pragma unroll
-    for (int c = 0; c < M; ++c) xh[c] = buf[c * N];
+    for (int c = 0; c < M; ++c) xh[c] = r[4 + c];
     if (coeffs) {
 #pragma unroll
       for (int c = 0; c < M; ++c)
@@ -385,7 +408,7 @@ cudaError_t launch_recon_fixup(const DeviceMesh& dm, const SchemeParams& sp, con
   *launches = 0;
   cudaError_t e = cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (!work.refine_list) return cudaErrorInvalidValue;
+    if (!work.refine_buf) return cudaErrorInvalidValue;
     // 16 lanes x 4 rows: every stencil the thread-per-cell path accepts (<= 64)
     constexpr int L = 16, RPL = 4, kThreads = 64;
     const int64_t want = (dm.N * L + kThreads - 1) / kThreads;

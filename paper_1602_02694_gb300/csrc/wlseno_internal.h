@@ -126,17 +126,20 @@ cudaError_t launch_ell_copy(const DeviceMesh& dm, cudaStream_t s);
 
 // Work lists of the thread-per-cell kernels.  Flagged cells go either to the
 // pivoted lane-group path (group_list) or, in FP32-bulk when only moderately
-// ill-conditioned, to the thread-level FP64-residual refinement (refine_list),
-// which reuses the FP32 factor the main kernel left in refine_buf.
+// ill-conditioned, to the thread-level FP64-residual refinement, which reuses
+// the FP32 factor the main kernel leaves in one refine record per cell.
 struct TpcWork {
   int* group_list;          // [N]
-  int* counts;              // [2]: lengths of group_list and refine_list
-  int* refine_list;         // [N] (FP32-bulk contexts; else null)
-  float* refine_buf;        // [refine_fields(m)][N]: x, d, strict upper U
+  int* counts;              // [2]: lengths of group_list and of the refine records
+  float* refine_buf;        // [N][refine_record_floats(m)] (FP32-bulk contexts; else null)
 };
 
-// Floats per refine-listed cell: solution x (m), D (m), strict upper U (m(m-1)/2).
-__host__ __device__ constexpr int refine_fields(int m) { return 2 * m + m * (m - 1) / 2; }
+// One refine record (16-byte aligned, read with 16-byte loads): cell index,
+// first CSR row, row count and a zero (as int32), then the solution x (m),
+// D (m) and the strict upper triangle of U (m(m-1)/2), zero padded.
+__host__ __device__ constexpr int refine_record_floats(int m) {
+  return (4 + 2 * m + m * (m - 1) / 2 + 3) / 4 * 4;
+}
 
 // Thread-per-cell reconstruction: the main kernel, then the follow-ups on
 // the cells it lists (*launches receives their number).
