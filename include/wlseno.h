@@ -144,7 +144,8 @@ typedef struct {
 
 /* Kernel kinds of the per-kind launch counts and timings.  RECONSTRUCT is
  * the main reconstruction kernel; FIXUP the follow-ups that redo the cells it
- * flags (refinement sweep, pivoted path). */
+ * flags (refinement sweep, pivoted path); DT the per-step preparation (CFL
+ * time step and, in FP32-bulk, the FP32 split of the state). */
 enum { WLSENO_KERNEL_MOMENTS = 0, WLSENO_KERNEL_RECONSTRUCT = 1, WLSENO_KERNEL_FLUX = 2,
        WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_KERNEL_FIXUP = 5,
        WLSENO_N_KERNEL_KINDS = 6 };

@@ -38,6 +38,7 @@ struct wlseno_ctx {
   int* d_wl_count = nullptr;     // [2] lengths of d_wl and of the refine records
   float* d_rbuf = nullptr;       // [N][refine_record_floats(m)] FP32-bulk refine records
   float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
+  float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk)
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
   cudaStream_t cap_stream = nullptr;
@@ -194,18 +195,33 @@ void reset_kind_stats(wlseno_ctx* ctx) {
 
 // fvals receives the facet values, or with fdev set (FP32-bulk) their FP32
 // deviations from the cell averages instead.
+// FP32 pairs of a state (the scratch slot of d_pair), counted as a per-step
+// preparation kernel.
+cudaError_t split_state(wlseno_ctx* ctx, const double* u, float2* pair, cudaStream_t s) {
+  KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
+  cudaError_t e = launch_split_pairs(u, pair, ctx->dm.N, s);
+  scope.done(e == cudaSuccess ? 1 : 0);
+  return e;
+}
+
+// pair: the FP32 pairs of ubar for the FP32-bulk thread-per-cell kernel; when
+// null they are made here, in the scratch slot of d_pair.
 cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
-                            cudaStream_t s, float* fdev = nullptr) {
+                            cudaStream_t s, float* fdev = nullptr, const float2* pair = nullptr) {
   ReconOut out{coeffs, fdev ? nullptr : fvals, ctx->d_counters, fdev};
   const DeviceMesh& dm = ctx->dm;
   const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
   cudaError_t e = cudaErrorInvalidValue;
+  if (f32 && ctx->G == 1 && !pair) {
+    if ((e = split_state(ctx, ubar, ctx->d_pair, s)) != cudaSuccess) return e;
+    pair = ctx->d_pair;
+  }
   // the work-list lengths start at zero (outside the timed kernel scope)
   if (ctx->G == 1 && (e = cudaMemsetAsync(ctx->d_wl_count, 0, 2 * sizeof(int), s)) != cudaSuccess)
     return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf};
+    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pair};
     const bool d2m6 = dm.dim == 2 && dm.m == 6, d2m10 = dm.dim == 2 && dm.m == 10,
                d3m10 = dm.dim == 3 && dm.m == 10;
     if (d2m6)
@@ -248,10 +264,11 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
 
 cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, const double* u0,
                      double a, double b, bool residual_only, double* out, cudaStream_t s,
-                     const float* fdev = nullptr) {
+                     const float* fdev = nullptr, const float2* pin = nullptr, float2* pout = nullptr) {
   KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
   cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, fdev, u, u0,
-                                         a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s);
+                                         a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s,
+                                         pin, pout);
   scope.done(e == cudaSuccess ? 1 : 0);
   return e;
 }
@@ -260,8 +277,11 @@ cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, cons
 // L(u)), or L(u) itself.  Euler reconstructs every component, applies the
 // positivity fix-up and runs the coupled flux; scalar equations go component
 // by component.
+// FP32-bulk scalar path: pin holds the FP32 pairs of u (else they are made
+// here), pout (may be null) receives those of out.
 cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double a, double b,
-                      bool residual_only, double* out, cudaStream_t s) {
+                      bool residual_only, double* out, cudaStream_t s, const float2* pin = nullptr,
+                      float2* pout = nullptr) {
   const int64_t N = ctx->dm.N;
   const int C = ctx->scheme.n_comp;
   const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
@@ -281,10 +301,18 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
   // FP32-bulk thread-per-cell: facet values travel as FP32 deviations
   float* fdev = ctx->G == 1 ? ctx->d_fdev : nullptr;
   for (int c = 0; c < C && e == cudaSuccess; ++c) {
-    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s, fdev);
+    const float2* pc = nullptr;
+    if (fdev) {
+      if (pin) {
+        pc = pin + c * N;
+      } else if ((e = split_state(ctx, u + c * N, ctx->d_pair, s)) == cudaSuccess) {
+        pc = ctx->d_pair;
+      }
+    }
+    if (e == cudaSuccess) e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s, fdev, pc);
     if (e == cudaSuccess)
       e = flux_one(ctx, ctx->d_fvals, u + c * N, u0 ? u0 + c * N : nullptr, a, b, residual_only,
-                   out + c * N, s, fdev);
+                   out + c * N, s, fdev, pc, fdev && pout ? pout + c * N : nullptr);
   }
   return e;
 }
@@ -324,9 +352,12 @@ cudaError_t ctx_launch_reconstruct(wlseno_ctx* ctx, const double* ubar, const Re
   return reconstruct_one(ctx, ubar, out.coeffs, out.fvals, s, out.fdev);
 }
 
+// With fdev, the pairs of ubar are the ones ctx_launch_reconstruct just made
+// in the scratch slot (same ubar, same stream).
 cudaError_t ctx_launch_flux_residual(wlseno_ctx* ctx, const double* fvals, const float* fdev,
                                      const double* ubar, double* residual, cudaStream_t s) {
-  return flux_one(ctx, fvals, ubar, nullptr, 0.0, 1.0, true, residual, s, fdev);
+  return flux_one(ctx, fvals, ubar, nullptr, 0.0, 1.0, true, residual, s, fdev,
+                  fdev ? ctx->d_pair : nullptr);
 }
 
 }  // namespace wlseno
@@ -500,7 +531,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (st = dalloc(ctx, &ctx->d_wl_count, 2)))
     return st;
   if (ctx->scheme.precision == WLSENO_FP32_BULK &&
-      ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) ||
+      ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) || (st = dalloc(ctx, &ctx->d_pair, 3 * C * N)) ||
        (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N))))
     return st;
   cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
@@ -648,9 +679,13 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
     double* k1 = ctx->d_k1;
     double* k2 = ctx->d_k2;
-    if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st)) != cudaSuccess ||
-        (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st)) != cudaSuccess ||
-        (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st)) != cudaSuccess)
+    // FP32 pairs: made for u at stage 1, written by the flux for k1 and k2
+    const int64_t CN = static_cast<int64_t>(ctx->scheme.n_comp) * ctx->dm.N;
+    float2* p1 = ctx->d_pair ? ctx->d_pair + CN : nullptr;
+    float2* p2 = ctx->d_pair ? ctx->d_pair + 2 * CN : nullptr;
+    if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st, nullptr, p1)) != cudaSuccess ||
+        (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st, p1, p2)) != cudaSuccess ||
+        (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st, p2, nullptr)) != cudaSuccess)
       return err;
     return cudaSuccess;
   };
@@ -865,8 +900,10 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   double* k1 = ctx->d_k1;
   double* k2 = ctx->d_k2;
   // (the same launches as the forward step, so the stages match it bitwise)
-  if ((e = stage_all(ctx, u, u, 0.0, 1.0, false, k1, s)) != cudaSuccess ||
-      (e = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, s)) != cudaSuccess)
+  const int64_t CN = static_cast<int64_t>(ctx->scheme.n_comp) * ctx->dm.N;
+  float2* p1 = ctx->d_pair ? ctx->d_pair + CN : nullptr;
+  if ((e = stage_all(ctx, u, u, 0.0, 1.0, false, k1, s, nullptr, p1)) != cudaSuccess ||
+      (e = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, s, p1, nullptr)) != cudaSuccess)
     return cuda_fail(ctx, e, "adjoint: forward stages");
   auto vjp = [&](const double* state, const double* lam, double* out) -> cudaError_t {
     cudaError_t err = reconstruct_one(ctx, state, nullptr, ctx->d_fvals, s);

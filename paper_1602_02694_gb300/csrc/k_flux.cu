@@ -144,14 +144,14 @@ flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fva
 // FP32-bulk flux from facet deviations: the facet values arrive as FP32
 // deviations from their cell averages, value = ubar_c + dev.  Each facet is
 // split at its lower-indexed cell's average u_ref = ubar_L (the same for both
-// cells, so both compute the bitwise-same flux): F(u_ref).n |f| in FP64 from
+// cells, so both compute the bitwise-same flux; ur = fl32(u_ref)): F(u_ref).n |f| in FP64 from
 // the precomputed reference coefficient, plus the FP32 flux of the deviations
 // from u_ref, where the other cell's deviations are shifted by the FP32
 // rounding of ubar_R - ubar_L.  FP64 work per facet: that subtraction, the
 // reference flux and the accumulation.
 template <int NQ>
 __device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, float speed, double uref,
-                                                 const float (&dL)[NQ], const float (&dR)[NQ]) {
+                                                 float ur, const float (&dL)[NQ], const float (&dR)[NQ]) {
   const float wq = 1.0f / NQ;
   float fsum = 0.0f;
   if (pde == WLSENO_ADVECTION) {
@@ -159,7 +159,6 @@ __device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, flo
     for (int q = 0; q < NQ; ++q) fsum += wq * (0.5f * (g.coef * (dL[q] + dR[q]) - speed * (dR[q] - dL[q])));
     return fma(g.pref, uref, static_cast<double>(g.area * fsum));
   }
-  const float ur = static_cast<float>(uref);
   float mx = 0.0f;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) mx = fmaxf(mx, fmaxf(fabsf(ur + dL[q]), fabsf(ur + dR[q])));
@@ -178,7 +177,8 @@ __global__ void __launch_bounds__(256)
 flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ fdev,
                       const double* __restrict__ u, const double* __restrict__ u0, double a, double b,
                       const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
-                      unsigned long long* __restrict__ counters) {
+                      unsigned long long* __restrict__ counters, const float2* __restrict__ pin,
+                      float2* __restrict__ pout) {
   constexpr int NF = DIM + 1;
   constexpr int NQ = DIM == 2 ? 2 : 3;
   constexpr int NP = NF * NQ;
@@ -189,6 +189,7 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
   for (int q = 0; q < DIM; ++q) speed2 += static_cast<float>(sp.vel[q] * sp.vel[q]);
   const float speed = sqrtf(speed2);
   const double ui = u[i];
+  const float2 pi = pin ? pin[i] : make_float2(0.0f, 0.0f);
   double acc = 0.0;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -197,6 +198,7 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
 #pragma unroll
     for (int q = 0; q < NQ; ++q) di[q] = fdev[i * NP + f * NQ + q];
     double uj = ui;
+    float2 pj = pi;
     bool owner = true;
     if (nb >= 0) {
       const int64_t j = nb >> 2;
@@ -204,20 +206,24 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
 #pragma unroll
       for (int q = 0; q < NQ; ++q) dj[q] = fdev[j * NP + f2 * NQ + q];
       uj = u[j];
+      if (pin) pj = pin[j];
       owner = i < j;
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) dj[q] = di[q];
     }
     const double uL = owner ? ui : uj;
-    const float jump = static_cast<float>((owner ? uj : ui) - uL);
+    // ubar_R - ubar_L in FP32: from the pairs when given (no FP64 work)
+    const float2 pL = owner ? pi : pj, pR = owner ? pj : pi;
+    const float jump = pin ? (pR.x - pL.x) + (pR.y - pL.y) : static_cast<float>((owner ? uj : ui) - uL);
     float dL[NQ], dR[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       dL[q] = owner ? di[q] : dj[q];
       dR[q] = (owner ? dj[q] : di[q]) + jump;
     }
-    const double flux = facet_flux_dev<NQ>(sp.pde, dm.ff32[i * NF + f], speed, uL, dL, dR);
+    const double flux = facet_flux_dev<NQ>(sp.pde, dm.ff32[i * NF + f], speed, uL,
+                                                pin ? pL.x : static_cast<float>(uL), dL, dR);
     acc += owner ? flux : -flux;
   }
   const double L = -acc * dm.inv_volume[i];
@@ -229,7 +235,19 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
     res = a * u0[i] + b * (ui + dt * L);
   }
   out[i] = res;
+  if (pout) {
+    const float hi = __double2float_rn(res);
+    pout[i] = make_float2(hi, __double2float_rn(res - static_cast<double>(hi)));
+  }
   if (!isfinite(res)) atomicAdd(&counters[2], 1ull);
+}
+
+__global__ void split_pairs_kernel(const double* __restrict__ u, float2* __restrict__ pair, int64_t n) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= n) return;
+  const double v = u[k];
+  const float hi = __double2float_rn(v);
+  pair[k] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
 }
 
 // Largest |ubar| per mesh, as the bits of a non-negative double (their
@@ -278,15 +296,17 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
                                    const double* fvals, const float* fdev, const double* u,
                                    const double* u0, double a, double b, const double* dt_mesh,
                                    bool residual_only, double* out, unsigned long long* counters,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const float2* pin, float2* pout) {
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   const int ro = residual_only ? 1 : 0;
   if (fdev) {
     if (dm.dim == 2)
-      flux_stage_dev_kernel<2><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters);
+      flux_stage_dev_kernel<2><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
+                                                          pin, residual_only ? nullptr : pout);
     else
-      flux_stage_dev_kernel<3><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters);
+      flux_stage_dev_kernel<3><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
+                                                          pin, residual_only ? nullptr : pout);
     return cudaGetLastError();
   }
   if (dm.dim == 2) {
@@ -300,6 +320,12 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
     else
       flux_stage_kernel<double, 3><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(const double* u, float2* pair, int64_t n, cudaStream_t s) {
+  const int threads = 256;
+  split_pairs_kernel<<<static_cast<unsigned>((n + threads - 1) / threads), threads, 0, s>>>(u, pair, n);
   return cudaGetLastError();
 }
 

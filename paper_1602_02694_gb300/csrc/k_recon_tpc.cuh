@@ -155,4 +155,27 @@ __device__ __forceinline__ void tpc_weights(const DeviceMesh& dm, const SchemePa
   *w_centre = static_cast<T>(sp.alpha_c) * e / bmin;
 }
 
+// The same weights in FP32-bulk from the FP32 pairs of ubar (no FP64 work
+// but eps h^2).
+template <int DIM>
+__device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const SchemeParams& sp,
+                                                 const float2* __restrict__ upair, int64_t i, float2 pi,
+                                                 float* eh2, float* w_centre) {
+  constexpr int NF = DIM + 1;
+  const double hi = dm.h[i];
+  const float e = static_cast<float>(sp.eps * hi * hi);
+  float bmin = INFINITY;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int nb = dm.nbr[i * NF + f];
+    if (nb >= 0) {
+      const float2 pj = upair[nb >> 2];
+      const float d = (pj.x - pi.x) + (pj.y - pi.y);
+      bmin = fminf(bmin, d * d + e);
+    }
+  }
+  *eh2 = e;
+  *w_centre = static_cast<float>(sp.alpha_c) * e / bmin;
+}
+
 }  // namespace wlseno

@@ -68,7 +68,7 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // FP32 fold with the rows staged through shared memory.  Each thread copies
 // its own rows asynchronously: the row record (moments + stencil index) kLeadR
-// rows ahead, and ubar_j kLeadU rows ahead (its index read from the staged
+// rows ahead, and the FP32 pair of ubar_j kLeadU rows ahead (its index read from the staged
 // record), so neither the HBM latency of the records nor the record -> index
 // -> ubar chain stalls the rotations, and no prefetched row occupies
 // registers.  Commit groups: one per iteration t, holding ubar of row t+kLeadU
@@ -83,13 +83,13 @@ constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (
 static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");
 
 template <int DIM, int M>
-__device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const double* __restrict__ ubar,
-                                                int64_t i, double ui, int n, float eh2, float w_centre,
+__device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const float2* __restrict__ upair,
+                                                int64_t i, float2 pi, int n, float eh2, float w_centre,
                                                 SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
   constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
   __shared__ float4 srec[kRec][W4][kTpcThreads];
-  __shared__ double su[kU][kTpcThreads];
+  __shared__ float2 su[kU][kTpcThreads];
   const int tid = threadIdx.x;
   const int64_t N = dm.N;
   const float4* rec = reinterpret_cast<const float4*>(dm.rec32);
@@ -100,7 +100,7 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
   };
   auto fetch_u = [&](int rec_slot, int u_slot) {
     const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][tid])[M % 4]);
-    cp_async8(&su[u_slot][tid], ubar + j);
+    cp_async8(&su[u_slot][tid], upair + j);
   };
   sqrt_free_init(f);
   for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
@@ -123,14 +123,14 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const doub
       for (int q = 0; q < 4; ++q)
         if (4 * k + q < M) z[4 * k + q] = vv[q];
     }
-    const double uj = su[sv][tid];
+    const float2 pj = su[sv][tid];
     const int srU = sr + kLeadU < kRec ? sr + kLeadU : sr + kLeadU - kRec;
     const int srR = sr + kLeadR < kRec ? sr + kLeadR : sr + kLeadR - kRec;
     const int svU = sv + kLeadU < kU ? sv + kLeadU : sv + kLeadU - kU;
     if (t + kLeadU < n) fetch_u(srU, svU);
     if (t + kLeadR < n) fetch_rec(t + kLeadR, srR);
     cp_async_commit();
-    const float dev = static_cast<float>(uj - ui);
+    const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
     const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
     z[M] = dev;
     sqrt_free_fold(f, z, w * w);
@@ -180,12 +180,15 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   const int n = dm.st_ptr[i + 1] - dm.st_ptr[i];
   const double ui = ubar[i];
   T eh2, wc;
-  tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
   SqrtFreeQR<T, M> f;
-  if constexpr (sizeof(T) == 4)
-    tpc_fold_staged<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
-  else
+  if constexpr (sizeof(T) == 4) {
+    const float2 pi = work.upair[i];
+    tpc_weights_pair<DIM>(dm, sp, work.upair, i, pi, &eh2, &wc);
+    tpc_fold_staged<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
+  } else {
+    tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
     tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
+  }
   T qmax, qmin;
   sqrt_free_spread(f, &qmax, &qmin);
   T x[M];
@@ -394,6 +397,7 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
   const bool f32 = sizeof(T) == 4;
   const T flag = f32 ? static_cast<T>(sp.kappa_flag) : T(1e6);
   const T pivot = f32 ? static_cast<T>(kRefinePivotBound) : flag;
+  if (f32 && !work.upair) return cudaErrorInvalidValue;
   recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
                                                         out.fdev, out.counters, work, flag, pivot);
   return cudaGetLastError();

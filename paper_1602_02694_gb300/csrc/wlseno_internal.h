@@ -132,7 +132,14 @@ struct TpcWork {
   int* group_list;          // [N]
   int* counts;              // [2]: lengths of group_list and of the refine records
   float* refine_buf;        // [N][refine_record_floats(m)] (FP32-bulk contexts; else null)
+  // FP32-bulk input: ubar split into FP32 pairs (hi, lo), hi = fl32(ubar),
+  // lo = fl32(ubar - hi), so ubar_j - ubar_i = (hi_j - hi_i) + (lo_j - lo_i)
+  // to FP32 accuracy without FP64 arithmetic (required when refine_buf is set)
+  const float2* upair;      // [N]
 };
+
+// pair[k] = (fl32(u[k]), fl32(u[k] - fl32(u[k]))) for k < n.
+cudaError_t launch_split_pairs(const double* u, float2* pair, int64_t n, cudaStream_t s);
 
 // One refine record (16-byte aligned, read with 16-byte loads): cell index,
 // first CSR row, row count and a zero (as int32), then the solution x (m),
@@ -187,10 +194,14 @@ WLSENO_DECLARE_RECON(float, 3, 10)
 // Per-cell flux gather + RK stage: out = a*u0 + b*(u + dt*L(u)); with
 // residual_only the output is L(u) itself.
 // fdev (FP32-bulk, scalar equations) replaces fvals when set.
+// With fdev, pin (the FP32 pairs of u, may be null) gives the jumps between
+// cell averages without FP64 arithmetic, and pout (may be null) receives the
+// pairs of the written state.
 cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
-                                   const double* fvals, const float* fdev, const double* u, const double* u0,
-                                   double a, double b, const double* dt_mesh, bool residual_only,
-                                   double* out, unsigned long long* counters, cudaStream_t s);
+                                   const double* fvals, const float* fdev, const double* u,
+                                   const double* u0, double a, double b, const double* dt_mesh,
+                                   bool residual_only, double* out, unsigned long long* counters,
+                                   cudaStream_t s, const float2* pin = nullptr, float2* pout = nullptr);
 // dt_mesh[k] = cfl * rmin[k] / lambda_max(mesh k), or dt_fixed when > 0.
 cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
                                const double* u, const double* rmin, double cfl, double dt_fixed,
