@@ -324,6 +324,36 @@ def euler_quadrant_initial(mesh: Mesh, seed: int, gamma: float = 1.4):
     return cons @ frac.T, prim
 
 
+def isentropic_vortex(points: np.ndarray, t: float, gamma: float = 1.4, strength: float = 5.0,
+                      core: float = 0.1, center=(0.5, 0.5), velocity=(1.0, 1.0)) -> np.ndarray:
+    """Conserved variables [4][P] of the isentropic vortex of the 2-D Euler
+    equations (the classic test of Shu's 1998 lecture notes), an exact
+    solution: a free stream rho = p = 1 with `velocity`, carrying a vortex
+    of temperature drop (gamma-1) s^2/(8 gamma pi^2) exp(1 - r^2) and swirl
+    s/(2 pi) exp((1 - r^2)/2) (r in units of `core`), translated with the
+    stream (periodic unit square: minimum-image distance).  Spatial units
+    scaled by `core` leave the equations unchanged; core 0.1 puts the
+    standard [-5, 5]^2 box on the unit square."""
+    x = points[:, 0] - center[0] - velocity[0] * t
+    y = points[:, 1] - center[1] - velocity[1] * t
+    x = (x - np.round(x)) / core
+    y = (y - np.round(y)) / core
+    r2 = x * x + y * y
+    temp = 1.0 - (gamma - 1.0) * strength ** 2 / (8.0 * gamma * np.pi ** 2) * np.exp(1.0 - r2)
+    rho = temp ** (1.0 / (gamma - 1.0))
+    swirl = strength / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    u = velocity[0] - swirl * y
+    v = velocity[1] + swirl * x
+    p = rho ** gamma
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def isentropic_vortex_averages(mesh: Mesh, t: float, k: int = 10, **kw) -> np.ndarray:
+    """Cell averages [4][n_cells] of `isentropic_vortex` at time t."""
+    return np.stack([cell_averages(mesh, lambda P, c=c: isentropic_vortex(P, t, **kw)[c], k=k)
+                     for c in range(4)])
+
+
 def random_unit_directions(n_cells: int, count: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     d = rng.normal(size=(count, n_cells))
