@@ -109,6 +109,17 @@ typedef struct {
  * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and flux
  *             in FP32; moments, residual accumulation and RK update in FP64).
  * gamma:      WLSENO_EULER only: ratio of specific heats (e.g. 1.4).
+ * characteristic: WLSENO_EULER only, 0 or 1: reconstruct characteristic-wise
+ *             (the characteristic decomposition of Sec. 5.1.4 and Sec. 5.2.4,
+ *             per facet on triangles): for facet f of cell i the stencil
+ *             averages are projected onto the eigenvectors of the Jacobian of
+ *             F(U).n_f at the mean of the averages of i and its neighbour
+ *             across f, each field gets its own weights and least-squares
+ *             solve (full-rank stencils, no pivoting), and the traces at f's
+ *             points are projected back.  wlseno_reconstruct then returns
+ *             facet values only (coeffs must be NULL: there is no single
+ *             polynomial per cell); flagged_cells counts (cell, facet) solves
+ *             above the flag threshold.
  *
  * WLSENO_EULER (2-D): n_comp = 4 conserved variables (rho, rho u, rho v, E),
  * each reconstructed with its own weights (componentwise WLS-ENO); LF alpha
@@ -125,6 +136,7 @@ typedef struct {
   double kappa_flag;
   int precision;
   double gamma;
+  int characteristic;
 } wlseno_scheme;
 
 typedef struct {

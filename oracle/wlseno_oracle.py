@@ -391,6 +391,7 @@ class Problem:
     rank_tol: float = 1e-10
     radius_cut: float = 0.0
     min_rows: int = 0
+    characteristic: bool = False  # Euler: characteristic-wise reconstruction
 
     def __post_init__(self):
         self.vertices = np.asarray(self.vertices, dtype=np.float64)
@@ -549,7 +550,7 @@ def residual(prob, ubar, coeffs=None):
     """L(ubar)_i = -(1/|tau_i|) * sum over facets of the integrated numerical
     flux out of tau_i (Eq. (fvm), divided by |tau_i|)."""
     if prob.pde == EULER:
-        return residual_euler(prob, ubar)
+        return residual_euler_char(prob, ubar) if prob.characteristic else residual_euler(prob, ubar)
     if coeffs is None:
         coeffs = reconstruct_all(prob, ubar)
     flux_out = np.zeros(prob.N)
@@ -668,6 +669,101 @@ def residual_euler(prob, ubar):
         flux_out[:, L] += g
         if R >= 0:
             flux_out[:, R] -= g
+    return -flux_out / prob.geo.volume[None, :]
+
+
+# ----------------------------------------------------------------------------
+# compressible Euler, characteristic-wise WLS-ENO (the characteristic
+# decomposition the paper applies to its Euler runs, Sec. 5.1.4 and Sec. 5.2.4,
+# in the per-facet form it cites for triangles): for facet f of cell i the
+# stencil averages are projected onto the eigenvectors of the Jacobian of
+# F(U).n_f at the mean of the two cells' averages, each characteristic field
+# is reconstructed with its own WLS-ENO weights, evaluated at the facet's
+# points and projected back.
+# ----------------------------------------------------------------------------
+
+def euler_char_basis(U, n, gamma):
+    """Right eigenvectors R (columns) of d(F(U).n)/dU for 2-D Euler, in the
+    order of the eigenvalues u.n - c, u.n (entropy), u.n (shear), u.n + c,
+    and L = R^-1."""
+    rho, vel, p = euler_primitive(np.asarray(U, dtype=np.float64), gamma)
+    u, v = vel
+    nx, ny = n
+    c = math.sqrt(gamma * p / rho)
+    H = (U[3] + p) / rho
+    un = u * nx + v * ny
+    ut = -u * ny + v * nx
+    R = np.array([[1.0, 1.0, 0.0, 1.0],
+                  [u - c * nx, u, -ny, u + c * nx],
+                  [v - c * ny, v, nx, v + c * ny],
+                  [H - c * un, 0.5 * (u * u + v * v), ut, H + c * un]])
+    return R, np.linalg.inv(R)
+
+
+def euler_char_poly(prob, ubar, i, f):
+    """Characteristic reconstruction of cell i for its facet f: (R, the four
+    fields' coefficient vectors)."""
+    j, _ = prob.sib[i, f]
+    ustar = 0.5 * (ubar[:, i] + ubar[:, j]) if j >= 0 else ubar[:, i]
+    n = outward_normal(prob.geo.coords[i], f)
+    R, L = euler_char_basis(ustar, n, prob.gamma)
+    S = prob.stencils[i]
+    w = {k: L @ ubar[:, k] for k in S}
+    return R, [prob.reconstruct_cell({k: w[k][c] for k in S}, i)[0] for c in range(4)]
+
+
+def residual_euler_char(prob, ubar):
+    """As residual_euler with characteristic-wise traces; the positivity
+    fallback is the same reading (a cell with rho or p <= 1e-12 at any of its
+    facet points uses its averages at all its facets)."""
+    ubar = np.asarray(ubar, dtype=np.float64)
+    assert prob.dim == 2
+    traces = {}
+    ok = np.ones(prob.N, dtype=bool)
+    for i in range(prob.N):
+        X = prob.geo.coords[i]
+        for f in range(3):
+            R, coef = euler_char_poly(prob, ubar, i, f)
+            pts, _ = facet_rule(np.delete(X, f, axis=0))
+            vals = np.array([R @ np.array([prob.eval_poly(coef[c], i, x) for c in range(4)]) for x in pts])
+            traces[i, f] = vals
+            for U in vals:
+                rho, _, pr = euler_primitive(U, prob.gamma)
+                if not (rho > POSITIVITY_FLOOR and pr > POSITIVITY_FLOOR):
+                    ok[i] = False
+    for i in range(prob.N):
+        if not ok[i]:
+            for f in range(3):
+                traces[i, f] = np.repeat(ubar[:, i][None, :], len(traces[i, f]), axis=0)
+    flux_out = np.zeros((4, prob.N))
+    for Lc, fL, Rc in facets(prob):
+        X = prob.geo.coords[Lc]
+        F = np.delete(X, fL, axis=0)
+        pts, w = facet_rule(F)
+        area = facet_measure(F)
+        n = outward_normal(X, fL)
+        UL = traces[Lc, fL]
+        if Rc < 0:
+            UR = UL.copy()
+        else:
+            # the sibling facet's points in R's frame are the same points; its
+            # rule lists them in R's vertex order: match them by position
+            fR = int(prob.sib[Lc, fL][1])
+            shift = min_image(prob.geo.centroid[Rc] - prob.geo.centroid[Lc], prob.period) - \
+                (prob.geo.centroid[Rc] - prob.geo.centroid[Lc])
+            ptsR, _ = facet_rule(np.delete(prob.geo.coords[Rc], fR, axis=0))
+            order = [int(np.argmin([np.linalg.norm((x - shift) - y) for y in ptsR])) for x in pts]
+            UR = traces[Rc, fR][order]
+        alpha = max(max(euler_wave_speed(UL[q], n, prob.gamma), euler_wave_speed(UR[q], n, prob.gamma))
+                    for q in range(len(w)))
+        g = np.zeros(4)
+        for q in range(len(w)):
+            g += w[q] * 0.5 * (euler_normal_flux(UL[q], n, prob.gamma) + euler_normal_flux(UR[q], n, prob.gamma)
+                               - alpha * (UR[q] - UL[q]))
+        g *= area
+        flux_out[:, Lc] += g
+        if Rc >= 0:
+            flux_out[:, Rc] -= g
     return -flux_out / prob.geo.volume[None, :]
 
 

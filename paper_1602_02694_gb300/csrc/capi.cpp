@@ -287,8 +287,14 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
   const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
   cudaError_t e = cudaSuccess;
   if (ctx->scheme.pde == WLSENO_EULER) {
-    for (int c = 0; c < C && e == cudaSuccess; ++c)
-      e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals + c * N * NP, s);
+    if (ctx->scheme.characteristic) {
+      KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
+      e = launch_euler_char(ctx->dm, ctx->sp, ctx->scheme.precision, u, ctx->d_fvals, ctx->d_counters, s);
+      scope.done(e == cudaSuccess ? 1 : 0);
+    } else {
+      for (int c = 0; c < C && e == cudaSuccess; ++c)
+        e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals + c * N * NP, s);
+    }
     if (e != cudaSuccess) return e;
     KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
     e = launch_euler_positivity(ctx->dm, ctx->sp.gamma, u, ctx->d_fvals, ctx->d_counters, s);
@@ -391,6 +397,8 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   if (scheme->pde == WLSENO_EULER ? scheme->n_comp != 4 || !(scheme->gamma > 1.0) : scheme->n_comp != 1)
     return WLSENO_ERR_INVALID_ARG;
   if (scheme->precision != WLSENO_FP64 && scheme->precision != WLSENO_FP32_BULK)
+    return WLSENO_ERR_INVALID_ARG;
+  if (scheme->characteristic != 0 && (scheme->characteristic != 1 || scheme->pde != WLSENO_EULER))
     return WLSENO_ERR_INVALID_ARG;
   if (!(scheme->eps > 0.0) || !(scheme->alpha_c > 0.0) || !(scheme->rank_tol >= 0.0))
     return WLSENO_ERR_INVALID_ARG;
@@ -561,6 +569,9 @@ wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* co
   wlseno_status st = check_ready(ctx);
   if (st != WLSENO_OK) return st;
   if (!ubar) return fail(ctx, WLSENO_ERR_INVALID_ARG, "ubar is null");
+  if (ctx->scheme.characteristic && coeffs)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG,
+                "characteristic reconstruction has no per-cell polynomial: pass coeffs = NULL");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ctx->last_stream = s;
@@ -582,7 +593,15 @@ wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* co
   if (fv_host && !ctx->d_fv_out && (st = dalloc(ctx, &ctx->d_fv_out, C * N * NP))) return st;
   if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
-  for (int c = 0; c < C; ++c) {
+  if (ctx->scheme.characteristic) {
+    // facet values of all components at once (there is no per-cell polynomial)
+    double* fv = facet_values ? (fv_host ? ctx->d_fv_out : facet_values) : ctx->d_fvals;
+    KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
+    e = launch_euler_char(ctx->dm, ctx->sp, ctx->scheme.precision, u, fv, ctx->d_counters, s);
+    scope.done(e == cudaSuccess ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruction kernel");
+  }
+  for (int c = 0; c < C && !ctx->scheme.characteristic; ++c) {
     double* co = coeffs ? (coef_host ? ctx->d_coef : coeffs) + c * N * m : nullptr;
     double* fv = facet_values ? (fv_host ? ctx->d_fv_out : facet_values) + c * N * NP : ctx->d_fvals;
     e = reconstruct_one(ctx, u + c * N, co, fv, s);

@@ -107,6 +107,10 @@ cudaError_t launch_euler_flux_stage(const DeviceMesh& dm, double gamma, int prec
                                     const double* fvals, const double* u, const double* u0,
                                     double a, double b, const double* dt_mesh, bool residual_only,
                                     double* out, unsigned long long* counters, cudaStream_t s);
+// Characteristic-wise reconstruction of all four components' facet values.
+cudaError_t launch_euler_char(const DeviceMesh& dm, const SchemeParams& sp, int precision,
+                              const double* ubar, double* fvals, unsigned long long* counters,
+                              cudaStream_t s);
 cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
                                unsigned long long* lmax_bits, int n_meshes, cudaStream_t s);
 

@@ -41,7 +41,8 @@ class wlseno_stencil_opts(ctypes.Structure):
 class wlseno_scheme(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("n_comp", ctypes.c_int), ("velocity", ctypes.c_double * 3),
                 ("eps", ctypes.c_double), ("alpha_c", ctypes.c_double), ("rank_tol", ctypes.c_double),
-                ("kappa_flag", ctypes.c_double), ("precision", ctypes.c_int), ("gamma", ctypes.c_double)]
+                ("kappa_flag", ctypes.c_double), ("precision", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("characteristic", ctypes.c_int)]
 
 
 class wlseno_info(ctypes.Structure):
@@ -153,12 +154,13 @@ class Context:
 
     def __init__(self, device: int = 0, pde="advection", velocity=(1.0, 1.0, 0.0), eps=1e-2,
                  alpha_c=1.5, rank_tol=1e-10, kappa_flag=1e3, precision="fp64", n_comp=None,
-                 gamma=1.4):
+                 gamma=1.4, characteristic=False):
         self.lib = load_library()
         sch = wlseno_scheme()
         sch.pde = _PDE[pde] if isinstance(pde, str) else int(pde)
         sch.n_comp = n_comp if n_comp is not None else (4 if sch.pde == EULER else 1)
         sch.gamma = gamma
+        sch.characteristic = 1 if characteristic else 0
         for a in range(3):
             sch.velocity[a] = float(velocity[a]) if a < len(velocity) else 0.0
         sch.eps, sch.alpha_c, sch.rank_tol, sch.kappa_flag = eps, alpha_c, rank_tol, kappa_flag

@@ -300,3 +300,74 @@ def test_euler_vortex_converges_to_exact_solution(dev):
     assert abs(orders["fp32_bulk"][-1] - orders["fp64"][-1]) <= 0.1, orders
     for a, b in zip(errs["fp32_bulk"], errs["fp64"]):
         assert abs(a - b) <= 0.05 * b, errs
+
+
+def test_euler_characteristic_parity(dev):
+    """Characteristic-wise reconstruction (per facet, Hu-Shu form): residual,
+    positivity decisions and two CFL-0.3 steps of the transmissive quadrant
+    problem against the oracle, and the vortex residual."""
+    mesh, U = euler_problem(12)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, min_rows=9,
+                     characteristic=True)
+    ctx = Context(pde="euler", characteristic=True)
+    ctx.build_stencils(mesh, order_p=3, ring=1.0, min_rows=9)
+    ctx.precompute_moments()
+    u = torch.tensor(U, device=dev).contiguous()
+    L = torch.empty_like(u)
+    ctx.flux_residual(u, L)
+    ref = O.residual(prob, U)
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    assert float(np.max(np.abs(L.cpu().numpy() - ref))) <= TOL64 * scale
+    ref2, dts = O.rk3_run(prob, U, 2, cfl=0.3)
+    dt = None
+    for _ in range(2):
+        dt = ctx.rk_step(u, cfl=0.3, n_steps=1, want_dt=True)
+    assert abs(dt - dts[-1]) <= 1e-14 * dt
+    assert float(np.max(np.abs(u.cpu().numpy() - ref2))) <= TOL64
+    # the reconstruction API: facet values only
+    fv = torch.empty(4 * mesh.n_cells * 6, dtype=torch.float64, device=dev)
+    ctx.reconstruct(torch.tensor(U, device=dev).contiguous(), None, fv)
+    coef = torch.empty(4 * mesh.n_cells * 6, dtype=torch.float64, device=dev)
+    from paper_1602_02694_gb300.wlseno import WlsenoError
+    with pytest.raises(WlsenoError):
+        ctx.reconstruct(torch.tensor(U, device=dev).contiguous(), coef)
+    ctx.close()
+    mesh = synth.tri_mesh(16, jitter=0.2, seed=1)
+    U = synth.isentropic_vortex_averages(mesh, 0.0, velocity=VORTEX_VEL)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, characteristic=True)
+    ref = O.residual(prob, U)
+    ctx = Context(pde="euler", characteristic=True)
+    ctx.build_stencils(mesh, order_p=3, ring=1.0)
+    ctx.precompute_moments()
+    u = torch.tensor(U, device=dev).contiguous()
+    L = torch.empty_like(u)
+    ctx.flux_residual(u, L)
+    assert float(np.max(np.abs(L.cpu().numpy() - ref))) <= TOL64 * max(1.0, float(np.max(np.abs(ref))))
+    ctx.close()
+
+
+def test_euler_characteristic_vortex_converges(dev):
+    """The vortex convergence test above with characteristic-wise
+    reconstruction, both precisions."""
+    errs = {"fp64": [], "fp32_bulk": []}
+    for n in (64, 128, 256):
+        mesh = synth.tri_mesh(n, jitter=0.2, seed=1)
+        U0 = synth.isentropic_vortex_averages(mesh, 0.0, core=0.08, velocity=VORTEX_VEL)
+        dt, steps = 0.02 / n, 2 * n
+        exact = synth.isentropic_vortex_averages(mesh, dt * steps, core=0.08, velocity=VORTEX_VEL)
+        for precision in errs:
+            ctx = Context(pde="euler", precision=precision, characteristic=True)
+            ctx.build_stencils(mesh, order_p=3, ring=1.0)
+            ctx.precompute_moments()
+            u = torch.tensor(U0, device=dev).contiguous()
+            ctx.rk_step(u, dt=dt, n_steps=steps)
+            assert ctx.diagnostics()["nonfinite"] == 0
+            errs[precision].append(float(np.mean(np.abs(u.cpu().numpy()[0] - exact[0]))))
+            ctx.close()
+    print("characteristic vortex density L1 errors", errs)
+    orders = {k: [math.log2(e[j] / e[j + 1]) for j in range(2)] for k, e in errs.items()}
+    print("orders", orders)
+    for k in orders:
+        assert orders[k][-1] >= 2.5, (k, errs, orders)
+    for a, b in zip(errs["fp32_bulk"], errs["fp64"]):
+        assert abs(a - b) <= 0.05 * b, errs

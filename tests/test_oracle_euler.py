@@ -101,3 +101,53 @@ def test_moving_isentropic_vortex_residual_converges_at_second_order():
         means.append(float(np.mean(np.abs(O.residual(prob, U) - dudt))))
     order = math.log2(means[0] / means[1])
     assert order >= 1.8, (means, order)
+
+
+def test_characteristic_basis_diagonalises_the_normal_flux_jacobian():
+    """L dF.n/dU R = diag(u.n - c, u.n, u.n, u.n + c), with the Jacobian taken
+    by central differences of the oracle's normal flux (an independent
+    check of the eigenvectors)."""
+    rng = np.random.default_rng(4)
+    for _ in range(6):
+        U = cons(rng.uniform(0.2, 2.0), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.1, 2.0))
+        a = rng.uniform(0, 2 * math.pi)
+        n = np.array([math.cos(a), math.sin(a)])
+        J = np.empty((4, 4))
+        for k in range(4):
+            h = 1e-6 * max(1.0, abs(U[k]))
+            e = np.zeros(4)
+            e[k] = h
+            J[:, k] = (O.euler_normal_flux(U + e, n, GAMMA) - O.euler_normal_flux(U - e, n, GAMMA)) / (2 * h)
+        R, L = O.euler_char_basis(U, n, GAMMA)
+        rho, vel, p = O.euler_primitive(U, GAMMA)
+        un, c = float(vel @ n), math.sqrt(GAMMA * p / rho)
+        assert np.allclose(L @ J @ R, np.diag([un - c, un, un, un + c]), atol=1e-6)
+
+
+def test_characteristic_equals_componentwise_for_data_independent_weights():
+    """With weights independent of the data (eps = 1e14: dev^2 / eps h^2 ~ 1e-15) the least-squares
+    reconstruction is linear, so projecting onto characteristic fields and
+    back changes nothing: both residuals agree to rounding."""
+    mesh = synth.tri_mesh(6, jitter=0.2, seed=2)
+    U = synth.isentropic_vortex_averages(mesh, 0.0, core=0.25, velocity=(0.3, -0.2))
+    a = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, eps=1e14)
+    b = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, eps=1e14,
+                  characteristic=True)
+    La, Lb = O.residual(a, U), O.residual(b, U)
+    assert np.max(np.abs(La - Lb)) <= 1e-10 * np.max(np.abs(La))
+
+
+def test_characteristic_vortex_residual_converges_at_second_order():
+    """The moving-vortex pin above for the characteristic-wise scheme."""
+    vel, step = (1.0, 0.5), 1e-4
+    means = []
+    for n in (16, 32):
+        mesh = synth.tri_mesh(n, jitter=0.2, seed=1)
+        U = synth.isentropic_vortex_averages(mesh, 0.0, velocity=vel)
+        dudt = (synth.isentropic_vortex_averages(mesh, step, velocity=vel)
+                - synth.isentropic_vortex_averages(mesh, -step, velocity=vel)) / (2 * step)
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER,
+                         characteristic=True)
+        means.append(float(np.mean(np.abs(O.residual(prob, U) - dudt))))
+    order = math.log2(means[0] / means[1])
+    assert order >= 1.8, (means, order)
