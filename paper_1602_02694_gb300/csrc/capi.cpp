@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "wlseno_internal.h"
@@ -195,6 +196,19 @@ void reset_kind_stats(wlseno_ctx* ctx) {
 
 // fvals receives the facet values, or with fdev set (FP32-bulk) their FP32
 // deviations from the cell averages instead.
+// Calls f(integral_constant<dim>, integral_constant<m>) for the compiled
+// (dimension, unknowns) pairs: 1-D p = 3, 5; 2-D p = 3, 4; 3-D p = 3.
+template <typename F>
+cudaError_t dispatch_dim_m(int dim, int m, F&& f) {
+  using std::integral_constant;
+  if (dim == 1 && m == 3) return f(integral_constant<int, 1>{}, integral_constant<int, 3>{});
+  if (dim == 1 && m == 5) return f(integral_constant<int, 1>{}, integral_constant<int, 5>{});
+  if (dim == 2 && m == 6) return f(integral_constant<int, 2>{}, integral_constant<int, 6>{});
+  if (dim == 2 && m == 10) return f(integral_constant<int, 2>{}, integral_constant<int, 10>{});
+  if (dim == 3 && m == 10) return f(integral_constant<int, 3>{}, integral_constant<int, 10>{});
+  return cudaErrorInvalidValue;
+}
+
 // FP32 pairs of a state (the scratch slot of d_pair), counted as a per-step
 // preparation kernel.
 cudaError_t split_state(wlseno_ctx* ctx, const double* u, float2* pair, cudaStream_t s) {
@@ -222,42 +236,28 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
     const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pair};
-    const bool d2m6 = dm.dim == 2 && dm.m == 6, d2m10 = dm.dim == 2 && dm.m == 10,
-               d3m10 = dm.dim == 3 && dm.m == 10;
-    if (d2m6)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s)
-              : launch_recon_tpc_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s);
-    else if (d2m10)
-      e = f32 ? launch_recon_tpc_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s)
-              : launch_recon_tpc_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s);
-    else if (d3m10)
-      e = f32 ? launch_recon_tpc_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s)
-              : launch_recon_tpc_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s);
+    e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
+      constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
+      return f32 ? launch_recon_tpc_inst<float, DD, MM>(dm, ctx->sp, ubar, out, wl, s)
+                 : launch_recon_tpc_inst<double, DD, MM>(dm, ctx->sp, ubar, out, wl, s);
+    });
     scope.done(e == cudaSuccess ? 1 : 0);
     if (e != cudaSuccess) return e;
     int nl = 0;
     KernelScope fix(ctx, WLSENO_KERNEL_FIXUP, s);
-    if (d2m6)
-      e = f32 ? launch_recon_fixup_inst<float, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_fixup_inst<double, 2, 6>(dm, ctx->sp, ubar, out, wl, s, &nl);
-    else if (d2m10)
-      e = f32 ? launch_recon_fixup_inst<float, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_fixup_inst<double, 2, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
-    else if (d3m10)
-      e = f32 ? launch_recon_fixup_inst<float, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl)
-              : launch_recon_fixup_inst<double, 3, 10>(dm, ctx->sp, ubar, out, wl, s, &nl);
+    e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
+      constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
+      return f32 ? launch_recon_fixup_inst<float, DD, MM>(dm, ctx->sp, ubar, out, wl, s, &nl)
+                 : launch_recon_fixup_inst<double, DD, MM>(dm, ctx->sp, ubar, out, wl, s, &nl);
+    });
     fix.done(e == cudaSuccess ? nl : 0);
     return e;
   }
-  if (dm.dim == 2 && dm.m == 6)
-    e = f32 ? launch_reconstruct_inst<float, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
-            : launch_reconstruct_inst<double, 2, 6>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
-  else if (dm.dim == 2 && dm.m == 10)
-    e = f32 ? launch_reconstruct_inst<float, 2, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
-            : launch_reconstruct_inst<double, 2, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
-  else if (dm.dim == 3 && dm.m == 10)
-    e = f32 ? launch_reconstruct_inst<float, 3, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
-            : launch_reconstruct_inst<double, 3, 10>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
+  e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
+    constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
+    return f32 ? launch_reconstruct_inst<float, DD, MM>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s)
+               : launch_reconstruct_inst<double, DD, MM>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
+  });
   scope.done(e == cudaSuccess ? 1 : 0);
   return e;
 }
@@ -450,7 +450,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   if (st != WLSENO_OK) return fail(ctx, st, err);
   if (ctx->scheme.pde == WLSENO_EULER && H.dim != 2)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the Euler path is built for 2-D meshes");
-  if ((H.dim == 2 && H.m != 6 && H.m != 10) || (H.dim == 3 && H.m != 10))
+  if ((H.dim == 1 && H.m != 3 && H.m != 5) || (H.dim == 2 && H.m != 6 && H.m != 10) ||
+      (H.dim == 3 && H.m != 10))
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "order p not compiled for this dimension");
   int G = opts->lanes_per_cell, R = opts->rows_per_lane;
   if (G == 0 && R == 0) {
@@ -862,6 +863,8 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   if (dt == 0.0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint needs a fixed dt (> 0, or < 0 for per-mesh steps)");
   if (ctx->scheme.pde == WLSENO_EULER)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for the scalar equations");
+  if (ctx->dm.dim == 1)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for 2-D and 3-D meshes");
   if (dt < 0.0 && !ctx->mesh_dt_set)
     return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
   DeviceGuard guard(ctx->device);

@@ -92,24 +92,24 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
     return WLSENO_ERR_INVALID_ARG;
   }
   const int dim = meshes[0].dim;
-  if (dim != 2 && dim != 3) {
-    *err = "dim must be 2 or 3";
+  if (dim < 1 || dim > 3) {
+    *err = "dim must be 1, 2 or 3";
     return WLSENO_ERR_INVALID_ARG;
   }
   const int p = opts->order_p;
-  if ((dim == 2 && (p < 3 || p > 4)) || (dim == 3 && p != 3)) {
+  if ((dim == 1 && p != 3 && p != 5) || (dim == 2 && (p < 3 || p > 4)) || (dim == 3 && p != 3)) {
     *err = "unsupported order p for this dimension";
     return WLSENO_ERR_INVALID_ARG;
   }
   std::vector<int> steps;
   if (!ring_steps(dim, opts->ring, &steps)) {
-    *err = "ring is not a positive multiple of 1/2 (2-D) or 1/3 (3-D)";
+    *err = "ring is not a positive integer (1-D) or multiple of 1/2 (2-D) or 1/3 (3-D)";
     return WLSENO_ERR_INVALID_ARG;
   }
   const int m = n_coeffs(dim, p);
   const int min_rows = opts->min_rows > 0 ? opts->min_rows : (3 * m + 1) / 2;
   const int nf = dim + 1;
-  const int nq = dim == 2 ? 2 : 3;
+  const int nq = nq_of(dim);
 
   HostSetup& S = *out;
   S = HostSetup();
@@ -182,8 +182,9 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
       double e[3][3];
       for (int v = 1; v < nf; ++v)
         for (int a = 0; a < dim; ++a) e[v - 1][a] = X[v * dim + a] - X[a];
-      double vol = dim == 2 ? 0.5 * (e[0][0] * e[1][1] - e[0][1] * e[1][0])
-                            : det3(e[0], e[1], e[2]) / 6.0;
+      double vol = dim == 1   ? e[0][0]
+                   : dim == 2 ? 0.5 * (e[0][0] * e[1][1] - e[0][1] * e[1][0])
+                              : det3(e[0], e[1], e[2]) / 6.0;
       if (!(vol > 0.0)) {
         *err = "mesh " + std::to_string(k) + ": cell " + std::to_string(c) +
                " is inverted or degenerate";
@@ -215,7 +216,10 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
         for (int v = 0; v < nf; ++v)
           if (v != f) loc[t++] = v;
         double n[3] = {0, 0, 0}, area;
-        if (dim == 2) {
+        if (dim == 1) {  // the facet is the vertex loc[0]: unit measure
+          area = 1.0;
+          n[0] = 1.0;
+        } else if (dim == 2) {
           double ex = X[loc[1] * 2] - X[loc[0] * 2], ey = X[loc[1] * 2 + 1] - X[loc[0] * 2 + 1];
           area = std::sqrt(ex * ex + ey * ey);
           n[0] = ey / area;
@@ -328,7 +332,9 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
                   [&](int a, int b) { return M.cells[c * nf + a] < M.cells[c * nf + b]; });
         for (int q = 0; q < nq; ++q) {
           double bary[3];
-          if (dim == 2) {
+          if (dim == 1) {
+            bary[0] = 1.0;
+          } else if (dim == 2) {
             double tq = q == 0 ? 0.5 - g : 0.5 + g;
             bary[0] = 1.0 - tq;
             bary[1] = tq;

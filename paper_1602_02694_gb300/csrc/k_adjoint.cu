@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256)
 adj_facet_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fvals,
                  const double* __restrict__ lambda, double* __restrict__ gfv) {
   constexpr int NF = DIM + 1;
-  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= dm.N) return;
@@ -108,7 +108,7 @@ adj_recon_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
                  double* __restrict__ selfbar, int* __restrict__ amin_cell,
                  double* __restrict__ amin_val) {
   constexpr int NF = DIM + 1;
-  constexpr int NP = NF * (DIM == 2 ? 2 : 3);
+  constexpr int NP = NF * nq_of(DIM);
   const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (c >= dm.N) return;
   const int64_t N = dm.N;

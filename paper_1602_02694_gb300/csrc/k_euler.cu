@@ -23,7 +23,7 @@ template <int DIM>
 __global__ void __launch_bounds__(256)
 euler_positivity_kernel(int64_t N, double gamma, const double* __restrict__ ubar,
                         double* __restrict__ fvals, unsigned long long* __restrict__ counters) {
-  constexpr int NP = (DIM + 1) * (DIM == 2 ? 2 : 3);
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
   constexpr int C = DIM + 2;
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= N) return;
@@ -74,7 +74,7 @@ euler_flux_stage_kernel(DeviceMesh dm, double gamma, const double* __restrict__ 
                         double b, const double* __restrict__ dt_mesh, int residual_only,
                         double* __restrict__ out, unsigned long long* __restrict__ counters) {
   constexpr int NF = DIM + 1;
-  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   constexpr int C = DIM + 2;
   const int64_t N = dm.N;

@@ -10,6 +10,7 @@
 // bitwise-same flux and use it with opposite signs: no atomics, a fixed
 // summation order, and exact discrete conservation up to the final FP64 sums.
 #include <cmath>
+#include <type_traits>
 
 #include "wlseno_internal.h"
 
@@ -98,7 +99,7 @@ flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fva
                   const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
                   unsigned long long* __restrict__ counters) {
   constexpr int NF = DIM + 1;
-  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= dm.N) return;
@@ -180,7 +181,7 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
                       unsigned long long* __restrict__ counters, const float2* __restrict__ pin,
                       float2* __restrict__ pout) {
   constexpr int NF = DIM + 1;
-  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= dm.N) return;
@@ -300,26 +301,22 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   const int ro = residual_only ? 1 : 0;
-  if (fdev) {
-    if (dm.dim == 2)
-      flux_stage_dev_kernel<2><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
-                                                          pin, residual_only ? nullptr : pout);
+  auto launch = [&](auto D) {
+    constexpr int DD = decltype(D)::value;
+    if (fdev)
+      flux_stage_dev_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
+                                                           pin, residual_only ? nullptr : pout);
+    else if (precision == WLSENO_FP32_BULK)
+      flux_stage_kernel<float, DD><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
     else
-      flux_stage_dev_kernel<3><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
-                                                          pin, residual_only ? nullptr : pout);
-    return cudaGetLastError();
-  }
-  if (dm.dim == 2) {
-    if (precision == WLSENO_FP32_BULK)
-      flux_stage_kernel<float, 2><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-    else
-      flux_stage_kernel<double, 2><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-  } else {
-    if (precision == WLSENO_FP32_BULK)
-      flux_stage_kernel<float, 3><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-    else
-      flux_stage_kernel<double, 3><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-  }
+      flux_stage_kernel<double, DD><<<blocks, threads, 0, s>>>(dm, sp, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  };
+  if (dm.dim == 1)
+    launch(std::integral_constant<int, 1>{});
+  else if (dm.dim == 2)
+    launch(std::integral_constant<int, 2>{});
+  else
+    launch(std::integral_constant<int, 3>{});
   return cudaGetLastError();
 }
 

@@ -3,11 +3,12 @@
 // For stencil row (i, j):  A[e][kappa] = (1/|tau_j|) int_{tau_j}
 //   prod_c ((x_c - x_i,c)/h_i)^kappa_c / kappa_c!  dx
 // with tau_j taken at its minimum-image copy next to tau_i.  The average over
-// the simplex is computed exactly with a collapsed (Duffy) Gauss-Legendre
-// product rule: 2-D  x = Y0 + s (Y1 - Y0) + s t (Y2 - Y1), weight 2 s;
-// 3-D x = Y0 + r (Y1 - Y0) + r s (Y2 - Y1) + r s t (Y3 - Y2), weight 6 r^2 s.
-// With K = 4 points per direction the rule is exact for the degrees used
-// (<= 3 in 2-D, <= 2 in 3-D, plus the Jacobian's powers).
+// the simplex is computed exactly with a (collapsed, Duffy) Gauss-Legendre
+// product rule: 1-D x = Y0 + s (Y1 - Y0); 2-D x = Y0 + s (Y1 - Y0) +
+// s t (Y2 - Y1), weight 2 s; 3-D x = Y0 + r (Y1 - Y0) + r s (Y2 - Y1) +
+// r s t (Y3 - Y2), weight 6 r^2 s.  With K = 4 points per direction the rule
+// is exact for the degrees used (<= 4 in 1-D, <= 3 in 2-D, <= 2 in 3-D, plus
+// the Jacobian's powers).
 #include <cmath>
 
 #include "wlseno_internal.h"
@@ -74,7 +75,16 @@ __global__ void moments_kernel(DeviceMesh dm, GaussRule g) {
   double acc[M];
 #pragma unroll
   for (int c = 0; c < M; ++c) acc[c] = 0.0;
-  if (DIM == 2) {
+  if (DIM == 1) {  // Gauss-Legendre on the segment (weights sum to 1)
+    for (int qs = 0; qs < K; ++qs) {
+      double y[DIM];
+      for (int a = 0; a < DIM; ++a) y[a] = Y[0][a] + g.x[qs] * (Y[1][a] - Y[0][a]);
+      double mono[M];
+      eval_monomials<double, DIM, M>(y, mono);
+#pragma unroll
+      for (int c = 0; c < M; ++c) acc[c] += g.w[qs] * mono[c];
+    }
+  } else if (DIM == 2) {
     for (int qs = 0; qs < K; ++qs)
       for (int qt = 0; qt < K; ++qt) {
         const double s = g.x[qs], t = g.x[qt];
@@ -121,7 +131,12 @@ cudaError_t launch_dm(const DeviceMesh& dm, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_moments(const DeviceMesh& dm, cudaStream_t s) {
-  if (dm.dim == 2) {
+  if (dm.dim == 1) {
+    switch (dm.m) {
+      case 3: return launch_dm<1, 3>(dm, s);
+      case 5: return launch_dm<1, 5>(dm, s);
+    }
+  } else if (dm.dim == 2) {
     switch (dm.m) {
       case 3: return launch_dm<2, 3>(dm, s);
       case 6: return launch_dm<2, 6>(dm, s);

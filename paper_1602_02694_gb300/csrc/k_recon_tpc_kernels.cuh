@@ -146,7 +146,7 @@ template <typename T, int DIM, int M>
 __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
                                           double* __restrict__ coeffs, double* __restrict__ fvals,
                                           float* __restrict__ fdev) {
-  constexpr int NP = (DIM + 1) * (DIM == 2 ? 2 : 3);
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
   if (coeffs) {
 #pragma unroll
     for (int c = 0; c < M; ++c) coeffs[i * M + c] = static_cast<double>(x[c]) + (c == 0 ? ui : 0.0);
@@ -240,7 +240,7 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
               double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
               TpcWork work) {
   constexpr int NF = DIM + 1;
-  constexpr int NP = NF * (DIM == 2 ? 2 : 3);
+  constexpr int NP = NF * nq_of(DIM);
   constexpr int kPerWarp = 32 / L;
   const int count = work.counts[1];
   const int lane = threadIdx.x % L;
@@ -267,7 +267,7 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
     const int beg = __float_as_int(r[1]);
     const int n = valid ? __float_as_int(r[2]) : 0;
     // all loads of this lane's rows next, from the CSR layout: a cell's rows
-    // are contiguous (16-byte aligned), so the group's loads share cache lines
+    // are contiguous, so the group's loads share cache lines
     int64_t jrow[RPL];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -278,12 +278,18 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int t = lane + q * L;
-      const double2* row = reinterpret_cast<const double2*>(dm.A64 + static_cast<int64_t>(beg + t) * M);
+      const double* row = dm.A64 + static_cast<int64_t>(beg + t) * M;
+      if constexpr (M % 2 == 0) {  // rows of 16-byte multiples: 16-byte loads
+        const double2* row2 = reinterpret_cast<const double2*>(row);
 #pragma unroll
-      for (int c = 0; c < M; c += 2) {
-        const double2 v = t < n ? row[c / 2] : make_double2(0.0, 0.0);
-        a[q][c] = v.x;
-        a[q][c + 1] = v.y;
+        for (int c = 0; c < M; c += 2) {
+          const double2 v = t < n ? row2[c / 2] : make_double2(0.0, 0.0);
+          a[q][c] = v.x;
+          a[q][c + 1] = v.y;
+        }
+      } else {  // odd m: rows start on 8-byte boundaries only
+#pragma unroll
+        for (int c = 0; c < M; ++c) a[q][c] = t < n ? row[c] : 0.0;
       }
     }
     const double ui = ubar[i];

@@ -215,7 +215,7 @@ __device__ __forceinline__ void group_reconstruct_cell(
     unsigned long long* __restrict__ counters, unsigned char* smem_raw, int g, int gib,
     int64_t cell, bool valid, bool listed) {
   constexpr int NF = DIM + 1;
-  constexpr int NQ = DIM == 2 ? 2 : 3;
+  constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   constexpr int NR = G * R;
   constexpr bool kF32 = sizeof(T) == 4;

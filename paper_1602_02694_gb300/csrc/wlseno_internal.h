@@ -17,6 +17,10 @@ constexpr int kMaxM = 10;        // Taylor coefficients the kernels are built fo
 constexpr int kMaxQ = 3;         // quadrature points per facet
 constexpr int kMaxFacets = 4;    // facets per simplex
 
+// Quadrature points per facet: the vertex (1-D), two Gauss-Legendre points
+// on an edge (2-D), the three-point degree-2 rule on a triangle (3-D).
+__host__ __device__ constexpr int nq_of(int dim) { return dim == 1 ? 1 : dim == 2 ? 2 : 3; }
+
 // Host-side result of the mesh / stencil setup (host_mesh.cpp).
 struct HostSetup {
   int dim = 0, p = 0, m = 0, nq = 0, n_meshes = 0;
@@ -170,6 +174,10 @@ cudaError_t launch_recon_fixup_inst(const DeviceMesh& dm, const SchemeParams& sp
   cudaError_t launch_recon_fixup_inst<T, D, M>(const DeviceMesh&, const SchemeParams&,            \
                                                const double*, const ReconOut&, const TpcWork&,    \
                                                cudaStream_t, int*);
+WLSENO_DECLARE_TPC(double, 1, 3)
+WLSENO_DECLARE_TPC(double, 1, 5)
+WLSENO_DECLARE_TPC(float, 1, 3)
+WLSENO_DECLARE_TPC(float, 1, 5)
 WLSENO_DECLARE_TPC(double, 2, 6)
 WLSENO_DECLARE_TPC(double, 2, 10)
 WLSENO_DECLARE_TPC(double, 3, 10)
@@ -187,6 +195,10 @@ cudaError_t launch_reconstruct_inst(const DeviceMesh& dm, const SchemeParams& sp
   cudaError_t launch_reconstruct_inst<T, D, M>(const DeviceMesh&, const SchemeParams&, int, \
                                                int, const double*, const ReconOut&,        \
                                                cudaStream_t);
+WLSENO_DECLARE_RECON(double, 1, 3)
+WLSENO_DECLARE_RECON(double, 1, 5)
+WLSENO_DECLARE_RECON(float, 1, 3)
+WLSENO_DECLARE_RECON(float, 1, 5)
 WLSENO_DECLARE_RECON(double, 2, 6)
 WLSENO_DECLARE_RECON(double, 2, 10)
 WLSENO_DECLARE_RECON(double, 3, 10)

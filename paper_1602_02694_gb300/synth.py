@@ -149,6 +149,18 @@ def line_mesh(nodes: np.ndarray) -> Mesh:
                 n=len(nodes) - 1, meta={"kind": "line"})
 
 
+def periodic_line_mesh(n: int, jitter: float = 0.0, seed: int = 0) -> Mesh:
+    """n intervals on the periodic unit interval: nodes k/n jittered by
+    U(-jitter, jitter)/n (PCG64 seed), the last interval wrapping to node 0."""
+    rng = np.random.default_rng(seed)
+    nodes = (np.arange(n) + (rng.uniform(-jitter, jitter, n) if jitter > 0 else 0.0)) / n
+    cells = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1)
+    right = nodes[cells[:, 1]] + (cells[:, 1] == 0)  # unwrap the last interval
+    coords = np.stack([nodes[cells[:, 0]], right], axis=1)[:, :, None]
+    return Mesh(nodes[:, None].copy(), cells.astype(np.int64), np.ones(1), coords,
+                n=n, meta={"kind": "periodic line"})
+
+
 # --------------------------------------------------------------------------
 # cell averages of analytic fields
 # --------------------------------------------------------------------------
