@@ -52,7 +52,8 @@ enum { WLSENO_FP64 = 0, WLSENO_FP32_BULK = 1 };
 
 typedef struct wlseno_ctx wlseno_ctx; /* opaque */
 
-/* One conforming simplex mesh (triangles in 2-D, tetrahedra in 3-D).
+/* One conforming simplex mesh (segments in 1-D, triangles in 2-D,
+ * tetrahedra in 3-D).
  * vertices: host [n_vertices][dim] float64.
  * cells:    host [n_cells][dim+1] int64 vertex indices, positively oriented.
  * period:   host [dim]; period[a] > 0 makes axis a periodic with that length
@@ -69,19 +70,21 @@ typedef struct {
 
 /* Stencil selection (Sec. 3.2).
  * order_p:    p; the reconstruction has degree p-1 and m = C(p-1+dim, dim)
- *             Taylor coefficients.  Supported: 2-D p in {3,4}; 3-D p = 3.
- * ring:       k-ring size in the paper's increments (2-D: multiples of 1/2,
- *             1/2 = facet-sharing, 1 = vertex-sharing; 3-D: multiples of 1/3,
+ *             Taylor coefficients.  Supported: 1-D p in {3,5}; 2-D p in {3,4};
+ *             3-D p = 3.
+ * ring:       k-ring size in the paper's increments (1-D: whole numbers, the
+ *             k-ring is 2k+1 cells; 2-D: multiples of 1/2, 1/2 =
+ *             facet-sharing, 1 = vertex-sharing; 3-D: multiples of 1/3,
  *             1/3 = face-, 2/3 = edge-, 1 = vertex-sharing).
  * radius_cut: > 0 adds the cells of the next whole ring whose centroid lies
  *             within radius_cut * h_i of the centre cell's centroid.
  * min_rows:   grow stencils (by facet-neighbour increments) until they have at
  *             least this many cells; 0 means ceil(1.5 m).
- * lanes_per_cell, rows_per_lane: shape of the reconstruction kernel (a group
- *             of lanes_per_cell lanes of a warp solves one cell, each lane
- *             holding rows_per_lane stencil rows); 0, 0 picks the smallest
- *             compiled shape that holds the largest stencil.  Compiled shapes:
- *             (8,2) (8,3) (8,5) (16,3) (16,4). */
+ * lanes_per_cell, rows_per_lane: shape of the reconstruction kernel: (1,0)
+ *             one thread per cell (stencils of at most 64 cells; the default
+ *             for 0, 0), or a group of lanes_per_cell lanes of a warp per cell,
+ *             each lane holding rows_per_lane stencil rows: (8,2) (8,3) (8,5)
+ *             (16,3) (16,4).  wlseno_autotune picks the fastest that fits. */
 typedef struct {
   int order_p;
   double ring;
@@ -220,7 +223,7 @@ wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream);
  *         device, may be NULL: the reconstruction of cell i at the quadrature
  *         points of its local facet f (the facet opposite its local vertex f).
  *         Points are ordered by the facet's vertices sorted by global vertex
- *         index: 2-D Gauss-Legendre t = 1/2 -+ sqrt(3)/6 from the lower to the
+ *         index: 1-D the facet's vertex; 2-D Gauss-Legendre t = 1/2 -+ sqrt(3)/6 from the lower to the
  *         higher vertex; 3-D barycentric (2/3,1/6,1/6) on the lowest vertex
  *         first, then the middle, then the highest.
  * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
