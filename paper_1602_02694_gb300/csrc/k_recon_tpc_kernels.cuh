@@ -292,6 +292,15 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
         for (int c = 0; c < M; ++c) a[q][c] = t < n ? row[c] : 0.0;
       }
     }
+    // the FP32 copy of the same rows for A^T W^2 r (no FP64 -> FP32 conversions)
+    float a32[RPL][M];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int t = lane + q * L;
+      const float* row = dm.A32 + static_cast<int64_t>(beg + t) * M;
+#pragma unroll
+      for (int c = 0; c < M; ++c) a32[q][c] = t < n ? row[c] : 0.0f;
+    }
     const double ui = ubar[i];
     double uj[RPL];
 #pragma unroll
@@ -330,7 +339,7 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
       }
       const float wr = t < n ? w * w * static_cast<float>(dev - (fit0 + fit1)) : 0.0f;
 #pragma unroll
-      for (int c = 0; c < M; ++c) g[c] = fmaf(wr, static_cast<float>(a[q][c]), g[c]);
+      for (int c = 0; c < M; ++c) g[c] = fmaf(wr, a32[q][c], g[c]);
     }
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1)
