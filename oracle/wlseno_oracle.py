@@ -392,6 +392,8 @@ class Problem:
     radius_cut: float = 0.0
     min_rows: int = 0
     characteristic: bool = False  # Euler: characteristic-wise reconstruction
+    balanced: bool = False        # scalar: balanced-stencil re-selection (Sec. 3.2)
+    balance_margin: float = 2e-2  # out of range: beyond [min, max] by this share of the data's range
 
     def __post_init__(self):
         self.vertices = np.asarray(self.vertices, dtype=np.float64)
@@ -514,7 +516,89 @@ def facets(prob):
 
 
 def reconstruct_all(prob, ubar):
-    return [prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)]
+    out = [prob.reconstruct_cell(ubar, i)[0] for i in range(prob.N)]
+    if prob.balanced:
+        for i in range(prob.N):
+            if out_of_range(prob, ubar, i, out[i]):
+                S = balanced_stencil(prob, i, out[i])
+                if S is not None:
+                    out[i] = reconstruct_on(prob, ubar, i, S)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# balanced-stencil re-selection (Sec. 3.2, last paragraph).  Readings: the
+# neighbourhood is the stencil S(i); a value is out of range when it leaves
+# [min, max] of the stencil averages by more than balance_margin times the
+# range of the averages over the mesh (2 %: a smooth extremum exceeds its
+# stencil's range by O(h^2), 1.2 % of the range on the 12 x 12 triangle mesh
+# with the smooth Burgers data, 0.34 % on 24 x 24, while overshoots at a jump
+# are several % of the jump; a margin also keeps averages that equal up to
+# rounding (flat regions) from deciding the test);
+# the enlarged stencil is the (ceil(ring) + 1)-vertex ring; the new stencil
+# keeps the centre and its facet neighbours and fills each side of the plane
+# through x_i normal to grad u(x_i) up to half of the old stencil size with
+# the side's nearest cells (ties by index; s <= 0 counts as the minus side),
+# topping up from the other side when one runs short.
+# ----------------------------------------------------------------------------
+
+def cell_facet_points(prob, i):
+    X = prob.geo.coords[i]
+    out = []
+    for f in range(prob.dim + 1):
+        pts, _ = facet_rule(np.delete(X, f, axis=0))
+        out.extend(pts)
+    return out
+
+
+def out_of_range(prob, ubar, i, dvec):
+    uS = np.asarray([ubar[j] for j in prob.stencils[i]])
+    lo, hi = float(np.min(uS)), float(np.max(uS))
+    tol = prob.balance_margin * (float(np.max(ubar)) - float(np.min(ubar)))
+    vals = [prob.eval_poly(dvec, i, x) for x in cell_facet_points(prob, i)]
+    return any(v < lo - tol or v > hi + tol for v in vals)
+
+
+def balanced_stencil(prob, i, dvec):
+    """The balanced stencil of cell i from its reconstruction dvec (the
+    gradient direction is its first-order coefficients), or None when the
+    gradient vanishes."""
+    g = np.asarray(dvec[1:1 + prob.dim], dtype=np.float64)
+    if not np.any(g != 0.0):
+        return None
+    n = len(prob.stencils[i])
+    face = set(int(j) for j in prob.face_nbrs[i])
+    steps = ["vertex"] * (int(math.ceil(prob.ring - 1e-9)) + 1)
+    cands = sorted(k_ring(i, steps, prob.nbr) - {i})
+    side, dist = {}, {}
+    for j in cands:
+        dx = min_image(prob.geo.centroid[j] - prob.geo.centroid[i], prob.period)
+        side[j] = float(np.dot(dx, g)) > 0.0
+        dist[j] = float(np.dot(dx, dx))
+    quota = {True: (n - 1 + 1) // 2, False: (n - 1) // 2}
+    chosen = set(face)
+    for j in face:
+        quota[side[j]] -= 1
+    pools = {sd: sorted((j for j in cands if side[j] == sd and j not in face), key=lambda j: (dist[j], j))
+             for sd in (True, False)}
+    for sd in (True, False):
+        take = max(0, quota[sd])
+        chosen.update(pools[sd][:take])
+        pools[sd] = pools[sd][take:]
+    rest = sorted(pools[True] + pools[False], key=lambda j: (dist[j], j))
+    while len(chosen) < n - 1 and rest:
+        chosen.add(rest.pop(0))
+    return [i] + sorted(chosen)
+
+
+def reconstruct_on(prob, ubar, i, S):
+    """WLS-ENO reconstruction of cell i on the stencil S (centre first)."""
+    A = moment_matrix(prob.geo, S, i, prob.p, prob.period)
+    face = set(int(j) for j in prob.face_nbrs[i])
+    uS = np.asarray([ubar[j] for j in S])
+    omega = wls_eno_weights(uS, [j in face for j in S], prob.geo.h[i], prob.eps, prob.alpha_c)
+    dvec, _, _ = scaled_wls_solve(A, omega, uS, prob.rank_tol)
+    return dvec
 
 
 def facet_states(prob, coeffs, L, fL, R):

@@ -466,3 +466,61 @@ def test_centre_weight_dominates_facet_neighbours():
         wf = [w[k] for k, j in enumerate(S) if j in face]
         assert len(wf) == 3
         assert w[0] >= 1.5 * max(wf) * (1 - 1e-15)
+
+
+# ---------------------------------------------------------------------------
+# balanced-stencil re-selection (Sec. 3.2, last paragraph)
+# ---------------------------------------------------------------------------
+
+def test_balanced_stencil_selection_invariants():
+    """The re-selected stencil keeps the centre (first) and its facet
+    neighbours, has at least the old size, and fills both sides of the plane
+    normal to the gradient up to their quotas (nearest cells first)."""
+    mesh = synth.tri_mesh(12, jitter=0.2, seed=3)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
+    rng = np.random.default_rng(8)
+    for i in rng.choice(prob.N, 12, replace=False):
+        i = int(i)
+        a = rng.uniform(0, 2 * np.pi)
+        d = np.zeros(prob.m)
+        d[1:3] = (np.cos(a), np.sin(a))
+        S = O.balanced_stencil(prob, i, d)
+        n = len(prob.stencils[i])
+        assert S[0] == i and len(S) >= n and len(set(S)) == len(S)
+        assert set(prob.face_nbrs[i]) <= set(S)
+        g = d[1:3]
+        side = {j: float(np.dot(O.min_image(prob.geo.centroid[j] - prob.geo.centroid[i], prob.period), g)) > 0
+                for j in S[1:]}
+        plus = sum(side.values())
+        minus = len(S) - 1 - plus
+        face_plus = sum(side[j] for j in prob.face_nbrs[i])
+        face_minus = len(prob.face_nbrs[i]) - face_plus
+        assert abs(plus - minus) <= 1 + abs(face_plus - face_minus), (plus, minus)
+
+
+def test_balanced_stencil_of_a_symmetric_1d_stencil_is_itself():
+    """On a uniform 1-D grid the k-ring is already balanced about the
+    centroid: the re-selection returns the same stencil for either sign of
+    the gradient."""
+    mesh = synth.periodic_line_mesh(20)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=5, ring=2.0)
+    for sgn in (1.0, -1.0):
+        d = np.zeros(prob.m)
+        d[1] = sgn
+        assert O.balanced_stencil(prob, 10, d) == prob.stencils[10]
+
+
+def test_balancing_leaves_smooth_data_alone_and_reduces_overshoot_at_a_jump():
+    """Smooth data: no facet value leaves its stencil's range, so the
+    balanced scheme's residual is the plain one.  A jump: the balanced
+    reconstructions leave the range at fewer cells."""
+    mesh = synth.tri_mesh(12, jitter=0.2, seed=3)
+    plain = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
+    bal = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS, balanced=True)
+    smooth = synth.burgers_2d_initial(mesh)
+    assert np.array_equal(O.residual(plain, smooth), O.residual(bal, smooth))
+    jump = synth.cell_averages(mesh, lambda P: (P[:, 0] + 0.4 * P[:, 1] > 0.55).astype(float), k=8)
+    before = [O.out_of_range(plain, jump, i, d) for i, d in enumerate(O.reconstruct_all(plain, jump))]
+    after = [O.out_of_range(plain, jump, i, d) for i, d in enumerate(O.reconstruct_all(bal, jump))]
+    assert sum(before) > 0
+    assert sum(after) < sum(before), (sum(before), sum(after))
