@@ -123,6 +123,23 @@ typedef struct {
  *             facet values only (coeffs must be NULL: there is no single
  *             polynomial per cell); flagged_cells counts (cell, facet) solves
  *             above the flag threshold.
+ * balanced:   scalar equations only, 0 or 1: the balanced-stencil
+ *             re-selection of Sec. 3.2.  After each reconstruction, a cell
+ *             whose value at any of its facet quadrature points leaves
+ *             [min, max] of its stencil's averages by more than
+ *             balance_margin * (max - min of the averages over its mesh) is
+ *             re-solved (FP64) on a stencil of the same size taken from the
+ *             (ceil(ring) + 1)-vertex ring: the centre, its facet neighbours
+ *             and, on each side of the plane through its centroid normal to
+ *             the reconstructed gradient, its nearest cells up to half the
+ *             stencil (the side (x_j - x_i).grad u > 0 takes floor(n/2), the
+ *             other floor((n-1)/2); a short side is made up from the nearest
+ *             remaining cells).  Cells with a zero gradient or an
+ *             ill-conditioned new system keep the plain result.  The
+ *             re-selected cells are counted in
+ *             wlseno_diagnostics.balanced_cells; the adjoint is not available.
+ * balance_margin: the range test's margin as a share of the averages' range
+ *             (>= 0; e.g. 0.02).
  *
  * WLSENO_EULER (2-D): n_comp = 4 conserved variables (rho, rho u, rho v, E),
  * each reconstructed with its own weights (componentwise WLS-ENO); LF alpha
@@ -140,6 +157,8 @@ typedef struct {
   int precision;
   double gamma;
   int characteristic;
+  int balanced;
+  double balance_margin;
 } wlseno_scheme;
 
 typedef struct {
@@ -159,7 +178,8 @@ typedef struct {
 
 /* Kernel kinds of the per-kind launch counts and timings.  RECONSTRUCT is
  * the main reconstruction kernel; FIXUP the follow-ups that redo the cells it
- * flags (refinement sweep, pivoted path); DT the per-step preparation (CFL
+ * flags (refinement sweep, pivoted path) and the balanced-stencil range test
+ * and re-selection; DT the per-step preparation (CFL
  * time step and, in FP32-bulk, the FP32 split of the state). */
 enum { WLSENO_KERNEL_MOMENTS = 0, WLSENO_KERNEL_RECONSTRUCT = 1, WLSENO_KERNEL_FLUX = 2,
        WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_KERNEL_FIXUP = 5,
@@ -177,6 +197,8 @@ typedef struct {
                                                       wlseno_set_timing (timing
                                                       mode only)                */
   int64_t positivity_fallbacks; /* Euler cells on first order (last call)      */
+  int64_t balanced_cells;  /* cells re-solved on balanced stencils, summed over
+                              the reconstructions of the last call            */
 } wlseno_diagnostics;
 
 /* Create a context on CUDA device `device`; copies *scheme.
@@ -291,7 +313,9 @@ wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host);
  * recomputed.  dt: > 0 fixed for every mesh, < 0 the per-mesh steps of
  * wlseno_set_mesh_dt (0 is rejected: a CFL step is not differentiated).
  * All arrays [n_cells] (n_comp = 1), host or device; the first call
- * allocates the adjoint's work arrays.  Errors: STATE, INVALID_ARG, CUDA. */
+ * allocates the adjoint's work arrays.  Scalar equations on 2-D and 3-D
+ * meshes with fixed stencils (balanced = 0), else INVALID_ARG.
+ * Errors: STATE, INVALID_ARG, CUDA. */
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
                                   const double* gbar_next, double* gbar_n, void* stream);
 

@@ -12,6 +12,10 @@
 
 using namespace wlseno;
 
+// device counters: flagged, rank deficient, nonfinite, positivity fallbacks,
+// balanced re-selections
+constexpr int kCounters = 5;
+
 struct wlseno_ctx {
   int device = 0;
   wlseno_scheme scheme{};
@@ -40,6 +44,7 @@ struct wlseno_ctx {
   float* d_rbuf = nullptr;       // [N][refine_record_floats(m)] FP32-bulk refine records
   float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
   float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk)
+  BalanceWork bal{};             // balanced-stencil re-selection (when the scheme asks for it)
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
   cudaStream_t cap_stream = nullptr;
@@ -220,8 +225,8 @@ cudaError_t split_state(wlseno_ctx* ctx, const double* u, float2* pair, cudaStre
 
 // pair: the FP32 pairs of ubar for the FP32-bulk thread-per-cell kernel; when
 // null they are made here, in the scratch slot of d_pair.
-cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
-                            cudaStream_t s, float* fdev = nullptr, const float2* pair = nullptr) {
+cudaError_t reconstruct_plain(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
+                              cudaStream_t s, float* fdev, const float2* pair) {
   ReconOut out{coeffs, fdev ? nullptr : fvals, ctx->d_counters, fdev};
   const DeviceMesh& dm = ctx->dm;
   const bool f32 = ctx->scheme.precision == WLSENO_FP32_BULK;
@@ -259,6 +264,21 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
                : launch_reconstruct_inst<double, DD, MM>(dm, ctx->sp, ctx->G, ctx->R, ubar, out, s);
   });
   scope.done(e == cudaSuccess ? 1 : 0);
+  return e;
+}
+
+// The reconstruction followed, when the scheme asks for it, by the
+// balanced-stencil re-selection of the cells out of range (counted as
+// follow-up kernels).
+cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs, double* fvals,
+                            cudaStream_t s, float* fdev = nullptr, const float2* pair = nullptr) {
+  cudaError_t e = reconstruct_plain(ctx, ubar, coeffs, fvals, s, fdev, pair);
+  if (e != cudaSuccess || !ctx->scheme.balanced) return e;
+  const ReconOut out{coeffs, fdev ? nullptr : fvals, ctx->d_counters, fdev};
+  int nl = 0;
+  KernelScope scope(ctx, WLSENO_KERNEL_FIXUP, s);
+  e = launch_balance(ctx->dm, ctx->sp, ctx->bal, ubar, out, s, &nl);
+  scope.done(e == cudaSuccess ? nl : 0);
   return e;
 }
 
@@ -400,6 +420,10 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
     return WLSENO_ERR_INVALID_ARG;
   if (scheme->characteristic != 0 && (scheme->characteristic != 1 || scheme->pde != WLSENO_EULER))
     return WLSENO_ERR_INVALID_ARG;
+  if (scheme->balanced != 0 &&
+      (scheme->balanced != 1 || scheme->pde == WLSENO_EULER || !(scheme->balance_margin >= 0.0) ||
+       !std::isfinite(scheme->balance_margin)))
+    return WLSENO_ERR_INVALID_ARG;
   if (!(scheme->eps > 0.0) || !(scheme->alpha_c > 0.0) || !(scheme->rank_tol >= 0.0))
     return WLSENO_ERR_INVALID_ARG;
   int n_dev = 0;
@@ -446,7 +470,11 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   ctx->adj = AdjointWork{};
   std::string err;
   HostSetup& H = ctx->host;
-  wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err);
+  // balanced stencils draw from the (ceil(ring) + 1)-vertex ring
+  const int bal_steps =
+      ctx->scheme.balanced && opts ? static_cast<int>(std::ceil(opts->ring - 1e-9)) + 1 : 0;
+  ctx->bal = BalanceWork{};
+  wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err, bal_steps);
   if (st != WLSENO_OK) return fail(ctx, st, err);
   if (ctx->scheme.pde == WLSENO_EULER && H.dim != 2)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the Euler path is built for 2-D meshes");
@@ -529,7 +557,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   const int NP = (H.dim + 1) * H.nq;
   if ((st = dalloc(ctx, &dm.A64, H.nnz * H.m)) || (st = dalloc(ctx, &dm.A32, H.nnz * H.m)) ||
       (st = dalloc(ctx, &ctx->d_dt, H.n_meshes)) || (st = dalloc(ctx, &ctx->d_lmax, H.n_meshes)) ||
-      (st = dalloc(ctx, &ctx->d_counters, 4)) || (st = dalloc(ctx, &ctx->d_fvals, C * N * NP)) ||
+      (st = dalloc(ctx, &ctx->d_counters, kCounters)) || (st = dalloc(ctx, &ctx->d_fvals, C * N * NP)) ||
       (st = dalloc(ctx, &ctx->d_k1, C * N)) || (st = dalloc(ctx, &ctx->d_k2, C * N)))
     return st;
   dm.nmax = H.max_n;
@@ -543,7 +571,23 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) || (st = dalloc(ctx, &ctx->d_pair, 3 * C * N)) ||
        (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N))))
     return st;
-  cudaError_t e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
+  if (ctx->scheme.balanced) {
+    BalanceWork& b = ctx->bal;
+    std::vector<int32_t> bp(N + 1), bi(H.bal_idx.size());
+    for (int64_t i = 0; i <= N; ++i) bp[i] = static_cast<int32_t>(H.bal_ptr[i]);
+    for (size_t k = 0; k < bi.size(); ++k) bi[k] = static_cast<int32_t>(H.bal_idx[k]);
+    int32_t *d_bp = nullptr, *d_bi = nullptr;
+    if ((st = upload(ctx, &d_bp, bp)) || (st = upload(ctx, &d_bi, bi)) ||
+        (st = dalloc(ctx, &b.state, 1 + 2 * static_cast<size_t>(H.n_meshes))) ||
+        (st = dalloc(ctx, &b.list, N)))
+      return st;
+    b.cand_ptr = d_bp;
+    b.cand_idx = d_bi;
+    b.count = ctx->d_counters + 4;
+    b.margin = ctx->scheme.balance_margin;
+    b.n_meshes = H.n_meshes;
+  }
+  cudaError_t e = cudaMemset(ctx->d_counters, 0, kCounters * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
   ctx->d_in = ctx->d_out = ctx->d_coef = ctx->d_fv_out = nullptr;
   ctx->built = true;
@@ -592,7 +636,7 @@ wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* co
   const bool fv_host = facet_values && !is_device_pointer(facet_values);
   if (coef_host && !ctx->d_coef && (st = dalloc(ctx, &ctx->d_coef, C * N * m))) return st;
   if (fv_host && !ctx->d_fv_out && (st = dalloc(ctx, &ctx->d_fv_out, C * N * NP))) return st;
-  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
   if (ctx->scheme.characteristic) {
     // facet values of all components at once (there is no per-cell polynomial)
@@ -646,7 +690,7 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
   }
   if (out_host && !ctx->d_out && (st = dalloc(ctx, &ctx->d_out, C * N))) return st;
   double* res = out_host ? ctx->d_out : residual;
-  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
   if ((e = stage_all(ctx, u, nullptr, 0.0, 1.0, true, res, s)) != cudaSuccess)
     return cuda_fail(ctx, e, "residual kernels");
@@ -683,7 +727,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
     u = ctx->d_in;
   }
-  if ((e = cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ctx->d_counters, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
   // one TVD-RK3 step on stream `st` (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta))
   auto enqueue_step = [&](cudaStream_t st) -> cudaError_t {
@@ -865,6 +909,9 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for the scalar equations");
   if (ctx->dm.dim == 1)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for 2-D and 3-D meshes");
+  if (ctx->scheme.balanced)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG,
+                "the adjoint is built for fixed stencils (balanced stencils depend on the solution)");
   if (dt < 0.0 && !ctx->mesh_dt_set)
     return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
   DeviceGuard guard(ctx->device);
@@ -1011,7 +1058,7 @@ wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out) {
   for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) out->launches_by_kind[k] = ctx->by_kind[k];
   if (!ctx->built) return WLSENO_OK;
   DeviceGuard guard(ctx->device);
-  unsigned long long c[4] = {0, 0, 0, 0};
+  unsigned long long c[kCounters] = {0, 0, 0, 0, 0};
   cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
   if (e == cudaSuccess) e = cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read counters");
@@ -1019,6 +1066,7 @@ wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out) {
   out->rank_deficient = static_cast<int64_t>(c[1]);
   out->nonfinite = static_cast<int64_t>(c[2]);
   out->positivity_fallbacks = static_cast<int64_t>(c[3]);
+  out->balanced_cells = static_cast<int64_t>(c[4]);
   for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) out->launches_by_kind[k] = ctx->by_kind[k];
   for (const auto& t : ctx->timed) {
     float ms = 0.0f;

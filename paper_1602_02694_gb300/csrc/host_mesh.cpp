@@ -86,7 +86,7 @@ void for_cells_sharing_edge(const MeshWork& w, int64_t a, int64_t b, F&& fn) {
 
 wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
                                const wlseno_stencil_opts* opts, HostSetup* out,
-                               std::string* err) {
+                               std::string* err, int balance_steps) {
   if (!meshes || n_meshes <= 0 || !opts || !out) {
     *err = "null argument or n_meshes <= 0";
     return WLSENO_ERR_INVALID_ARG;
@@ -145,6 +145,7 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
   S.fgeo.assign(N * nf * 4, 0.0);
   S.fpts.assign(N * nf * nq * dim, 0.0);
   S.row_ptr.assign(N + 1, 0);
+  if (balance_steps > 0) S.bal_ptr.assign(N + 1, 0);
   S.cols.clear();
 
   std::vector<double> own_normal(N * nf * 3, 0.0), own_area(N * nf, 0.0);
@@ -353,6 +354,7 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
     std::vector<int64_t> stamp(nc, -1);
     std::vector<int64_t> set, grown, outer;
     std::vector<int> outer_steps(static_cast<int>(std::floor(opts->ring + 1e-9)) + 1, kVertex);
+    const std::vector<int> bal_steps(std::max(balance_steps, 0), kVertex);
     auto add = [&](int64_t x, int64_t tag, std::vector<int64_t>& into) {
       if (stamp[x] != tag) {
         stamp[x] = tag;
@@ -439,10 +441,23 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
       }
       S.row_ptr[gc + 1] = static_cast<int64_t>(members.size());
       for (int64_t y : members) S.cols.push_back(base + y);
+      if (balance_steps > 0) {
+        grow(bal_steps, c);
+        std::sort(set.begin() + 1, set.end());
+        S.bal_ptr[gc + 1] = static_cast<int64_t>(set.size()) - 1;
+        for (size_t t = 1; t < set.size(); ++t) S.bal_idx.push_back(base + set[t]);
+      }
     }
     base += nc;
   }
   for (int64_t i = 0; i < N; ++i) S.row_ptr[i + 1] += S.row_ptr[i];
+  if (balance_steps > 0) {
+    for (int64_t i = 0; i < N; ++i) S.bal_ptr[i + 1] += S.bal_ptr[i];
+    if (S.bal_ptr[N] >= (int64_t(1) << 31)) {
+      *err = "balanced-stencil candidates exceed 32-bit offsets";
+      return WLSENO_ERR_STENCIL;
+    }
+  }
   S.nnz = S.row_ptr[N];
   S.max_n = 0;
   S.min_n = 1 << 30;

@@ -43,11 +43,17 @@ struct HostSetup {
   // with stencil row t >= 1 of cell c equal to j, ordered by (c, t)
   std::vector<int64_t> tr_ptr;    // [N+1]
   std::vector<int64_t> tr_slot;   // [nnz - N]
+  // balanced-stencil candidates (when asked for): the cells of the enlarged
+  // ring of each cell, centre excluded, ascending
+  std::vector<int64_t> bal_ptr;   // [N+1]
+  std::vector<int64_t> bal_idx;
 };
 
+// balance_steps > 0 also collects, for every cell, the cells within that
+// many vertex-sharing steps (the balanced-stencil candidates).
 wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
                                const wlseno_stencil_opts* opts, HostSetup* out,
-                               std::string* err);
+                               std::string* err, int balance_steps = 0);
 
 // ---------------------------------------------------------------------------
 // device-side views handed to the kernel launchers
@@ -126,6 +132,22 @@ struct ReconOut {
   // average, value = ubar_i + fdev (written instead of fvals when set)
   float* fdev = nullptr;    // [N][dim+1][nq]
 };
+
+// Balanced-stencil re-selection (k_balance.cu).
+struct BalanceWork {
+  const int32_t* cand_ptr;   // [N+1]
+  const int32_t* cand_idx;   // enlarged-ring candidates, centre excluded, ascending
+  unsigned long long* state; // [1 + 2 n_meshes]: list length, then per mesh the
+                             // order keys of max u and of max -u
+  int* list;                 // [N] cells out of range
+  unsigned long long* count; // cells re-solved on a balanced stencil (accumulated)
+  double margin;             // out of range: beyond [min, max] by margin * range of u
+  int n_meshes;
+};
+// Range test and re-selection on the output of a reconstruction of ubar;
+// overwrites the outputs of the re-solved cells.  *launches = kernels run.
+cudaError_t launch_balance(const DeviceMesh& dm, const SchemeParams& sp, const BalanceWork& bw,
+                           const double* ubar, const ReconOut& out, cudaStream_t s, int* launches);
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_moments(const DeviceMesh& dm, cudaStream_t s);

@@ -42,7 +42,8 @@ class wlseno_scheme(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("n_comp", ctypes.c_int), ("velocity", ctypes.c_double * 3),
                 ("eps", ctypes.c_double), ("alpha_c", ctypes.c_double), ("rank_tol", ctypes.c_double),
                 ("kappa_flag", ctypes.c_double), ("precision", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("characteristic", ctypes.c_int)]
+                ("characteristic", ctypes.c_int), ("balanced", ctypes.c_int),
+                ("balance_margin", ctypes.c_double)]
 
 
 class wlseno_info(ctypes.Structure):
@@ -62,7 +63,7 @@ class wlseno_diagnostics(ctypes.Structure):
                 ("last_dt", ctypes.c_double),
                 ("launches_by_kind", ctypes.c_int64 * len(KERNEL_KINDS)),
                 ("kernel_ms", ctypes.c_double * len(KERNEL_KINDS)),
-                ("positivity_fallbacks", ctypes.c_int64)]
+                ("positivity_fallbacks", ctypes.c_int64), ("balanced_cells", ctypes.c_int64)]
 
 
 # every symbol include/wlseno.h declares, with its C signature
@@ -154,13 +155,15 @@ class Context:
 
     def __init__(self, device: int = 0, pde="advection", velocity=(1.0, 1.0, 0.0), eps=1e-2,
                  alpha_c=1.5, rank_tol=1e-10, kappa_flag=1e3, precision="fp64", n_comp=None,
-                 gamma=1.4, characteristic=False):
+                 gamma=1.4, characteristic=False, balanced=False, balance_margin=0.02):
         self.lib = load_library()
         sch = wlseno_scheme()
         sch.pde = _PDE[pde] if isinstance(pde, str) else int(pde)
         sch.n_comp = n_comp if n_comp is not None else (4 if sch.pde == EULER else 1)
         sch.gamma = gamma
         sch.characteristic = 1 if characteristic else 0
+        sch.balanced = 1 if balanced else 0
+        sch.balance_margin = balance_margin
         for a in range(3):
             sch.velocity[a] = float(velocity[a]) if a < len(velocity) else 0.0
         sch.eps, sch.alpha_c, sch.rank_tol, sch.kappa_flag = eps, alpha_c, rank_tol, kappa_flag
@@ -315,6 +318,7 @@ class Context:
         out["launches_by_kind"] = dict(zip(KERNEL_KINDS, list(d.launches_by_kind)))
         out["kernel_ms"] = dict(zip(KERNEL_KINDS, list(d.kernel_ms)))
         out["positivity_fallbacks"] = d.positivity_fallbacks
+        out["balanced_cells"] = d.balanced_cells
         return out
 
     def set_timing(self, enable=True):

@@ -61,3 +61,17 @@ def test_create_reports_missing_device(lib):
     sch.pde, sch.n_comp, sch.eps, sch.alpha_c, sch.rank_tol = 0, 1, 1e-2, 1.5, 1e-10
     h = ctypes.c_void_p()
     assert lib.wlseno_create(ctypes.byref(h), 0, ctypes.byref(sch)) == -4
+
+
+def test_balanced_option_is_validated_before_any_cuda_call(lib):
+    """balanced: 0 or 1, scalar equations only, a finite margin >= 0."""
+    base = dict(pde=1, n_comp=1, eps=1e-2, alpha_c=1.5, rank_tol=1e-10, balance_margin=0.02)
+    bad = [dict(balanced=2), dict(balanced=1, pde=2, n_comp=4, gamma=1.4),
+           dict(balanced=1, balance_margin=-1.0), dict(balanced=1, balance_margin=float("nan")),
+           dict(balanced=1, balance_margin=float("inf"))]
+    for change in bad:
+        sch = W.wlseno_scheme()
+        for k, v in {**base, **change}.items():
+            setattr(sch, k, v)
+        h = ctypes.c_void_p()
+        assert lib.wlseno_create(ctypes.byref(h), 0, ctypes.byref(sch)) == -1, change
