@@ -511,9 +511,9 @@ def test_balanced_stencil_of_a_symmetric_1d_stencil_is_itself():
 
 
 def test_balancing_leaves_smooth_data_alone_and_reduces_overshoot_at_a_jump():
-    """Smooth data: no facet value leaves its stencil's range, so the
-    balanced scheme's residual is the plain one.  A jump: the balanced
-    reconstructions leave the range at fewer cells."""
+    """Smooth data: no facet value leaves its stencil's range by the margin,
+    so the balanced scheme's residual is the plain one.  A jump and random
+    data: the balanced reconstructions leave the range at fewer cells."""
     mesh = synth.tri_mesh(12, jitter=0.2, seed=3)
     plain = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
     bal = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS, balanced=True)
@@ -524,3 +524,9 @@ def test_balancing_leaves_smooth_data_alone_and_reduces_overshoot_at_a_jump():
     after = [O.out_of_range(plain, jump, i, d) for i, d in enumerate(O.reconstruct_all(bal, jump))]
     assert sum(before) > 0
     assert sum(after) < sum(before), (sum(before), sum(after))
+    # random averages: every local extremum tests the range; balancing keeps
+    # most reconstructions inside it (Sec. 3.2: "typically" within range)
+    rnd = np.random.default_rng(4).uniform(-1.0, 1.0, plain.N)
+    before = sum(O.out_of_range(plain, rnd, i, d) for i, d in enumerate(O.reconstruct_all(plain, rnd)))
+    after = sum(O.out_of_range(plain, rnd, i, d) for i, d in enumerate(O.reconstruct_all(bal, rnd)))
+    assert before >= 10 and 2 * after <= before, (before, after)
