@@ -45,6 +45,10 @@ struct wlseno_ctx {
   float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
   float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk)
   BalanceWork bal{};             // balanced-stencil re-selection (when the scheme asks for it)
+  // side stream of the pivoted-path kernel, forked from and joined to the
+  // caller's stream around the refinement sweep
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool mesh_dt_set = false;      // d_dt holds per-mesh steps from wlseno_set_mesh_dt
   // one captured RK step, replayed for multi-step calls
   cudaStream_t cap_stream = nullptr;
@@ -240,7 +244,7 @@ cudaError_t reconstruct_plain(wlseno_ctx* ctx, const double* ubar, double* coeff
     return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pair};
+    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pair, ctx->side, ctx->ev_fork, ctx->ev_join};
     e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
       constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
       return f32 ? launch_recon_tpc_inst<float, DD, MM>(dm, ctx->sp, ubar, out, wl, s)
@@ -452,6 +456,9 @@ void wlseno_destroy(wlseno_ctx* ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     free_all(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   }
@@ -589,6 +596,12 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   }
   cudaError_t e = cudaMemset(ctx->d_counters, 0, kCounters * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
+  if (ctx->scheme.precision == WLSENO_FP32_BULK && !ctx->side) {
+    if ((e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(ctx, e, "side stream");
+  }
   ctx->d_in = ctx->d_out = ctx->d_coef = ctx->d_fv_out = nullptr;
   ctx->built = true;
   return WLSENO_OK;

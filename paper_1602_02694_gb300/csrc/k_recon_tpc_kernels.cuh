@@ -203,7 +203,7 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
     v[0] = __int_as_float(static_cast<int>(i));
     v[1] = __int_as_float(dm.st_ptr[i]);
     v[2] = __int_as_float(n);
-    v[3] = 0.0f;
+    v[3] = static_cast<float>(wc);
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       v[4 + c] = static_cast<float>(x[c]);
@@ -213,8 +213,12 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
     for (int k = 0; k < M; ++k)
 #pragma unroll
       for (int j = k + 1; j < M; ++j) v[4 + 2 * M + strict_upper_index(M, k, j)] = static_cast<float>(f.U[k][j]);
+    constexpr int RE = refine_record_eps(M);
+    v[RE] = static_cast<float>(eh2);
+    v[RE + 1] = __int_as_float(__double2loint(ui));
+    v[RE + 2] = __int_as_float(__double2hiint(ui));
 #pragma unroll
-    for (int c = 4 + 2 * M + M * (M - 1) / 2; c < RW; ++c) v[c] = 0.0f;
+    for (int c = RE + 3; c < RW; ++c) v[c] = 0.0f;
     const int slot = atomicAdd(&work.counts[1], 1);
     float4* rec = reinterpret_cast<float4*>(work.refine_buf + static_cast<int64_t>(slot) * RW);
 #pragma unroll
@@ -230,50 +234,62 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
 // b - A x formed in FP64 from the FP64 moments and deviations (the FP32
 // factor only preconditions the correction).  L lanes share a
 // cell, lane l taking rows l, l+L, ..., l+(RPL-1)L (the thread-per-cell path
-// serves stencils of at most L*RPL rows); every load of those rows is issued
-// before any arithmetic, so a cell costs about one memory round trip.  The
-// partial sums are combined by shuffles.  It overwrites the main kernel's
-// outputs for those cells.
+// serves stencils of at most L*RPL rows).  The kernel is a latency chain on
+// few warps, so its dependent loads are kept to three levels: the list length
+// and the first record together; then everything the record addresses (the
+// stencil indices, both copies of the moment rows, the lane's facet point;
+// the record carries the weights' eps h^2 and w_c and ubar_i); then ubar of the
+// stencil cells.  The partial sums are combined by shuffles.  It overwrites
+// the main kernel's outputs for those cells.
 template <int DIM, int M, int L, int RPL>
 __global__ void __launch_bounds__(64)
-refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-              double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
-              TpcWork work) {
-  constexpr int NF = DIM + 1;
-  constexpr int NP = NF * nq_of(DIM);
+refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict__ coeffs,
+              double* __restrict__ fvals, float* __restrict__ fdev, TpcWork work) {
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
+  static_assert(NP <= L && M <= L, "one facet point and one coefficient per lane");
   constexpr int kPerWarp = 32 / L;
-  const int count = work.counts[1];
+  constexpr int RW = refine_record_floats(M);
+  constexpr int RE = refine_record_eps(M);
   const int lane = threadIdx.x % L;
   const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / 32;
   const int64_t warps = gridDim.x * static_cast<int64_t>(blockDim.x) / 32;
-  constexpr int RW = refine_record_floats(M);
-  for (int64_t base = warp * kPerWarp; base < count; base += warps * kPerWarp) {
-    const int64_t slot = base + (threadIdx.x % 32) / L;
-    const bool valid = slot < count;
-    // the cell's record (the same address for all L lanes: broadcast loads)
-    float r[RW];
-    {
-      const float4* rec = reinterpret_cast<const float4*>(work.refine_buf + (valid ? slot : 0) * RW);
+  const int64_t sub = (threadIdx.x % 32) / L;
+  const int64_t last = dm.N - 1;  // the record buffer holds N records
+  float r[RW];
+  auto load_record = [&](int64_t slot) {
+    const float4* rec = reinterpret_cast<const float4*>(work.refine_buf + (slot < last ? slot : last) * RW);
 #pragma unroll
-      for (int q = 0; q < RW / 4; ++q) {
-        const float4 v = rec[q];
-        r[4 * q] = v.x;
-        r[4 * q + 1] = v.y;
-        r[4 * q + 2] = v.z;
-        r[4 * q + 3] = v.w;
-      }
+    for (int q = 0; q < RW / 4; ++q) {
+      const float4 v = rec[q];
+      r[4 * q] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
     }
+  };
+  const int64_t first = warp * kPerWarp;
+  load_record(first + sub);  // issued together with the list length
+  const int count = work.counts[1];
+  for (int64_t base = first; base < count; base += warps * kPerWarp) {
+    if (base != first) load_record(base + sub);
+    const int64_t slot = base + sub;
+    const bool valid = slot < count;
     const int64_t i = valid ? __float_as_int(r[0]) : 0;
     const int beg = __float_as_int(r[1]);
     const int n = valid ? __float_as_int(r[2]) : 0;
-    // all loads of this lane's rows next, from the CSR layout: a cell's rows
-    // are contiguous, so the group's loads share cache lines
+    const float wc = r[3];
+    const float e = r[RE];
+    const double ui = __hiloint2double(__float_as_int(r[RE + 2]), __float_as_int(r[RE + 1]));
+    // every load the record addresses, stencil indices first (the longest chain)
     int64_t jrow[RPL];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int t = lane + q * L;
       jrow[q] = t < n ? dm.st_idx[beg + t] : i;
     }
+    float yy[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) yy[a] = lane < NP ? dm.fpts32[(i * NP + lane) * DIM + a] : 0.0f;
     double a[RPL][M];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -298,29 +314,27 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
     for (int q = 0; q < RPL; ++q) {
       const int t = lane + q * L;
       const float* row = dm.A32 + static_cast<int64_t>(beg + t) * M;
+      if constexpr (M % 2 == 0) {  // rows of 8-byte multiples: 8-byte loads
+        const float2* row2 = reinterpret_cast<const float2*>(row);
 #pragma unroll
-      for (int c = 0; c < M; ++c) a32[q][c] = t < n ? row[c] : 0.0f;
+        for (int c = 0; c < M; c += 2) {
+          const float2 v = t < n ? row2[c / 2] : make_float2(0.0f, 0.0f);
+          a32[q][c] = v.x;
+          a32[q][c + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < M; ++c) a32[q][c] = t < n ? row[c] : 0.0f;
+      }
     }
-    const double ui = ubar[i];
     double uj[RPL];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) uj[q] = ubar[jrow[q]];
     double x[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) x[c] = static_cast<double>(r[4 + c]);
-    // weights of the FP64 problem (Sec. 3.1.2), to FP32 relative accuracy:
+    // weights of the FP64 problem (Sec. 3.1.2) to FP32 relative accuracy:
     // only the residual needs FP64 (its cancellation), A^T W^2 r does not
-    const double hi = dm.h[i];
-    const float e = static_cast<float>(sp.eps * hi * hi);
-    float bmin = INFINITY;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int nb = dm.nbr[i * NF + f];
-      if (nb >= 0) {
-        const float dv = static_cast<float>(ubar[nb >> 2] - ui);
-        bmin = fminf(bmin, fmaf(dv, dv, e));
-      }
-    }
     float g[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) g[c] = 0.0f;
@@ -329,8 +343,7 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
       const int t = lane + q * L;
       const double dev = uj[q] - ui;
       const float devf = static_cast<float>(dev);
-      const float beta = t == 0 ? bmin : fmaf(devf, devf, e);
-      const float w = (t == 0 ? static_cast<float>(sp.alpha_c) * e : e) / beta;
+      const float w = t == 0 ? wc : e / fmaf(devf, devf, e);
       double fit0 = 0.0, fit1 = 0.0;
 #pragma unroll
       for (int c = 0; c < M; c += 2) {
@@ -370,16 +383,10 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
     if (coeffs) {
 #pragma unroll
       for (int c = 0; c < M; ++c)
-        if (c % L == lane)
+        if (c == lane)
           coeffs[i * M + c] = static_cast<double>(xh[c]) + static_cast<double>(dl[c]) + (c == 0 ? ui : 0.0);
     }
-    const float* P = dm.fpts32 + i * NP * DIM;
-#pragma unroll
-    for (int pt = 0; pt < NP; ++pt) {
-      if (pt % L != lane) continue;
-      float yy[DIM];
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) yy[q] = P[pt * DIM + q];
+    if (lane < NP) {
       float mono[M];
       eval_monomials<float, DIM, M>(yy, mono);
       float sh = 0.0f, sl = 0.0f;
@@ -389,9 +396,9 @@ refine_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
         sl = fmaf(dl[c], mono[c], sl);
       }
       if (fdev)
-        fdev[i * NP + pt] = sh + sl;
+        fdev[i * NP + lane] = sh + sl;
       else
-        fvals[i * NP + pt] = ui + static_cast<double>(sh) + static_cast<double>(sl);
+        fvals[i * NP + lane] = ui + static_cast<double>(sh) + static_cast<double>(sl);
     }
   }
 }
@@ -418,6 +425,15 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
   return cudaGetLastError();
 }
 
+// The pivoted cells, one lane group each: rows spread over the lanes.
+template <typename T, int DIM, int M>
+cudaError_t launch_list(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                        const ReconOut& out, const TpcWork& work, cudaStream_t s) {
+  if (dm.nmax <= 40)
+    return launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, work.group_list, work.counts, s);
+  return launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, work.group_list, work.counts, s);
+}
+
 // The follow-ups on the listed cells: the refinement sweep (FP32-bulk) and
 // the pivoted path; *launches receives the number of kernels launched.
 template <typename T, int DIM, int M>
@@ -432,17 +448,26 @@ cudaError_t launch_recon_fixup(const DeviceMesh& dm, const SchemeParams& sp, con
     constexpr int L = 16, RPL = 4, kThreads = 64;
     const int64_t want = (dm.N * L + kThreads - 1) / kThreads;
     const unsigned rblocks = static_cast<unsigned>(want < 8 * 152 ? want : 8 * 152);
+    // the pivoted path on the side stream when one is given (different cells,
+    // the same inputs): fork before the refinement, join after it
+    const bool fork = work.side && work.fork && work.join;
+    cudaStream_t sl = s;
+    if (fork) {
+      if ((e = cudaEventRecord(work.fork, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(work.side, work.fork, 0)) != cudaSuccess) return e;
+      sl = work.side;
+      if ((e = launch_list<T, DIM, M>(dm, sp, ubar, out, work, sl)) != cudaSuccess) return e;
+      ++*launches;
+      if ((e = cudaEventRecord(work.join, sl)) != cudaSuccess) return e;
+    }
     refine_kernel<DIM, M, L, RPL>
-        <<<rblocks, kThreads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals, out.fdev, work);
+        <<<rblocks, kThreads, 0, s>>>(dm, ubar, out.coeffs, out.fvals, out.fdev, work);
     ++*launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (fork) return cudaStreamWaitEvent(s, work.join, 0);
   }
-  // the pivoted cells, one lane group each: rows spread over the lanes
-  if (dm.nmax <= 40)
-    e = launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, work.group_list, work.counts, s);
-  else
-    e = launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, work.group_list, work.counts, s);
+  e = launch_list<T, DIM, M>(dm, sp, ubar, out, work, s);
   ++*launches;
   return e;
 }

@@ -166,16 +166,22 @@ struct TpcWork {
   // lo = fl32(ubar - hi), so ubar_j - ubar_i = (hi_j - hi_i) + (lo_j - lo_i)
   // to FP32 accuracy without FP64 arithmetic (required when refine_buf is set)
   const float2* upair;      // [N]
+  // optional side stream: the pivoted-path kernel runs there, concurrently
+  // with the refinement sweep (fork and join through the two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // pair[k] = (fl32(u[k]), fl32(u[k] - fl32(u[k]))) for k < n.
 cudaError_t launch_split_pairs(const double* u, float2* pair, int64_t n, cudaStream_t s);
 
 // One refine record (16-byte aligned, read with 16-byte loads): cell index,
-// first CSR row, row count and a zero (as int32), then the solution x (m),
-// D (m) and the strict upper triangle of U (m(m-1)/2), zero padded.
+// first CSR row and row count (as int32), the centre weight w_c, then the
+// solution x (m), D (m), the strict upper triangle of U (m(m-1)/2), eps h^2
+// and ubar_i (its FP64 bits as two words, low then high), zero padded.
+__host__ __device__ constexpr int refine_record_eps(int m) { return 4 + 2 * m + m * (m - 1) / 2; }
 __host__ __device__ constexpr int refine_record_floats(int m) {
-  return (4 + 2 * m + m * (m - 1) / 2 + 3) / 4 * 4;
+  return (refine_record_eps(m) + 3 + 3) / 4 * 4;
 }
 
 // Thread-per-cell reconstruction: the main kernel, then the follow-ups on
