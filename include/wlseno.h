@@ -109,8 +109,12 @@ typedef struct {
  *             the factor of W A) exceeds this get one FP64-residual
  *             refinement sweep (e.g. 1e3); above 1e5 they take the pivoted
  *             path below.
- * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and flux
- *             in FP32; moments, residual accumulation and RK update in FP64).
+ * precision:  WLSENO_FP64 or WLSENO_FP32_BULK (QR, facet evaluation and the
+ *             flux of the deviations in FP32; moments and the refinement
+ *             residual in FP64; the reference flux, facet sums, residual and
+ *             RK update in FP64 for Euler and in double-float arithmetic --
+ *             pairs of FP32 numbers, about 48 bits -- for the scalar
+ *             equations, whose FP64 results are hi + lo exactly).
  * gamma:      WLSENO_EULER only: ratio of specific heats (e.g. 1.4).
  * characteristic: WLSENO_EULER only, 0 or 1: reconstruct characteristic-wise
  *             (the characteristic decomposition of Sec. 5.1.4 and Sec. 5.2.4,

@@ -288,11 +288,12 @@ cudaError_t reconstruct_one(wlseno_ctx* ctx, const double* ubar, double* coeffs,
 
 cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, const double* u0,
                      double a, double b, bool residual_only, double* out, cudaStream_t s,
-                     const float* fdev = nullptr, const float2* pin = nullptr, float2* pout = nullptr) {
+                     const float* fdev = nullptr, const float2* pin = nullptr, float2* pout = nullptr,
+                     const float2* p0 = nullptr) {
   KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
   cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, fdev, u, u0,
                                          a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s,
-                                         pin, pout);
+                                         pin, pout, p0);
   scope.done(e == cudaSuccess ? 1 : 0);
   return e;
 }
@@ -302,10 +303,11 @@ cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, cons
 // positivity fix-up and runs the coupled flux; scalar equations go component
 // by component.
 // FP32-bulk scalar path: pin holds the FP32 pairs of u (else they are made
-// here), pout (may be null) receives those of out.
+// here), pout (may be null) receives those of out, p0 (may be null) holds
+// those of u0.
 cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double a, double b,
                       bool residual_only, double* out, cudaStream_t s, const float2* pin = nullptr,
-                      float2* pout = nullptr) {
+                      float2* pout = nullptr, const float2* p0 = nullptr) {
   const int64_t N = ctx->dm.N;
   const int C = ctx->scheme.n_comp;
   const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
@@ -342,7 +344,8 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
     if (e == cudaSuccess) e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals, s, fdev, pc);
     if (e == cudaSuccess)
       e = flux_one(ctx, ctx->d_fvals, u + c * N, u0 ? u0 + c * N : nullptr, a, b, residual_only,
-                   out + c * N, s, fdev, pc, fdev && pout ? pout + c * N : nullptr);
+                   out + c * N, s, fdev, pc, fdev && pout ? pout + c * N : nullptr,
+                   fdev && p0 ? p0 + c * N : nullptr);
   }
   return e;
 }
@@ -541,6 +544,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.fpts = fpts;
   dm.fpts32 = fp32;
   dm.ff32 = nullptr;
+  dm.inv_vol2 = nullptr;
   if (ctx->scheme.precision == WLSENO_FP32_BULK && ctx->scheme.pde != WLSENO_EULER) {
     const int nf = H.dim + 1;
     std::vector<FacetF32> ff(static_cast<size_t>(N) * nf);
@@ -552,13 +556,24 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
         vn += ctx->sp.vel[a] * G[a];
       }
       const bool adv = ctx->scheme.pde == WLSENO_ADVECTION;
-      ff[k].pref = adv ? G[3] * vn : 0.5 * G[3] * nsum;
+      const double pref = adv ? G[3] * vn : 0.5 * G[3] * nsum;
+      ff[k].pref_hi = static_cast<float>(pref);
+      ff[k].pref_lo = static_cast<float>(pref - static_cast<double>(ff[k].pref_hi));
       ff[k].coef = static_cast<float>(adv ? vn : nsum);
       ff[k].area = static_cast<float>(G[3]);
     }
     FacetF32* d_ff = nullptr;
     if ((st = upload(ctx, &d_ff, ff))) return st;
     dm.ff32 = d_ff;
+    std::vector<float2> iv(static_cast<size_t>(N));
+    for (int64_t i = 0; i < N; ++i) {
+      const double v = 1.0 / H.volume[i];
+      const float hi = static_cast<float>(v);
+      iv[i] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+    }
+    float2* d_iv = nullptr;
+    if ((st = upload(ctx, &d_iv, iv))) return st;
+    dm.inv_vol2 = d_iv;
   }
   const int C = ctx->scheme.n_comp;
   const int NP = (H.dim + 1) * H.nq;
@@ -760,9 +775,11 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     const int64_t CN = static_cast<int64_t>(ctx->scheme.n_comp) * ctx->dm.N;
     float2* p1 = ctx->d_pair ? ctx->d_pair + CN : nullptr;
     float2* p2 = ctx->d_pair ? ctx->d_pair + 2 * CN : nullptr;
+    // the pairs of u stay in the scratch slot from stage 1 on (one component)
+    float2* p0 = ctx->d_pair && ctx->scheme.n_comp == 1 ? ctx->d_pair : nullptr;
     if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st, nullptr, p1)) != cudaSuccess ||
-        (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st, p1, p2)) != cudaSuccess ||
-        (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st, p2, nullptr)) != cudaSuccess)
+        (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st, p1, p2, p0)) != cudaSuccess ||
+        (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st, p2, nullptr, p0)) != cudaSuccess)
       return err;
     return cudaSuccess;
   };

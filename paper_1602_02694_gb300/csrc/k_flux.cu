@@ -12,6 +12,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "wlseno_internal.h"
 
 namespace wlseno {
@@ -150,15 +151,21 @@ flux_stage_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ fva
 // from u_ref, where the other cell's deviations are shifted by the FP32
 // rounding of ubar_R - ubar_L.  FP64 work per facet: that subtraction, the
 // reference flux and the accumulation.
+__device__ __forceinline__ double pref64(const FacetF32& g) {
+  return static_cast<double>(g.pref_hi) + static_cast<double>(g.pref_lo);
+}
+
+// The FP32 flux of the deviations dL, dR from u_ref (ur = its FP32 value):
+// the facet's flux minus F(u_ref).n |f|, before the factor |f|.
 template <int NQ>
-__device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, float speed, double uref,
-                                                 float ur, const float (&dL)[NQ], const float (&dR)[NQ]) {
+__device__ __forceinline__ float facet_flux_dev_part(int pde, const FacetF32& g, float speed, float ur,
+                                                     const float (&dL)[NQ], const float (&dR)[NQ]) {
   const float wq = 1.0f / NQ;
   float fsum = 0.0f;
   if (pde == WLSENO_ADVECTION) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) fsum += wq * (0.5f * (g.coef * (dL[q] + dR[q]) - speed * (dR[q] - dL[q])));
-    return fma(g.pref, uref, static_cast<double>(g.area * fsum));
+    return fsum;
   }
   float mx = 0.0f;
 #pragma unroll
@@ -170,7 +177,15 @@ __device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, flo
     const float fr = g.coef * dR[q] * (ur + 0.5f * dR[q]);
     fsum += wq * (0.5f * ((fl + fr) - alpha * (dR[q] - dL[q])));
   }
-  return fma(g.pref * uref, uref, static_cast<double>(g.area * fsum));
+  return fsum;
+}
+
+template <int NQ>
+__device__ __forceinline__ double facet_flux_dev(int pde, const FacetF32& g, float speed, double uref,
+                                                 float ur, const float (&dL)[NQ], const float (&dR)[NQ]) {
+  const float fsum = facet_flux_dev_part<NQ>(pde, g, speed, ur, dL, dR);
+  if (pde == WLSENO_ADVECTION) return fma(pref64(g), uref, static_cast<double>(g.area * fsum));
+  return fma(pref64(g) * uref, uref, static_cast<double>(g.area * fsum));
 }
 
 template <int DIM>
@@ -243,6 +258,84 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
   if (!isfinite(res)) atomicAdd(&counters[2], 1ull);
 }
 
+// The same flux, residual and stage with every FP64 operation replaced by
+// double-float arithmetic (dfloat.cuh) on the FP32 pairs of the states: per
+// facet F(u_ref).n |f| = pref u_ref (u_ref) from the pair of the reference
+// coefficient and the pair of u_ref = ubar_L, plus the exact product |f| fsum
+// of the FP32 deviation flux; the facet sum, the factor 1/|tau_i| (a pair)
+// and a u0 + b (u + dt L) likewise.  Both cells of a facet form its flux from
+// the same operands in the same order, so it is bitwise the same in both and
+// discrete conservation stays exact up to the final rounding.  FP64 is left
+// with forming the pair of dt and the FP64 output (hi + lo, exact).
+template <int DIM>
+__global__ void __launch_bounds__(256)
+flux_stage_df_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ fdev,
+                     const float2* __restrict__ pin, const float2* __restrict__ p0, dfloat a, dfloat b,
+                     const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
+                     unsigned long long* __restrict__ counters, float2* __restrict__ pout) {
+  constexpr int NF = DIM + 1;
+  constexpr int NQ = nq_of(DIM);
+  constexpr int NP = NF * NQ;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= dm.N) return;
+  float speed2 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) speed2 += static_cast<float>(sp.vel[q] * sp.vel[q]);
+  const float speed = sqrtf(speed2);
+  const float2 pi = pin[i];
+  dfloat acc = {0.0f, 0.0f};
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int nb = dm.nbr[i * NF + f];
+    float di[NQ], dj[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) di[q] = fdev[i * NP + f * NQ + q];
+    float2 pj = pi;
+    bool owner = true;
+    if (nb >= 0) {
+      const int64_t j = nb >> 2;
+      const int f2 = nb & 3;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dj[q] = fdev[j * NP + f2 * NQ + q];
+      pj = pin[j];
+      owner = i < j;
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dj[q] = di[q];
+    }
+    const float2 pL = owner ? pi : pj, pR = owner ? pj : pi;
+    const float jump = (pR.x - pL.x) + (pR.y - pL.y);  // ubar_R - ubar_L
+    float dL[NQ], dR[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      dL[q] = owner ? di[q] : dj[q];
+      dR[q] = (owner ? dj[q] : di[q]) + jump;
+    }
+    const FacetF32 g = dm.ff32[i * NF + f];
+    const float fsum = facet_flux_dev_part<NQ>(sp.pde, g, speed, pL.x, dL, dR);
+    const dfloat uref = {pL.x, pL.y};
+    const dfloat pref = {g.pref_hi, g.pref_lo};
+    dfloat ref = df_mul(pref, uref);
+    if (sp.pde != WLSENO_ADVECTION) ref = df_mul(ref, uref);
+    const dfloat flux = df_add(ref, df_two_prod(g.area, fsum));
+    acc = df_add(acc, owner ? flux : df_neg(flux));
+  }
+  const float2 iv = dm.inv_vol2[i];
+  dfloat res = df_neg(df_mul(acc, dfloat{iv.x, iv.y}));  // L
+  if (!residual_only) {
+    const dfloat dt = df_from_double(dt_mesh[dm.mesh_of[i]]);
+    res = df_mul(b, df_add(dfloat{pi.x, pi.y}, df_mul(dt, res)));
+    if (a.hi != 0.0f) {
+      const float2 q0 = p0[i];
+      res = df_add(df_mul(a, dfloat{q0.x, q0.y}), res);
+    }
+  }
+  const double v = static_cast<double>(res.hi) + static_cast<double>(res.lo);
+  out[i] = v;
+  if (pout) pout[i] = make_float2(res.hi, res.lo);
+  if (!isfinite(v)) atomicAdd(&counters[2], 1ull);
+}
+
 __global__ void split_pairs_kernel(const double* __restrict__ u, float2* __restrict__ pair, int64_t n) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= n) return;
@@ -297,13 +390,18 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
                                    const double* fvals, const float* fdev, const double* u,
                                    const double* u0, double a, double b, const double* dt_mesh,
                                    bool residual_only, double* out, unsigned long long* counters,
-                                   cudaStream_t s, const float2* pin, float2* pout) {
+                                   cudaStream_t s, const float2* pin, float2* pout, const float2* p0) {
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   const int ro = residual_only ? 1 : 0;
+  const bool df = fdev && pin && dm.ff32 && dm.inv_vol2 && (residual_only || a == 0.0 || p0);
   auto launch = [&](auto D) {
     constexpr int DD = decltype(D)::value;
-    if (fdev)
+    if (df)
+      flux_stage_df_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp, fdev, pin, p0, df_from_double(a),
+                                                          df_from_double(b), dt_mesh, ro, out, counters,
+                                                          residual_only ? nullptr : pout);
+    else if (fdev)
       flux_stage_dev_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
                                                            pin, residual_only ? nullptr : pout);
     else if (precision == WLSENO_FP32_BULK)

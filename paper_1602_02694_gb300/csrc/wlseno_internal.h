@@ -59,12 +59,12 @@ wlseno_status build_host_setup(const wlseno_mesh* meshes, int n_meshes,
 // device-side views handed to the kernel launchers
 // ---------------------------------------------------------------------------
 // Per-facet coefficients of the FP32-bulk scalar flux, in the orientation of
-// the facet's lower-indexed cell (identical in both cells' records): the FP64
-// reference coefficient (Burgers: |f| (n_1+..+n_d)/2, advection: |f| v.n),
-// the FP32 normal factor (Burgers: n_1+..+n_d, advection: v.n) and the FP32
-// facet measure |f|.
+// the facet's lower-indexed cell (identical in both cells' records): the
+// reference coefficient (Burgers: |f| (n_1+..+n_d)/2, advection: |f| v.n) as
+// a double-float pair (hi + lo), the FP32 normal factor (Burgers:
+// n_1+..+n_d, advection: v.n) and the FP32 facet measure |f|.
 struct FacetF32 {
-  double pref;
+  float pref_hi, pref_lo;
   float coef;
   float area;
 };
@@ -97,6 +97,7 @@ struct DeviceMesh {
   // the stencil index (int32 bits), then zero padding to a 16-byte multiple
   float* rec32;             // [nmax][N][rec_width]
   const FacetF32* ff32;     // [N][dim+1] FP32-bulk scalar flux coefficients (else null)
+  const float2* inv_vol2;   // [N] FP32-bulk scalar: 1/|tau| as a double-float pair (else null)
   int rec_width;            // round_up(m + 1, 4)
 };
 
@@ -240,12 +241,15 @@ WLSENO_DECLARE_RECON(float, 3, 10)
 // fdev (FP32-bulk, scalar equations) replaces fvals when set.
 // With fdev, pin (the FP32 pairs of u, may be null) gives the jumps between
 // cell averages without FP64 arithmetic, and pout (may be null) receives the
-// pairs of the written state.
+// pairs of the written state.  With fdev and pin, and p0 (the pairs of u0)
+// unless a = 0 or residual_only, the flux, residual and stage run in
+// double-float arithmetic (dfloat.cuh); otherwise in FP64.
 cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp, int precision,
                                    const double* fvals, const float* fdev, const double* u,
                                    const double* u0, double a, double b, const double* dt_mesh,
                                    bool residual_only, double* out, unsigned long long* counters,
-                                   cudaStream_t s, const float2* pin = nullptr, float2* pout = nullptr);
+                                   cudaStream_t s, const float2* pin = nullptr, float2* pout = nullptr,
+                                   const float2* p0 = nullptr);
 // dt_mesh[k] = cfl * rmin[k] / lambda_max(mesh k), or dt_fixed when > 0.
 cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
                                const double* u, const double* rmin, double cfl, double dt_fixed,
