@@ -30,6 +30,7 @@ struct wlseno_ctx {
   int32_t* d_st_idx = nullptr;
   double* d_rmin = nullptr;
   double* d_dt = nullptr;
+  float2* d_dt2 = nullptr;       // [n_meshes] double-float pairs of d_dt
   unsigned long long* d_lmax = nullptr;
   unsigned long long* d_counters = nullptr;
   double* d_fvals = nullptr;     // [N][NP]
@@ -293,7 +294,7 @@ cudaError_t flux_one(wlseno_ctx* ctx, const double* fvals, const double* u, cons
   KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
   cudaError_t e = launch_flux_stage_impl(ctx->dm, ctx->sp, ctx->scheme.precision, fvals, fdev, u, u0,
                                          a, b, ctx->d_dt, residual_only, out, ctx->d_counters, s,
-                                         pin, pout, p0);
+                                         pin, pout, p0, ctx->d_dt2);
   scope.done(e == cudaSuccess ? 1 : 0);
   return e;
 }
@@ -578,7 +579,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   const int C = ctx->scheme.n_comp;
   const int NP = (H.dim + 1) * H.nq;
   if ((st = dalloc(ctx, &dm.A64, H.nnz * H.m)) || (st = dalloc(ctx, &dm.A32, H.nnz * H.m)) ||
-      (st = dalloc(ctx, &ctx->d_dt, H.n_meshes)) || (st = dalloc(ctx, &ctx->d_lmax, H.n_meshes)) ||
+      (st = dalloc(ctx, &ctx->d_dt, H.n_meshes)) || (st = dalloc(ctx, &ctx->d_dt2, H.n_meshes)) ||
+      (st = dalloc(ctx, &ctx->d_lmax, H.n_meshes)) ||
       (st = dalloc(ctx, &ctx->d_counters, kCounters)) || (st = dalloc(ctx, &ctx->d_fvals, C * N * NP)) ||
       (st = dalloc(ctx, &ctx->d_k1, C * N)) || (st = dalloc(ctx, &ctx->d_k2, C * N)))
     return st;
@@ -764,7 +766,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       int nl = 0;
       KernelScope scope(ctx, WLSENO_KERNEL_DT, st);
       err = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
-                               dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl);
+                               dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl, ctx->d_dt2);
       scope.done(nl);
       if (err != cudaSuccess) return err;
     }
@@ -922,8 +924,15 @@ wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host) {
   for (int k = 0; k < ctx->host.n_meshes; ++k)
     if (!(dt_host[k] > 0.0)) return fail(ctx, WLSENO_ERR_INVALID_ARG, "per-mesh dt must be > 0");
   DeviceGuard guard(ctx->device);
+  std::vector<float2> pairs(ctx->host.n_meshes);
+  for (int k = 0; k < ctx->host.n_meshes; ++k) {
+    const float hi = static_cast<float>(dt_host[k]);
+    pairs[k] = make_float2(hi, static_cast<float>(dt_host[k] - static_cast<double>(hi)));
+  }
   cudaError_t e = cudaMemcpy(ctx->d_dt, dt_host, sizeof(double) * ctx->host.n_meshes,
                              cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->d_dt2, pairs.data(), sizeof(float2) * pairs.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set mesh dt");
   ctx->mesh_dt_set = true;
   return WLSENO_OK;
@@ -990,7 +999,7 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
     int nl = 0;
     KernelScope scope(ctx, WLSENO_KERNEL_DT, s);
     e = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, 0.0, dt,
-                           ctx->d_lmax, ctx->d_dt, s, &nl);
+                           ctx->d_lmax, ctx->d_dt, s, &nl, ctx->d_dt2);
     scope.done(nl);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dt");
     ctx->mesh_dt_set = false;

@@ -269,71 +269,73 @@ flux_stage_dev_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ 
 // with forming the pair of dt and the FP64 output (hi + lo, exact).
 template <int DIM>
 __global__ void __launch_bounds__(256)
-flux_stage_df_kernel(DeviceMesh dm, SchemeParams sp, const float* __restrict__ fdev,
+flux_stage_df_kernel(DeviceMesh dm, int pde, float speed, const float* __restrict__ fdev,
                      const float2* __restrict__ pin, const float2* __restrict__ p0, dfloat a, dfloat b,
-                     const double* __restrict__ dt_mesh, int residual_only, double* __restrict__ out,
+                     const float2* __restrict__ dt2, int residual_only, double* __restrict__ out,
                      unsigned long long* __restrict__ counters, float2* __restrict__ pout) {
   constexpr int NF = DIM + 1;
   constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= dm.N) return;
-  float speed2 = 0.0f;
+  // every load up front: the neighbours first (the other loads depend on
+  // them), then this cell's data, then the neighbours' (a boundary facet reads
+  // this cell's own values and discards them)
+  int nb[NF];
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) speed2 += static_cast<float>(sp.vel[q] * sp.vel[q]);
-  const float speed = sqrtf(speed2);
+  for (int f = 0; f < NF; ++f) nb[f] = dm.nbr[i * NF + f];
   const float2 pi = pin[i];
+  float di[NF][NQ];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) di[f][q] = fdev[i * NP + f * NQ + q];
+  FacetF32 g[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) g[f] = dm.ff32[i * NF + f];
+  const float2 iv = dm.inv_vol2[i];
+  float2 dtp = make_float2(0.0f, 0.0f), q0 = make_float2(0.0f, 0.0f);
+  if (!residual_only) {
+    dtp = dt2[dm.mesh_of[i]];
+    if (a.hi != 0.0f) q0 = p0[i];
+  }
+  float dj[NF][NQ];
+  float2 pj[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int64_t j = nb[f] >= 0 ? (nb[f] >> 2) : i;
+    const int f2 = nb[f] >= 0 ? (nb[f] & 3) : f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dj[f][q] = fdev[j * NP + f2 * NQ + q];
+    pj[f] = pin[j];
+  }
   dfloat acc = {0.0f, 0.0f};
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int nb = dm.nbr[i * NF + f];
-    float di[NQ], dj[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) di[q] = fdev[i * NP + f * NQ + q];
-    float2 pj = pi;
-    bool owner = true;
-    if (nb >= 0) {
-      const int64_t j = nb >> 2;
-      const int f2 = nb & 3;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) dj[q] = fdev[j * NP + f2 * NQ + q];
-      pj = pin[j];
-      owner = i < j;
-    } else {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) dj[q] = di[q];
-    }
-    const float2 pL = owner ? pi : pj, pR = owner ? pj : pi;
+    const bool owner = nb[f] < 0 || i < (nb[f] >> 2);
+    const float2 pL = owner ? pi : pj[f], pR = owner ? pj[f] : pi;
     const float jump = (pR.x - pL.x) + (pR.y - pL.y);  // ubar_R - ubar_L
     float dL[NQ], dR[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      dL[q] = owner ? di[q] : dj[q];
-      dR[q] = (owner ? dj[q] : di[q]) + jump;
+      dL[q] = owner ? di[f][q] : dj[f][q];
+      dR[q] = (owner ? dj[f][q] : di[f][q]) + jump;
     }
-    const FacetF32 g = dm.ff32[i * NF + f];
-    const float fsum = facet_flux_dev_part<NQ>(sp.pde, g, speed, pL.x, dL, dR);
+    const float fsum = facet_flux_dev_part<NQ>(pde, g[f], speed, pL.x, dL, dR);
     const dfloat uref = {pL.x, pL.y};
-    const dfloat pref = {g.pref_hi, g.pref_lo};
-    dfloat ref = df_mul(pref, uref);
-    if (sp.pde != WLSENO_ADVECTION) ref = df_mul(ref, uref);
-    const dfloat flux = df_add(ref, df_two_prod(g.area, fsum));
+    dfloat ref = df_mul(dfloat{g[f].pref_hi, g[f].pref_lo}, uref);
+    if (pde != WLSENO_ADVECTION) ref = df_mul(ref, uref);
+    const dfloat flux = df_add(ref, df_two_prod(g[f].area, fsum));
     acc = df_add(acc, owner ? flux : df_neg(flux));
   }
-  const float2 iv = dm.inv_vol2[i];
   dfloat res = df_neg(df_mul(acc, dfloat{iv.x, iv.y}));  // L
   if (!residual_only) {
-    const dfloat dt = df_from_double(dt_mesh[dm.mesh_of[i]]);
-    res = df_mul(b, df_add(dfloat{pi.x, pi.y}, df_mul(dt, res)));
-    if (a.hi != 0.0f) {
-      const float2 q0 = p0[i];
-      res = df_add(df_mul(a, dfloat{q0.x, q0.y}), res);
-    }
+    res = df_mul(b, df_add(dfloat{pi.x, pi.y}, df_mul(dfloat{dtp.x, dtp.y}, res)));
+    if (a.hi != 0.0f) res = df_add(df_mul(a, dfloat{q0.x, q0.y}), res);
   }
-  const double v = static_cast<double>(res.hi) + static_cast<double>(res.lo);
-  out[i] = v;
+  out[i] = static_cast<double>(res.hi) + static_cast<double>(res.lo);
   if (pout) pout[i] = make_float2(res.hi, res.lo);
-  if (!isfinite(v)) atomicAdd(&counters[2], 1ull);
+  if (!isfinite(res.hi) || !isfinite(res.lo)) atomicAdd(&counters[2], 1ull);
 }
 
 __global__ void split_pairs_kernel(const double* __restrict__ u, float2* __restrict__ pair, int64_t n) {
@@ -371,17 +373,22 @@ __global__ void max_abs_kernel(int64_t N, const double* __restrict__ u,
 __global__ void cfl_dt_kernel(int n_meshes, int pde, int dim, double adv_speed,
                               const unsigned long long* __restrict__ lmax_bits,
                               const double* __restrict__ rmin, double cfl, double dt_fixed,
-                              double* __restrict__ dt_mesh) {
+                              double* __restrict__ dt_mesh, float2* __restrict__ dt2) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_meshes) return;
-  if (dt_fixed > 0.0) {
-    dt_mesh[k] = dt_fixed;
-    return;
+  double dt = dt_fixed;
+  if (dt_fixed <= 0.0) {
+    double lam = adv_speed;
+    if (pde == WLSENO_BURGERS)
+      lam = sqrt(static_cast<double>(dim)) * __longlong_as_double(static_cast<long long>(lmax_bits[k]));
+    if (pde == WLSENO_EULER) lam = __longlong_as_double(static_cast<long long>(lmax_bits[k]));  // max |u| + c
+    dt = lam > 0.0 ? cfl * rmin[k] / lam : 0.0;
   }
-  double lam = adv_speed;
-  if (pde == WLSENO_BURGERS) lam = sqrt(static_cast<double>(dim)) * __longlong_as_double(static_cast<long long>(lmax_bits[k]));
-  if (pde == WLSENO_EULER) lam = __longlong_as_double(static_cast<long long>(lmax_bits[k]));  // max |u| + c
-  dt_mesh[k] = lam > 0.0 ? cfl * rmin[k] / lam : 0.0;
+  dt_mesh[k] = dt;
+  if (dt2) {
+    const dfloat v = df_from_double(dt);
+    dt2[k] = make_float2(v.hi, v.lo);
+  }
 }
 
 }  // namespace
@@ -390,17 +397,22 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
                                    const double* fvals, const float* fdev, const double* u,
                                    const double* u0, double a, double b, const double* dt_mesh,
                                    bool residual_only, double* out, unsigned long long* counters,
-                                   cudaStream_t s, const float2* pin, float2* pout, const float2* p0) {
+                                   cudaStream_t s, const float2* pin, float2* pout, const float2* p0,
+                                   const float2* dt2) {
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
   const int ro = residual_only ? 1 : 0;
-  const bool df = fdev && pin && dm.ff32 && dm.inv_vol2 && (residual_only || a == 0.0 || p0);
+  const bool df = fdev && pin && dm.ff32 && dm.inv_vol2 && (residual_only || dt2) &&
+                  (residual_only || a == 0.0 || p0);
+  double speed = 0.0;
+  for (int k = 0; k < dm.dim; ++k) speed += sp.vel[k] * sp.vel[k];
+  const float speedf = static_cast<float>(std::sqrt(speed));
   auto launch = [&](auto D) {
     constexpr int DD = decltype(D)::value;
     if (df)
-      flux_stage_df_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp, fdev, pin, p0, df_from_double(a),
-                                                          df_from_double(b), dt_mesh, ro, out, counters,
-                                                          residual_only ? nullptr : pout);
+      flux_stage_df_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp.pde, speedf, fdev, pin, p0,
+                                                          df_from_double(a), df_from_double(b), dt2, ro,
+                                                          out, counters, residual_only ? nullptr : pout);
     else if (fdev)
       flux_stage_dev_kernel<DD><<<blocks, threads, 0, s>>>(dm, sp, fdev, u, u0, a, b, dt_mesh, ro, out, counters,
                                                            pin, residual_only ? nullptr : pout);
@@ -427,7 +439,7 @@ cudaError_t launch_split_pairs(const double* u, float2* pair, int64_t n, cudaStr
 cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
                                const double* u, const double* rmin, double cfl, double dt_fixed,
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
-                               int* launches) {
+                               int* launches, float2* dt2) {
   double speed = 0.0;
   for (int a = 0; a < dm.dim; ++a) speed += sp.vel[a] * sp.vel[a];
   speed = std::sqrt(speed);
@@ -445,7 +457,7 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
     ++*launches;
   }
   cfl_dt_kernel<<<(n_meshes + 127) / 128, 128, 0, s>>>(n_meshes, sp.pde, dm.dim, speed, lmax_bits,
-                                                        rmin, cfl, dt_fixed, dt_mesh);
+                                                        rmin, cfl, dt_fixed, dt_mesh, dt2);
   ++*launches;
   return cudaGetLastError();
 }

@@ -341,6 +341,8 @@ refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int t = lane + q * L;
+      // rows past both cells' stencils: skip their FP64 work (warp-uniform)
+      if (!__any_sync(0xffffffffu, t < n)) continue;
       const double dev = uj[q] - ui;
       const float devf = static_cast<float>(dev);
       const float w = t == 0 ? wc : e / fmaf(devf, devf, e);
