@@ -275,6 +275,10 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
  *         Burgers sqrt(dim) max |ubar|), computed on the device per mesh.
  * dt_out: optional host pointer receiving the last step's dt (of mesh 0); it
  *         synchronises the stream when non-NULL.
+ * One step is captured as a CUDA graph (on the context's own stream) and
+ * replayed for n_steps >= 2, for a host ubar (staged through the context's
+ * buffer), and for one step whose arguments match the captured one; not in
+ * timing mode or while `stream` is being captured.
  * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
 wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
                              double* dt_out, void* stream);

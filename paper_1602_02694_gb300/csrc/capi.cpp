@@ -785,18 +785,22 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       return err;
     return cudaSuccess;
   };
-  // Several steps: capture one step as a CUDA graph (on the context's own
-  // stream) and launch it n_steps times on `s`.  Not when timing, and not when
-  // `s` is itself being captured (then the launches join the caller's graph).
+  // Capture one step as a CUDA graph (on the context's own stream) and launch
+  // it n_steps times on `s`.  Not when timing, and not when `s` is itself
+  // being captured (then the launches join the caller's graph).
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
     cudaGetLastError();
     cap = cudaStreamCaptureStatusActive;
   }
-  const bool use_graph = n_steps >= 2 && !ctx->timing && cap == cudaStreamCaptureStatusNone;
+  // One step replays the captured step too when that graph is already there
+  // for these arguments, or when the state is staged through the context's
+  // own buffer (a host array: the same device address every call).
+  const bool same = ctx->graph_exec && ctx->graph_u == u && ctx->graph_dt == dt &&
+                    ctx->graph_cfl == cfl && ctx->graph_G == ctx->G;
+  const bool use_graph = (n_steps >= 2 || (n_steps == 1 && (host || same))) && !ctx->timing &&
+                         cap == cudaStreamCaptureStatusNone;
   if (use_graph) {
-    const bool same = ctx->graph_exec && ctx->graph_u == u && ctx->graph_dt == dt &&
-                      ctx->graph_cfl == cfl && ctx->graph_G == ctx->G;
     if (!same) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
       ctx->graph_exec = nullptr;
