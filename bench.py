@@ -46,7 +46,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal)
 # kernel on this workload, from an ncu capture of the same kernel
 # (profiles/recon_tpc_fp32_burgers256_p4.md); None where no capture of the
 # current kernel exists.
-TRAFFIC_PER_LAUNCH = {"fp32_bulk": 244.92e6 + 4.62e6, "fp64": None}
+TRAFFIC_PER_LAUNCH = {"fp32_bulk": 244.78e6 + 4.41e6, "fp64": None}
 
 
 def parse_args():
