@@ -84,7 +84,15 @@ typedef struct {
  *             one thread per cell (stencils of at most 64 cells; the default
  *             for 0, 0), or a group of lanes_per_cell lanes of a warp per cell,
  *             each lane holding rows_per_lane stencil rows: (8,2) (8,3) (8,5)
- *             (16,3) (16,4).  wlseno_autotune picks the fastest that fits. */
+ *             (16,3) (16,4).  wlseno_autotune picks the fastest that fits.
+ * moments_mode: FP32-bulk thread-per-cell kernel only (else 0): 0 streams
+ *             each stencil row's stored FP32 moments (48 bytes per row for
+ *             m = 10); 1 forms them on the fly from the offset
+ *             (x_j - x_i)/h_i of the row's cell (16 bytes per row) and that
+ *             cell's own central moments (gathered, 16 or 32 bytes per cell)
+ *             by the binomial expansion of the Taylor monomials about x_j:
+ *             a third of the row bytes for about 40 more FP32 operations per
+ *             row.  wlseno_autotune also tries both. */
 typedef struct {
   int order_p;
   double ring;
@@ -92,6 +100,7 @@ typedef struct {
   int min_rows;
   int lanes_per_cell;
   int rows_per_lane;
+  int moments_mode;
 } wlseno_stencil_opts;
 
 /* Scheme parameters.
@@ -178,6 +187,7 @@ typedef struct {
   int quad_per_facet;      /* 2 in 2-D, 3 in 3-D                                */
   int lanes_per_cell;      /* kernel shape chosen for the reconstruction        */
   int rows_per_lane;
+  int moments_mode;        /* 0 stored rows, 1 formed on the fly (see opts)     */
 } wlseno_info;
 
 /* Kernel kinds of the per-kind launch counts and timings.  RECONSTRUCT is
@@ -328,7 +338,8 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
                                   const double* gbar_next, double* gbar_n, void* stream);
 
 /* Autotuner: times the reconstruction kernel with every compiled shape
- * (lanes_per_cell, rows_per_lane) whose rows hold the largest stencil, on
+ * (lanes_per_cell, rows_per_lane) whose rows hold the largest stencil (and,
+ * for the FP32-bulk thread-per-cell shape, both moments modes), on
  * `ubar` ([n_comp][n_cells], host or device), `reps` launches each after one
  * warm-up launch, and keeps the fastest for the context.  best_us (host,
  * nullable) receives its mean launch time in microseconds.  Synchronises

@@ -1,6 +1,7 @@
 // C ABI of libwlseno: context, device buffers, host/device pointer staging
 // and the entry points of include/wlseno.h.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,6 +25,7 @@ struct wlseno_ctx {
   bool moments_ready = false;
   HostSetup host;
   int G = 0, R = 0;
+  bool otf = false;              // FP32-bulk main kernel forms its moment rows on the fly
   DeviceMesh dm{};
   std::vector<void*> allocs;     // every device allocation of the context
   int32_t* d_st_ptr = nullptr;
@@ -56,7 +58,7 @@ struct wlseno_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   const double* graph_u = nullptr;
   double graph_dt = 0.0, graph_cfl = 0.0;
-  int graph_G = 0;
+  int graph_shape = 0;           // shape_key of the captured step
   int64_t graph_launches = 0;
   int64_t graph_kind[WLSENO_N_KERNEL_KINDS] = {};
   // adjoint work (allocated on the first wlseno_step_adjoint)
@@ -245,7 +247,8 @@ cudaError_t reconstruct_plain(wlseno_ctx* ctx, const double* ubar, double* coeff
     return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    const TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pair, ctx->side, ctx->ev_fork, ctx->ev_join};
+    const TpcWork wl{ctx->d_wl,   ctx->d_wl_count, ctx->d_rbuf, pair,
+                     ctx->side,   ctx->ev_fork,    ctx->ev_join, ctx->otf && f32};
     e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
       constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
       return f32 ? launch_recon_tpc_inst<float, DD, MM>(dm, ctx->sp, ubar, out, wl, s)
@@ -350,6 +353,9 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
   }
   return e;
 }
+
+// The kernel variant a captured step used: shape and moments mode.
+int shape_key(const wlseno_ctx* ctx) { return (ctx->G * 64 + ctx->R) * 2 + (ctx->otf ? 1 : 0); }
 
 wlseno_status check_ready(wlseno_ctx* ctx) {
   if (!ctx) return WLSENO_ERR_INVALID_ARG;
@@ -501,8 +507,13 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   if (G == 0 || !shape_fits(G, R, H.max_n))
     return fail(ctx, WLSENO_ERR_STENCIL, "largest stencil (" + std::to_string(H.max_n) +
                                              " cells) exceeds the kernel's rows");
+  if (opts->moments_mode != 0 &&
+      (opts->moments_mode != 1 || G != 1 || ctx->scheme.precision != WLSENO_FP32_BULK))
+    return fail(ctx, WLSENO_ERR_INVALID_ARG,
+                "moments_mode 1 needs FP32-bulk precision and the thread-per-cell shape");
   ctx->G = G;
   ctx->R = R;
+  ctx->otf = opts->moments_mode == 1;
   const int64_t N = H.N;
   std::vector<int32_t> ptr32(N + 1), idx32(H.nnz);
   for (int64_t i = 0; i <= N; ++i) ptr32[i] = static_cast<int32_t>(H.row_ptr[i]);
@@ -591,9 +602,13 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (st = dalloc(ctx, &dm.rec32, ell * dm.rec_width)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
       (st = dalloc(ctx, &ctx->d_wl_count, 2)))
     return st;
+  dm.geo32 = dm.own32 = nullptr;
+  dm.own_width = own32_width(H.dim, H.m);
   if (ctx->scheme.precision == WLSENO_FP32_BULK &&
       ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) || (st = dalloc(ctx, &ctx->d_pair, 3 * C * N)) ||
-       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N))))
+       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N)) ||
+       (st = dalloc(ctx, &dm.geo32, ell * 4)) ||
+       (st = dalloc(ctx, &dm.own32, static_cast<size_t>(N) * dm.own_width))))
     return st;
   if (ctx->scheme.balanced) {
     BalanceWork& b = ctx->bal;
@@ -797,7 +812,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   // for these arguments, or when the state is staged through the context's
   // own buffer (a host array: the same device address every call).
   const bool same = ctx->graph_exec && ctx->graph_u == u && ctx->graph_dt == dt &&
-                    ctx->graph_cfl == cfl && ctx->graph_G == ctx->G;
+                    ctx->graph_cfl == cfl && ctx->graph_shape == shape_key(ctx);
   const bool use_graph = (n_steps >= 2 || (n_steps == 1 && (host || same))) && !ctx->timing &&
                          cap == cudaStreamCaptureStatusNone;
   if (use_graph) {
@@ -834,7 +849,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       ctx->graph_u = u;
       ctx->graph_dt = dt;
       ctx->graph_cfl = cfl;
-      ctx->graph_G = ctx->G;
+      ctx->graph_shape = shape_key(ctx);
     }
     for (int step = 0; step < n_steps; ++step) {
       if ((e = cudaGraphLaunch(ctx->graph_exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -888,12 +903,21 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
     return cuda_fail(ctx, e, "event");
   }
   const int G0 = ctx->G, R0 = ctx->R;
+  const bool otf0 = ctx->otf;
   int bestG = G0, bestR = R0;
+  bool bestO = otf0;
   float best = -1.0f;
+  // (G, R, moments on the fly): the thread-per-cell shape twice in FP32-bulk
+  std::vector<std::array<int, 3>> cands;
   for (auto& sh : kShapes) {
+    cands.push_back({sh[0], sh[1], 0});
+    if (sh[0] == 1 && ctx->scheme.precision == WLSENO_FP32_BULK) cands.push_back({sh[0], sh[1], 1});
+  }
+  for (auto& sh : cands) {
     if (!shape_fits(sh[0], sh[1], ctx->host.max_n)) continue;
     ctx->G = sh[0];
     ctx->R = sh[1];
+    ctx->otf = sh[2] != 0;
     e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int k = 0; k < reps && e == cudaSuccess; ++k) e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
@@ -906,18 +930,21 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
       cudaEventDestroy(e1);
       ctx->G = G0;
       ctx->R = R0;
+      ctx->otf = otf0;
       return cuda_fail(ctx, e, "autotune");
     }
     if (best < 0.0f || ms < best) {
       best = ms;
       bestG = sh[0];
       bestR = sh[1];
+      bestO = sh[2] != 0;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->G = bestG;
   ctx->R = bestR;
+  ctx->otf = bestO;
   if (best_us) *best_us = best < 0.0f ? 0.0 : 1e3 * best / reps;
   return WLSENO_OK;
 }
@@ -1070,6 +1097,7 @@ wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out) {
   out->quad_per_facet = H.nq;
   out->lanes_per_cell = ctx->G;
   out->rows_per_lane = ctx->R;
+  out->moments_mode = ctx->otf ? 1 : 0;
   return WLSENO_OK;
 }
 

@@ -6,12 +6,24 @@
 //    floats, W = round_up(m + 1, 4): the m moments, the stencil index as int32
 //    bits, zeros.  A warp's records are one contiguous 16-byte-aligned span,
 //    moved into shared memory by 16-byte asynchronous copies.
+//  * FP32-bulk only, for the moments-on-the-fly kernel: per row the offset
+//    (x_j - x_i)/h_i of the stencil cell's centroid at its minimum image
+//    (the image the moments use) and the stencil index, 16 bytes; per cell its
+//    own central moments of degree >= 2 in absolute units (the centre row of
+//    its moments times h_i^|kappa|).
 // Rows past a cell's stencil (t >= n) point at the cell itself with zero
 // moments; the kernels never read them.
 #include "wlseno_internal.h"
 
 namespace wlseno {
 namespace {
+
+// Total degree of Taylor column c (the column order of monomials.cuh).
+__device__ int taylor_degree(int dim, int c) {
+  if (dim == 1) return c;
+  if (dim == 2) return c == 0 ? 0 : c < 3 ? 1 : c < 6 ? 2 : 3;
+  return c == 0 ? 0 : c < 4 ? 1 : 2;
+}
 
 __global__ void ell_copy_kernel(DeviceMesh dm) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -34,6 +46,32 @@ __global__ void ell_copy_kernel(DeviceMesh dm) {
     }
     rec[m] = __int_as_float(j);
     for (int c = m + 1; c < W; ++c) rec[c] = 0.0f;
+    if (dm.geo32) {
+      const int dim = dm.dim;
+      const double hinv = 1.0 / dm.h[i];
+      const double* per = dm.period + 3 * dm.mesh_of[i];
+      float* g = dm.geo32 + (static_cast<int64_t>(t) * N + i) * 4;
+      for (int a = 0; a < 4; ++a) g[a] = 0.0f;
+      if (in) {
+        for (int a = 0; a < dim; ++a) {
+          double d = dm.centroid[static_cast<int64_t>(j) * dim + a] - dm.centroid[i * dim + a];
+          if (per[a] > 0.0) d -= per[a] * nearbyint(d / per[a]);
+          g[a] = static_cast<float>(d * hinv);
+        }
+      }
+      g[dim] = __int_as_float(j);
+    }
+  }
+  if (dm.own32) {
+    // the centre row (t = 0) about x_i in h_i units, scaled back by h_i^|kappa|
+    const double hi = dm.h[i];
+    float* o = dm.own32 + i * dm.own_width;
+    int k = 0;
+    for (int c = 0; c < m; ++c) {
+      const int deg = taylor_degree(dm.dim, c);
+      if (deg >= 2) o[k++] = static_cast<float>(dm.A64[static_cast<int64_t>(beg) * m + c] * pow(hi, deg));
+    }
+    for (; k < dm.own_width; ++k) o[k] = 0.0f;
   }
 }
 

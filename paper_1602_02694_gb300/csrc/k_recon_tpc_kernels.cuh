@@ -140,6 +140,137 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
   cp_async_wait<0>();
 }
 
+// Moments on the fly.  The row of stencil cell j is the cell average over
+// tau_j of prod_a y_a^kappa_a / kappa_a! with y = (x - x_i)/h_i.  Writing
+// y = w + d, w = (x - x_j)/h_i and d = (x_j - x_i)/h_i, the binomial theorem
+// gives (w_a + d_a)^k / k! = sum_{b <= k} w_a^b / b! d_a^(k-b) / (k-b)!, so
+//   A[kappa] = sum_{alpha <= kappa} M_j[alpha] h_i^-|alpha| d^(kappa-alpha) / (kappa-alpha)!
+// with M_j[alpha] cell j's own central moments (absolute units; M_j[0] = 1,
+// M_j[alpha] = 0 for |alpha| = 1 about the centroid).  own holds M_j for the
+// columns of degree >= 2 in column order, hp[k] = h_i^-k.
+template <int DIM>
+__host__ __device__ constexpr int taylor_deg(int c) {
+  int s = 0;
+  for (int a = 0; a < DIM; ++a) s += exponent<DIM>(c, a);
+  return s;
+}
+
+template <int DIM, int M>
+__device__ __forceinline__ void shifted_row(const float (&d)[DIM], const float (&hp)[5], const float* own,
+                                            float (&row)[M]) {
+  float pw[DIM][5];  // d_a^k / k!
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    pw[a][0] = 1.0f;
+    pw[a][1] = d[a];
+    pw[a][2] = d[a] * d[a] * 0.5f;
+    pw[a][3] = pw[a][2] * d[a] * (1.0f / 3.0f);
+    pw[a][4] = pw[a][3] * d[a] * 0.25f;
+  }
+  float ms[M];  // own moments in h_i units, by column
+#pragma unroll
+  for (int c = 0, k = 0; c < M; ++c) {
+    if (taylor_deg<DIM>(c) >= 2) ms[c] = own[k++] * hp[taylor_deg<DIM>(c)];
+    else ms[c] = c == 0 ? 1.0f : 0.0f;
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c2 = 0; c2 < M; ++c2) {
+      if (taylor_deg<DIM>(c2) == 1) continue;
+      bool below = true;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) below = below && exponent<DIM>(c2, a) <= exponent<DIM>(c, a);
+      if (!below) continue;
+      float term = ms[c2];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int e = exponent<DIM>(c, a) - exponent<DIM>(c2, a);
+        if (e > 0) term *= pw[a][e];
+      }
+      acc += term;
+    }
+    row[c] = acc;
+  }
+}
+
+// The FP32 fold of tpc_fold_staged with the rows formed on the fly: the
+// 16-byte geometry record (offset and index) kLeadR rows ahead, and the pair
+// of ubar_j with cell j's own moments kLeadU rows ahead, through the same
+// commit-group schedule.
+template <int DIM, int M>
+__device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const float2* __restrict__ upair,
+                                                    int64_t i, float2 pi, int n, float eh2, float w_centre,
+                                                    SqrtFreeQR<float, M>& f) {
+  constexpr int OW4 = own32_width(DIM, M) / 4;
+  constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
+  __shared__ float4 sgeo[kRec][kTpcThreads];
+  __shared__ float4 sown[kU][OW4][kTpcThreads];
+  __shared__ float2 su[kU][kTpcThreads];
+  const int tid = threadIdx.x;
+  const int64_t N = dm.N;
+  const float4* geo = reinterpret_cast<const float4*>(dm.geo32);
+  const float4* own = reinterpret_cast<const float4*>(dm.own32);
+  float hp[5];
+  hp[0] = 1.0f;
+  hp[1] = static_cast<float>(1.0 / dm.h[i]);
+#pragma unroll
+  for (int k = 2; k < 5; ++k) hp[k] = hp[k - 1] * hp[1];
+  auto fetch_rec = [&](int t, int slot) { cp_async16(&sgeo[slot][tid], geo + static_cast<int64_t>(t) * N + i); };
+  auto fetch_u = [&](int rec_slot, int u_slot) {
+    const int j = __float_as_int(reinterpret_cast<const float*>(&sgeo[rec_slot][tid])[DIM]);
+    cp_async8(&su[u_slot][tid], upair + j);
+#pragma unroll
+    for (int k = 0; k < OW4; ++k) cp_async16(&sown[u_slot][k][tid], own + static_cast<int64_t>(j) * OW4 + k);
+  };
+  sqrt_free_init(f);
+  for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
+  cp_async_commit();
+  cp_async_wait<0>();
+  for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
+  cp_async_commit();
+#pragma unroll
+  for (int k = 0; k < kPending; ++k) cp_async_commit();
+  int sr = 0, sv = 0;  // slots of row t
+  for (int t = 0; t < n; ++t) {
+    cp_async_wait<kPending>();
+    const float4 gv = sgeo[sr][tid];
+    const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+    float d[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) d[a] = gg[a];
+    float ow[OW4 * 4];
+#pragma unroll
+    for (int k = 0; k < OW4; ++k) {
+      const float4 v = sown[sv][k][tid];
+      ow[4 * k] = v.x;
+      ow[4 * k + 1] = v.y;
+      ow[4 * k + 2] = v.z;
+      ow[4 * k + 3] = v.w;
+    }
+    const float2 pj = su[sv][tid];
+    const int srU = sr + kLeadU < kRec ? sr + kLeadU : sr + kLeadU - kRec;
+    const int srR = sr + kLeadR < kRec ? sr + kLeadR : sr + kLeadR - kRec;
+    const int svU = sv + kLeadU < kU ? sv + kLeadU : sv + kLeadU - kU;
+    if (t + kLeadU < n) fetch_u(srU, svU);
+    if (t + kLeadR < n) fetch_rec(t + kLeadR, srR);
+    cp_async_commit();
+    float z[M + 1];
+    float row[M];
+    shifted_row<DIM, M>(d, hp, ow, row);
+#pragma unroll
+    for (int c = 0; c < M; ++c) z[c] = row[c];
+    const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
+    const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
+    z[M] = dev;
+    sqrt_free_fold(f, z, w * w);
+    sr = sr + 1 < kRec ? sr + 1 : 0;
+    sv = sv + 1 < kU ? sv + 1 : 0;
+  }
+  cp_async_wait<0>();
+}
+
 // Coefficients and facet values of cell i (FP32-bulk: the polynomial in FP32,
 // ubar_i added in FP64), or with fdev set the FP32 deviations ubar - ubar_i.
 template <typename T, int DIM, int M>
@@ -169,7 +300,7 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
   }
 }
 
-template <typename T, int DIM, int M>
+template <typename T, int DIM, int M, bool OTF = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
                  double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
@@ -184,7 +315,10 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
   if constexpr (sizeof(T) == 4) {
     const float2 pi = work.upair[i];
     tpc_weights_pair<DIM>(dm, sp, work.upair, i, pi, &eh2, &wc);
-    tpc_fold_staged<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
+    if constexpr (OTF)
+      tpc_fold_staged_otf<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
+    else
+      tpc_fold_staged<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
   } else {
     tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
     tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
@@ -422,6 +556,14 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
   const T flag = f32 ? static_cast<T>(sp.kappa_flag) : T(1e6);
   const T pivot = f32 ? static_cast<T>(kRefinePivotBound) : flag;
   if (f32 && !work.upair) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (work.otf) {
+      if (!dm.geo32 || !dm.own32) return cudaErrorInvalidValue;
+      recon_tpc_kernel<T, DIM, M, true><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
+                                                                  out.fdev, out.counters, work, flag, pivot);
+      return cudaGetLastError();
+    }
+  }
   recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
                                                         out.fdev, out.counters, work, flag, pivot);
   return cudaGetLastError();

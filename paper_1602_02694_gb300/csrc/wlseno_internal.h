@@ -96,6 +96,13 @@ struct DeviceMesh {
   // (t*N + i)*rec_width floats holds the m moments of row t of cell i, then
   // the stencil index (int32 bits), then zero padding to a 16-byte multiple
   float* rec32;             // [nmax][N][rec_width]
+  // FP32 row geometry for the moments-on-the-fly kernel (FP32-bulk): record
+  // (t, i) at (t*N + i)*4 floats holds (x_j - x_i)/h_i (dim floats, minimum
+  // image), the stencil index as int32 bits, zeros; own32 holds every cell's
+  // own central moments of degree >= 2 in absolute units (own_width floats)
+  float* geo32;             // [nmax][N][4]
+  float* own32;             // [N][own_width]
+  int own_width;            // own32_width(dim, m)
   const FacetF32* ff32;     // [N][dim+1] FP32-bulk scalar flux coefficients (else null)
   const float2* inv_vol2;   // [N] FP32-bulk scalar: 1/|tau| as a double-float pair (else null)
   int rec_width;            // round_up(m + 1, 4)
@@ -103,6 +110,9 @@ struct DeviceMesh {
 
 // Width in floats of one FP32 row record (moments + index, 16-byte padded).
 __host__ __device__ constexpr int rec32_width(int m) { return (m + 1 + 3) / 4 * 4; }
+// Width in floats of a cell's own-moment record: the m - 1 - dim Taylor
+// columns of degree >= 2, 16-byte padded.
+__host__ __device__ constexpr int own32_width(int dim, int m) { return (m - 1 - dim + 3) / 4 * 4; }
 
 struct SchemeParams {
   int pde;
@@ -171,6 +181,9 @@ struct TpcWork {
   // with the refinement sweep (fork and join through the two events)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // FP32-bulk main kernel: form each moment row from geo32/own32 instead of
+  // streaming the stored row records
+  bool otf = false;
 };
 
 // pair[k] = (fl32(u[k]), fl32(u[k] - fl32(u[k]))) for k < n.

@@ -35,7 +35,7 @@ class wlseno_mesh(ctypes.Structure):
 class wlseno_stencil_opts(ctypes.Structure):
     _fields_ = [("order_p", ctypes.c_int), ("ring", ctypes.c_double), ("radius_cut", ctypes.c_double),
                 ("min_rows", ctypes.c_int), ("lanes_per_cell", ctypes.c_int),
-                ("rows_per_lane", ctypes.c_int)]
+                ("rows_per_lane", ctypes.c_int), ("moments_mode", ctypes.c_int)]
 
 
 class wlseno_scheme(ctypes.Structure):
@@ -51,7 +51,8 @@ class wlseno_info(ctypes.Structure):
                 ("n_comp", ctypes.c_int), ("n_meshes", ctypes.c_int), ("n_cells", ctypes.c_int64),
                 ("stencil_nnz", ctypes.c_int64), ("max_stencil", ctypes.c_int),
                 ("min_stencil", ctypes.c_int), ("quad_per_facet", ctypes.c_int),
-                ("lanes_per_cell", ctypes.c_int), ("rows_per_lane", ctypes.c_int)]
+                ("lanes_per_cell", ctypes.c_int), ("rows_per_lane", ctypes.c_int),
+                ("moments_mode", ctypes.c_int)]
 
 
 KERNEL_KINDS = ("moments", "reconstruct", "flux", "dt", "adjoint", "fixup")
@@ -202,7 +203,7 @@ class Context:
 
     # -- entry points
     def build_stencils(self, meshes, order_p, ring, radius_cut=0.0, min_rows=0,
-                       lanes_per_cell=0, rows_per_lane=0):
+                       lanes_per_cell=0, rows_per_lane=0, moments_mode=0):
         """wlseno_build_stencils over one mesh or a list of meshes (objects with
         .vertices [nv][d] float64, .cells [nc][d+1] int64 and .period [d])."""
         if not isinstance(meshes, (list, tuple)):
@@ -221,7 +222,7 @@ class Context:
             arr[k].cells = c.ctypes.data
             arr[k].period = p.ctypes.data
         opts = wlseno_stencil_opts(order_p, float(ring), float(radius_cut), min_rows,
-                                   lanes_per_cell, rows_per_lane)
+                                   lanes_per_cell, rows_per_lane, moments_mode)
         self._check(self.lib.wlseno_build_stencils(self.h, arr, len(meshes), ctypes.byref(opts)),
                     "wlseno_build_stencils")
         self._info = self.info()
