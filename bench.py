@@ -42,11 +42,12 @@ N_SIDE, P_ORDER, RING, CFL, JITTER, SEED = 256, 4, 2.0, 0.3, 0.2, 1
 FP32_PEAK_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
 N_SMS = 152
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal)
-# DRAM bytes (read + write) of one launch of the FP32 main reconstruction
-# kernel on this workload, from an ncu capture of the same kernel
-# (profiles/recon_tpc_fp32_burgers256_p4.md); None where no capture of the
-# current kernel exists.
-TRAFFIC_PER_LAUNCH = {"fp32_bulk": 244.78e6 + 4.41e6, "fp64": None}
+# DRAM bytes (read + write) of one launch of the main reconstruction kernel
+# on this workload, by (precision, moments mode), from an ncu capture of the
+# same kernel (profiles/recon_tpc_*_burgers256_p4.md); None where no capture
+# of the current kernel exists.
+TRAFFIC_PER_LAUNCH = {("fp32_bulk", 0): 244.78e6 + 4.41e6, ("fp32_bulk", 1): 93.36e6 + 2.78e6,
+                      ("fp64", 0): None}
 
 
 def parse_args():
@@ -61,7 +62,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="auto",
                     help="reconstruction kernel shape 'lanes,rows' (1,0 = thread per cell); "
-                         "default: the autotuner picks")
+                         "default: the autotuner picks the shape and the moments mode")
+    ap.add_argument("--moments", type=int, default=0, choices=[0, 1],
+                    help="with a fixed --shape 1,0: FP32 moment rows stored (0) or formed on the fly (1)")
     return ap.parse_args()
 
 
@@ -83,11 +86,13 @@ def algorithmic_flops_per_cell(n, m, npts):
     return f
 
 
-def algorithmic_bytes_per_cell(n, m, npts, dim, a_bytes):
+def algorithmic_bytes_per_cell(n, m, npts, dim, a_bytes, on_the_fly=False):
     """Bytes one cell's reconstruction must move at least once: its stencil
-    rows of A, its stencil indices, its own state, h, facet neighbours and
-    points, and its facet values."""
-    return n * m * a_bytes + 4 * n + 8 + 8 + 4 * (dim + 1) + npts * dim * a_bytes + 8 * npts
+    rows of A (formed on the fly: each row's offset instead, and the cell's
+    own central moments of degree >= 2), its stencil indices, its own state,
+    h, facet neighbours and points, and its facet values."""
+    rows = n * dim * 4 + (m - 1 - dim) * 4 if on_the_fly else n * m * a_bytes
+    return rows + 4 * n + 8 + 8 + 4 * (dim + 1) + npts * dim * a_bytes + 8 * npts
 
 
 class ClockSampler:
@@ -264,11 +269,13 @@ def gpu_uuid(torch, dev):
         return None
 
 
-def make_context(precision, mesh, dev_index, shape="auto"):
+def make_context(precision, mesh, dev_index, shape="auto", moments=0):
     from paper_1602_02694_gb300.wlseno import Context
     ctx = Context(dev_index, pde="burgers", precision=precision)
     lanes, rows = (0, 0) if shape == "auto" else (int(v) for v in shape.split(","))
-    ctx.build_stencils(mesh, order_p=P_ORDER, ring=RING, lanes_per_cell=lanes, rows_per_lane=rows)
+    mode = moments if shape != "auto" and precision == "fp32_bulk" else 0
+    ctx.build_stencils(mesh, order_p=P_ORDER, ring=RING, lanes_per_cell=lanes, rows_per_lane=rows,
+                       moments_mode=mode)
     ctx.autotune_enabled = shape == "auto"
     return ctx
 
@@ -323,8 +330,34 @@ def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
         ms = float(t.item())
     stages = max(1, diag["launches_by_kind"]["flux"])  # one flux/RK launch per stage
     return {"ms": ms, "u": u, "diag": diag, "launches": launches,
-            "clocks": clocks, "setup_s": setup_s, "shape": shape[:2],
+            "clocks": clocks, "setup_s": setup_s, "shape": shape[:2], "info": ctx.info(),
             "flagged_per_stage": diag["flagged_cells"] / stages}
+
+
+def run_moments_mode(torch, mesh, u0, dev_index, mode, steps):
+    """The FP32-bulk thread-per-cell kernel in one moments mode: step time
+    (captured steps, CUDA events) and the main kernel's mean launch time."""
+    ctx = make_context("fp32_bulk", mesh, dev_index, "1,0", mode)
+    ctx.precompute_moments()
+    dev = torch.device("cuda", dev_index)
+    u = torch.tensor(u0, dtype=torch.float64, device=dev)
+    ctx.rk_step(u, cfl=CFL, n_steps=3)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    ctx.rk_step(u, cfl=CFL, n_steps=steps)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    ctx.set_timing(True)
+    ctx.rk_step(u, cfl=CFL, n_steps=steps)
+    torch.cuda.synchronize(dev)
+    d = ctx.diagnostics()
+    ctx.set_timing(False)
+    ctx.close()
+    k = d["launches_by_kind"]["reconstruct"]
+    return {"ms_per_step": ms / steps, "main_kernel_us": 1e3 * d["kernel_ms"]["reconstruct"] / max(1, k)}
 
 
 def run_e2e(torch, ctx, u0, steps):
@@ -349,6 +382,7 @@ def roofline(info, diag, n_cells, precision, peaks, sm_mhz):
     n = info["stencil_nnz"] / n_cells
     m = info["m"]
     npts = (info["dim"] + 1) * info["quad_per_facet"]
+    otf = precision == "fp32_bulk" and info.get("moments_mode", 0) == 1
     launches = diag["launches_by_kind"]["reconstruct"]
     ms = diag["kernel_ms"]["reconstruct"]
     if launches == 0 or ms <= 0:
@@ -356,7 +390,7 @@ def roofline(info, diag, n_cells, precision, peaks, sm_mhz):
     dur = ms / launches * 1e-3
     flops = algorithmic_flops_per_cell(n, m, npts) * n_cells
     a_bytes = 4 if precision == "fp32_bulk" else 8
-    nbytes = algorithmic_bytes_per_cell(n, m, npts, info["dim"], a_bytes) * n_cells
+    nbytes = algorithmic_bytes_per_cell(n, m, npts, info["dim"], a_bytes, otf) * n_cells
     clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     if precision == "fp32_bulk":
         alu_peak = N_SMS * FP32_PEAK_LANES_PER_SM * 2 * clock / 1e12
@@ -365,12 +399,13 @@ def roofline(info, diag, n_cells, precision, peaks, sm_mhz):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alu = flops / dur / 1e12
     hbm = nbytes / dur / 1e9
-    name = f"main reconstruction kernel ({precision}), per launch"
+    name = f"main reconstruction kernel ({precision}{', moments on the fly' if otf else ''}), per launch"
+    traffic = TRAFFIC_PER_LAUNCH.get((precision, 1 if otf else 0))
     out_alu = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
-               "frac": alu / alu_peak, "traffic": None, "kernel": name,
+               "frac": alu / alu_peak, "traffic": traffic, "kernel": name,
                "flops_per_launch": flops, "launch_us": dur * 1e6}
     out_hbm = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
-               "frac": hbm / hbm_peak, "traffic": TRAFFIC_PER_LAUNCH[precision], "kernel": name,
+               "frac": hbm / hbm_peak, "traffic": traffic, "kernel": name,
                "bytes_per_launch": nbytes, "launch_us": dur * 1e6}
     return (out_alu, out_hbm) if out_alu["frac"] >= out_hbm["frac"] else (out_hbm, out_alu)
 
@@ -461,7 +496,7 @@ def main():
     peaks = load_peaks()
     sampler = ClockSampler(gpu_uuid(torch, dev))
 
-    ctx32 = make_context("fp32_bulk", mesh, dev.index, args.shape)
+    ctx32 = make_context("fp32_bulk", mesh, dev.index, args.shape, args.moments)
     info = ctx32.info()
     r32 = run_precision(torch, ctx32, u0, args.steps, args.warmup, dist, sampler)
     ctx64 = make_context("fp64", mesh, dev.index, args.shape)
@@ -484,8 +519,12 @@ def main():
     value = total / (r32["ms"] * 1e-3)
     value64 = total / (r64["ms"] * 1e-3)
     clocks = r32["clocks"] or {}
-    roof = roofline(info, r32["diag"], n_cells, "fp32_bulk", peaks, None)
-    roof64 = roofline(info, r64["diag"], n_cells, "fp64", peaks, None)
+    roof = roofline(r32["info"], r32["diag"], n_cells, "fp32_bulk", peaks, None)
+    roof64 = roofline(r64["info"], r64["diag"], n_cells, "fp64", peaks, None)
+    mode_steps = max(3, min(args.steps, 50))
+    modes = {name: run_moments_mode(torch, mesh, u0, dev.index, mode, mode_steps)
+             for mode, name in ((0, "stored_rows"), (1, "on_the_fly"))}
+    modes["chosen"] = "on_the_fly" if r32["info"]["moments_mode"] == 1 else "stored_rows"
     kern = {k: {"launches": r32["diag"]["launches_by_kind"][k], "ms": r32["diag"]["kernel_ms"][k]}
             for k in ("reconstruct", "fixup", "flux", "dt")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -508,6 +547,7 @@ def main():
             "setup_s": {"moments_and_autotune_fp32": r32["setup_s"],
                         "moments_and_autotune_fp64": r64["setup_s"]},
             "kernel_shape": {"fp32_bulk": list(r32["shape"]), "fp64": list(r64["shape"])},
+            "moments_modes": modes,
             "refined_cells_per_stage": r32["flagged_per_stage"],
             "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                        "reasons": clocks.get("reasons", [])},
