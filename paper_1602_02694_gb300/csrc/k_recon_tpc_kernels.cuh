@@ -204,7 +204,10 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
                                                     int64_t i, float2 pi, int n, float eh2, float w_centre,
                                                     SqrtFreeQR<float, M>& f) {
   constexpr int OW4 = own32_width(DIM, M) / 4;
-  constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
+  // the 16-byte geometry records allow a deeper lead than the stored rows
+  constexpr int kLeadRo = 7, kRec = kLeadRo + 1, kU = kLeadU + 1, kUnrollO = 8;
+  constexpr int kPendingO = (kLeadU - 1) < (kLeadRo - kLeadU - 1) ? (kLeadU - 1) : (kLeadRo - kLeadU - 1);
+  static_assert(kUnrollO % kRec == 0 && kUnrollO % kU == 0, "unroll by whole slot cycles");
   __shared__ float4 sgeo[kRec][kTpcThreads];
   __shared__ float4 sown[kU][OW4][kTpcThreads];
   __shared__ float2 su[kU][kTpcThreads];
@@ -225,48 +228,50 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
     for (int k = 0; k < OW4; ++k) cp_async16(&sown[u_slot][k][tid], own + static_cast<int64_t>(j) * OW4 + k);
   };
   sqrt_free_init(f);
-  for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
+  for (int t = 0; t < kLeadRo && t < n; ++t) fetch_rec(t, t);
   cp_async_commit();
   cp_async_wait<0>();
   for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
 #pragma unroll
-  for (int k = 0; k < kPending; ++k) cp_async_commit();
-  int sr = 0, sv = 0;  // slots of row t
-  for (int t = 0; t < n; ++t) {
-    cp_async_wait<kPending>();
-    const float4 gv = sgeo[sr][tid];
-    const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
-    float d[DIM];
+  for (int k = 0; k < kPendingO; ++k) cp_async_commit();
+  // unrolled by a common multiple of both slot counts: every slot, and so
+  // every shared-memory address, is a compile-time constant
+  for (int t0 = 0; t0 < n; t0 += kUnrollO) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) d[a] = gg[a];
-    float ow[OW4 * 4];
+    for (int s = 0; s < kUnrollO; ++s) {
+      const int t = t0 + s;
+      if (t >= n) break;
+      const int sr = s % kRec, sv = s % kU;  // slots of row t
+      cp_async_wait<kPendingO>();
+      const float4 gv = sgeo[sr][tid];
+      const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+      float d[DIM];
 #pragma unroll
-    for (int k = 0; k < OW4; ++k) {
-      const float4 v = sown[sv][k][tid];
-      ow[4 * k] = v.x;
-      ow[4 * k + 1] = v.y;
-      ow[4 * k + 2] = v.z;
-      ow[4 * k + 3] = v.w;
+      for (int a = 0; a < DIM; ++a) d[a] = gg[a];
+      float ow[OW4 * 4];
+#pragma unroll
+      for (int k = 0; k < OW4; ++k) {
+        const float4 v = sown[sv][k][tid];
+        ow[4 * k] = v.x;
+        ow[4 * k + 1] = v.y;
+        ow[4 * k + 2] = v.z;
+        ow[4 * k + 3] = v.w;
+      }
+      const float2 pj = su[sv][tid];
+      if (t + kLeadU < n) fetch_u((s + kLeadU) % kRec, (s + kLeadU) % kU);
+      if (t + kLeadRo < n) fetch_rec(t + kLeadRo, (s + kLeadRo) % kRec);
+      cp_async_commit();
+      float z[M + 1];
+      float row[M];
+      shifted_row<DIM, M>(d, hp, ow, row);
+#pragma unroll
+      for (int c = 0; c < M; ++c) z[c] = row[c];
+      const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
+      const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
+      z[M] = dev;
+      sqrt_free_fold(f, z, w * w);
     }
-    const float2 pj = su[sv][tid];
-    const int srU = sr + kLeadU < kRec ? sr + kLeadU : sr + kLeadU - kRec;
-    const int srR = sr + kLeadR < kRec ? sr + kLeadR : sr + kLeadR - kRec;
-    const int svU = sv + kLeadU < kU ? sv + kLeadU : sv + kLeadU - kU;
-    if (t + kLeadU < n) fetch_u(srU, svU);
-    if (t + kLeadR < n) fetch_rec(t + kLeadR, srR);
-    cp_async_commit();
-    float z[M + 1];
-    float row[M];
-    shifted_row<DIM, M>(d, hp, ow, row);
-#pragma unroll
-    for (int c = 0; c < M; ++c) z[c] = row[c];
-    const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
-    const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
-    z[M] = dev;
-    sqrt_free_fold(f, z, w * w);
-    sr = sr + 1 < kRec ? sr + 1 : 0;
-    sv = sv + 1 < kU ? sv + 1 : 0;
   }
   cp_async_wait<0>();
 }
