@@ -46,7 +46,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal)
 # on this workload, by (precision, moments mode), from an ncu capture of the
 # same kernel (profiles/recon_tpc_*_burgers256_p4.md); None where no capture
 # of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("fp32_bulk", 0): 244.78e6 + 4.41e6, ("fp32_bulk", 1): 93.36e6 + 2.78e6,
+TRAFFIC_PER_LAUNCH = {("fp32_bulk", 0): 244.78e6 + 4.41e6, ("fp32_bulk", 1): 93.38e6 + 2.62e6,
                       ("fp64", 0): None}
 
 
