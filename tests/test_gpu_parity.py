@@ -166,9 +166,13 @@ def test_rk3_steps_fp64(dev, name, pde, steps):
     ctx.close()
 
 
-def test_rk3_fp32_bulk_matches_fp64_oracle(dev):
-    ctx, mesh, prob = make_ctx("tri10_p4_ring2", precision="fp32_bulk", pde="burgers")
-    ubar = synth.burgers_2d_initial(mesh)
+@pytest.mark.parametrize("name,pde", [("tri10_p4_ring2", "burgers"), ("tri9_p3_periodic", "advection"),
+                                      ("tri7_p3_open", "advection")])
+def test_rk3_fp32_bulk_matches_fp64_oracle(dev, name, pde):
+    """FP32-bulk steps (double-float flux sums and RK update) against the
+    FP64 oracle, for both scalar fluxes and a transmissive boundary."""
+    ctx, mesh, prob = make_ctx(name, precision="fp32_bulk", pde=pde)
+    ubar = synth.burgers_2d_initial(mesh) if pde == "burgers" else field(mesh)
     u = torch.tensor(ubar, device=dev)
     steps = 4
     for _ in range(steps):
