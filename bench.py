@@ -33,6 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_1602_02694_gb300 import synth  # noqa: E402
+from paper_1602_02694_gb300.replicas import max_over_ranks, sum_over_ranks  # noqa: E402
 
 METRIC = "cell-stage updates/sec (WLS-ENO recon+flux) vs plain FP64 GPU, equal accuracy"
 UNIT = "cell-stage updates/s"
@@ -345,10 +346,7 @@ def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
     diag = ctx.diagnostics()
     ctx.set_timing(False)
     del v
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)  # the job is as slow as its slowest rank
     stages = max(1, diag["launches_by_kind"]["flux"])  # one flux/RK launch per stage
     return {"ms": ms, "u": u, "diag": diag, "launches": launches,
             "clocks": clocks, "setup_s": setup_s, "shape": shape[:2], "info": ctx.info(),
@@ -526,13 +524,12 @@ def main():
 
     e2e_steps = max(3, min(args.steps, 50))
     el, state_bytes = run_e2e(torch, ctx32, u0, e2e_steps)
-    if dist:
-        t = torch.tensor([el], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, dist, dev)
     ctx32.close()
 
-    total = world * n_cells * 3 * args.steps
+    # every rank steps its own replica: the units of all ranks over the
+    # slowest rank's time (already max-reduced)
+    total = sum_over_ranks(n_cells * 3 * args.steps, dist, dev)
     value = total / (r32["ms"] * 1e-3)
     value64 = total / (r64["ms"] * 1e-3)
     clocks = r32["clocks"] or {}
@@ -554,7 +551,7 @@ def main():
                          "rel_l1_fp32_bulk_vs_fp64_after_timed_steps": rel_l1,
                          "accuracy": accuracy,
                          "roofline": roof64[0] if roof64 else None},
-            "e2e": {"value": world * n_cells * 3 * e2e_steps / el, "unit": UNIT,
+            "e2e": {"value": sum_over_ranks(n_cells * 3 * e2e_steps, dist, dev) / el, "unit": UNIT,
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                     "steps": e2e_steps},
             "gpu_launches": r32["launches"],
