@@ -775,15 +775,21 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   if ((e = cudaMemsetAsync(ctx->d_counters, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset counters");
   // one TVD-RK3 step on stream `st` (Sec. 4.2.1, Eq. (3rd-order-Runge-Kutta))
+  // FP32-bulk scalar thread-per-cell path: the FP32 pairs of u for stage 1
+  // are made with the time step (scratch slot of d_pair; stages 2 and 3 read
+  // them as the pairs of u0)
+  float2* pre = ctx->d_pair && ctx->G == 1 && C == 1 && ctx->scheme.pde != WLSENO_EULER ? ctx->d_pair : nullptr;
   auto enqueue_step = [&](cudaStream_t st) -> cudaError_t {
     cudaError_t err = cudaSuccess;
     if (dt >= 0.0) {  // dt < 0: the per-mesh steps already in d_dt
       int nl = 0;
       KernelScope scope(ctx, WLSENO_KERNEL_DT, st);
       err = launch_cfl_dt_impl(ctx->dm, ctx->sp, ctx->host.n_meshes, u, ctx->d_rmin, cfl,
-                               dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl, ctx->d_dt2);
+                               dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl, ctx->d_dt2, pre);
       scope.done(nl);
       if (err != cudaSuccess) return err;
+    } else if (pre && (err = split_state(ctx, u, pre, st)) != cudaSuccess) {
+      return err;
     }
     // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
     double* k1 = ctx->d_k1;
@@ -794,7 +800,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     float2* p2 = ctx->d_pair ? ctx->d_pair + 2 * CN : nullptr;
     // the pairs of u stay in the scratch slot from stage 1 on (one component)
     float2* p0 = ctx->d_pair && ctx->scheme.n_comp == 1 ? ctx->d_pair : nullptr;
-    if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st, nullptr, p1)) != cudaSuccess ||
+    if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st, pre, p1)) != cudaSuccess ||
         (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st, p1, p2, p0)) != cudaSuccess ||
         (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st, p2, nullptr, p0)) != cudaSuccess)
       return err;

@@ -350,8 +350,13 @@ __global__ void split_pairs_kernel(const double* __restrict__ u, float2* __restr
 // integer order is the numeric order, so atomicMax is exact and deterministic).
 __global__ void max_abs_kernel(int64_t N, const double* __restrict__ u,
                                const int32_t* __restrict__ mesh_of,
-                               unsigned long long* __restrict__ lmax_bits) {
+                               unsigned long long* __restrict__ lmax_bits, float2* __restrict__ pairs) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (pairs && i < N) {  // the FP32 pairs of the state, in the same pass
+    const double v = u[i];
+    const float hi = __double2float_rn(v);
+    pairs[i] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+  }
   const bool in = i < N;
   const int mesh = in ? mesh_of[i] : -1;
   unsigned long long bits = in ? static_cast<unsigned long long>(__double_as_longlong(fabs(u[i]))) : 0ull;
@@ -439,7 +444,7 @@ cudaError_t launch_split_pairs(const double* u, float2* pair, int64_t n, cudaStr
 cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
                                const double* u, const double* rmin, double cfl, double dt_fixed,
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
-                               int* launches, float2* dt2) {
+                               int* launches, float2* dt2, float2* pairs_out) {
   double speed = 0.0;
   for (int a = 0; a < dm.dim; ++a) speed += sp.vel[a] * sp.vel[a];
   speed = std::sqrt(speed);
@@ -449,11 +454,18 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
-    max_abs_kernel<<<blocks, threads, 0, s>>>(dm.N, u, dm.mesh_of, lmax_bits);
+    max_abs_kernel<<<blocks, threads, 0, s>>>(dm.N, u, dm.mesh_of, lmax_bits, pairs_out);
     ++*launches;
+    pairs_out = nullptr;  // made
   } else if (dt_fixed <= 0.0 && sp.pde == WLSENO_EULER) {
     cudaError_t e = launch_euler_speed(dm, sp.gamma, u, lmax_bits, n_meshes, s);
     if (e != cudaSuccess) return e;
+    ++*launches;
+  }
+  if (pairs_out) {  // no wave-speed pass to carry them
+    const int threads = 256;
+    split_pairs_kernel<<<static_cast<unsigned>((dm.N + threads - 1) / threads), threads, 0, s>>>(u, pairs_out,
+                                                                                               dm.N);
     ++*launches;
   }
   cfl_dt_kernel<<<(n_meshes + 127) / 128, 128, 0, s>>>(n_meshes, sp.pde, dm.dim, speed, lmax_bits,

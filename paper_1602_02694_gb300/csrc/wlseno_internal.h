@@ -264,11 +264,12 @@ cudaError_t launch_flux_stage_impl(const DeviceMesh& dm, const SchemeParams& sp,
                                    cudaStream_t s, const float2* pin = nullptr, float2* pout = nullptr,
                                    const float2* p0 = nullptr, const float2* dt2 = nullptr);
 // dt_mesh[k] = cfl * rmin[k] / lambda_max(mesh k), or dt_fixed when > 0;
-// dt2 (may be null) receives their double-float pairs.
+// dt2 (may be null) receives their double-float pairs, pairs_out (may be
+// null) the FP32 pairs of u (made in the wave-speed pass when there is one).
 cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int n_meshes,
                                const double* u, const double* rmin, double cfl, double dt_fixed,
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
-                               int* launches, float2* dt2 = nullptr);
+                               int* launches, float2* dt2 = nullptr, float2* pairs_out = nullptr);
 
 // Work arrays of the adjoint (k_adjoint.cu).
 struct AdjointWork {
