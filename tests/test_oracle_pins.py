@@ -530,3 +530,45 @@ def test_balancing_leaves_smooth_data_alone_and_reduces_overshoot_at_a_jump():
     before = sum(O.out_of_range(plain, rnd, i, d) for i, d in enumerate(O.reconstruct_all(plain, rnd)))
     after = sum(O.out_of_range(plain, rnd, i, d) for i, d in enumerate(O.reconstruct_all(bal, rnd)))
     assert before >= 10 and 2 * after <= before, (before, after)
+
+
+# ---------------------------------------------------------------------------
+# moment rows from a cell's own central moments (the binomial shift the
+# moments-on-the-fly kernel uses)
+# ---------------------------------------------------------------------------
+
+def test_moment_rows_are_binomial_shifts_of_own_central_moments():
+    """Row j of cell i's moment matrix (Sec. 3.2, h_i-normalised Taylor
+    monomials about x_i) equals sum over alpha <= kappa of cell j's own
+    central moments M_j[alpha] (about x_j, absolute units) times
+    h_i^-|alpha| d^(kappa-alpha)/(kappa-alpha)!, d = (x_j - x_i)/h_i at the
+    minimum image: the binomial theorem; M_j[0] = 1 and the first moments
+    vanish about the centroid."""
+    rng = np.random.default_rng(12)
+    for mesh, p, ring in ((synth.tri_mesh(8, seed=4), 4, 2.0), (synth.tet_mesh(3, seed=5), 3, 2.0 / 3.0),
+                          (synth.periodic_line_mesh(12, jitter=0.2, seed=6), 5, 2.0)):
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=p, ring=ring)
+        kap = prob.kappas
+        geo = prob.geo
+        for i in rng.choice(prob.N, 6, replace=False):
+            i = int(i)
+            S = prob.stencils[i]
+            A = prob.A(i)
+            Ys = O.stencil_coords(geo, S, i, prob.period)
+            for t, j in enumerate(S):
+                cj = Ys[t].mean(axis=0)  # centroid of the image next to tau_i
+                own = O.moment_row(Ys[t], cj, 1.0, kap)
+                assert abs(own[0] - 1.0) <= 1e-13
+                for k, kp in enumerate(kap):
+                    if sum(kp) == 1:
+                        assert abs(own[k]) <= 1e-13
+                d = (cj - geo.centroid[i]) / geo.h[i]
+                for k, kp in enumerate(kap):
+                    want = 0.0
+                    for k2, al in enumerate(kap):
+                        if all(a <= b for a, b in zip(al, kp)):
+                            term = own[k2] * geo.h[i] ** (-sum(al))
+                            for c in range(len(kp)):
+                                term *= d[c] ** (kp[c] - al[c]) / math.factorial(kp[c] - al[c])
+                            want += term
+                    assert abs(A[t, k] - want) <= 1e-11 * max(1.0, abs(want)), (i, j, kp)
