@@ -28,9 +28,10 @@ def test_static_residual_matches_flux_residual(dev):
 
     mesh = synth.tri_mesh(64, seed=3)  # 8,192 cells
     data = [synth.burgers_2d_initial(mesh), synth.advection_2d_initial(mesh)]
-    for precision, pde, p, ring in (("fp64", "burgers", 4, 2.0), ("fp32_bulk", "advection", 3, 1.0)):
+    for precision, pde, p, ring, mode in (("fp64", "burgers", 4, 2.0, 0), ("fp32_bulk", "advection", 3, 1.0, 0),
+                                          ("fp32_bulk", "burgers", 4, 2.0, 1)):
         ctx = Context(0, pde=pde, precision=precision)
-        ctx.build_stencils(mesh, order_p=p, ring=ring)
+        ctx.build_stencils(mesh, order_p=p, ring=ring, moments_mode=mode)
         ctx.precompute_moments()
         for ubar in data:  # two calls in a row; the second sees other data
             u = torch.tensor(ubar, dtype=torch.float64, device=dev)
