@@ -180,8 +180,12 @@ __global__ void euler_speed_kernel(int64_t N, double gamma, const double* __rest
 cudaError_t launch_euler_positivity(const DeviceMesh& dm, double gamma, const double* ubar,
                                     double* fvals, unsigned long long* counters, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((dm.N + 255) / 256);
-  if (dm.dim != 2) return cudaErrorInvalidValue;
-  euler_positivity_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
+  if (dm.dim == 1)
+    euler_positivity_kernel<1><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
+  else if (dm.dim == 2)
+    euler_positivity_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -190,22 +194,33 @@ cudaError_t launch_euler_flux_stage(const DeviceMesh& dm, double gamma, int prec
                                     double a, double b, const double* dt_mesh, bool residual_only,
                                     double* out, unsigned long long* counters, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((dm.N + 127) / 128);
-  if (dm.dim != 2) return cudaErrorInvalidValue;
+  if (dm.dim != 1 && dm.dim != 2) return cudaErrorInvalidValue;
   const int ro = residual_only ? 1 : 0;
-  if (precision == WLSENO_FP32_BULK)
-    euler_flux_stage_kernel<float, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-  else
-    euler_flux_stage_kernel<double, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  const bool f32 = precision == WLSENO_FP32_BULK;
+  if (dm.dim == 1) {
+    if (f32)
+      euler_flux_stage_kernel<float, 1><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+    else
+      euler_flux_stage_kernel<double, 1><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  } else {
+    if (f32)
+      euler_flux_stage_kernel<float, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+    else
+      euler_flux_stage_kernel<double, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
                                unsigned long long* lmax_bits, int n_meshes, cudaStream_t s) {
-  if (dm.dim != 2) return cudaErrorInvalidValue;
+  if (dm.dim != 1 && dm.dim != 2) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(lmax_bits, 0, sizeof(unsigned long long) * n_meshes, s);
   if (e != cudaSuccess) return e;
   const unsigned blocks = static_cast<unsigned>((dm.N + 255) / 256);
-  euler_speed_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
+  if (dm.dim == 1)
+    euler_speed_kernel<1><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
+  else
+    euler_speed_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
   return cudaGetLastError();
 }
 

@@ -336,6 +336,23 @@ def euler_quadrant_initial(mesh: Mesh, seed: int, gamma: float = 1.4):
     return cons @ frac.T, prim
 
 
+def shock_tube_initial(mesh: Mesh, x0: float = 0.5, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1),
+                       gamma: float = 1.4) -> np.ndarray:
+    """1-D Riemann data (density, velocity, pressure) on each side of x0 --
+    by default the textbook shock-tube states -- as exact conserved cell
+    averages [3][n_cells] (rho, rho u, E) of a 1-D mesh."""
+    assert mesh.dim == 1
+    a = np.minimum(mesh.cell_coords[:, 0, 0], mesh.cell_coords[:, 1, 0])
+    b = np.maximum(mesh.cell_coords[:, 0, 0], mesh.cell_coords[:, 1, 0])
+    frac = np.clip((x0 - a) / (b - a), 0.0, 1.0)  # share of the cell left of x0
+
+    def cons(state):
+        rho, u, p = state
+        return np.array([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u])
+
+    return cons(left)[:, None] * frac[None, :] + cons(right)[:, None] * (1.0 - frac)[None, :]
+
+
 def isentropic_vortex(points: np.ndarray, t: float, gamma: float = 1.4, strength: float = 5.0,
                       core: float = 0.1, center=(0.5, 0.5), velocity=(1.0, 1.0)) -> np.ndarray:
     """Conserved variables [4][P] of the isentropic vortex of the 2-D Euler
