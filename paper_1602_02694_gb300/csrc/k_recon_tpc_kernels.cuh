@@ -4,16 +4,20 @@
 // W A = Q R, solve R d = Q^T W (ubar_S - ubar_i), and estimate the
 // conditioning of W A S from the column-scaled diagonal of R.  For a
 // full-rank system this d is the least-squares solution the paper's QR with
-// column pivoting returns (Sec. 3.3.2).  Cells whose estimate exceeds the
-// flag threshold -- where pivoting and rank truncation could matter, and in
-// FP32-bulk mode where a refinement is due -- go to a work list.
+// column pivoting returns (Sec. 3.3.2).  In FP32-bulk mode the rows are
+// either streamed from stored records or formed on the fly from each stencil
+// cell's offset and own central moments (moments mode 1).  Cells whose
+// estimate exceeds the flag threshold -- where pivoting and rank truncation
+// could matter, and in FP32-bulk mode where a refinement is due -- go to a
+// refine record or a work list.
 //
-// Work-listed cells are then redone by the lane-group kernel (rows spread over
-// the lanes of a group, so their loads run in parallel): the paper's path in
-// full -- column scaling, QR with column pivoting, numerical rank, basic
-// solution -- and, in FP32-bulk mode, one refinement sweep with the FP64
-// residual (FP64 weights and moments).  It overwrites the main kernel's
-// outputs for those cells.
+// Refine records are finished by one sweep with the FP64 residual
+// (refine_kernel).  Work-listed cells are redone by the lane-group kernel
+// (rows spread over the lanes of a group, so their loads run in parallel):
+// the paper's path in full -- column scaling, QR with column pivoting,
+// numerical rank, basic solution -- and, in FP32-bulk mode, one refinement
+// sweep with the FP64 residual (FP64 weights and moments).  Both overwrite
+// the main kernel's outputs for their cells.
 #pragma once
 
 #include "k_recon_tpc.cuh"
