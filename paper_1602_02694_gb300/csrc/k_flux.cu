@@ -8,7 +8,11 @@
 // facet's lower-indexed cell with that cell's normal and area (stored
 // identically in both cells' facet records).  Both cells therefore compute the
 // bitwise-same flux and use it with opposite signs: no atomics, a fixed
-// summation order, and exact discrete conservation up to the final FP64 sums.
+// summation order, and exact discrete conservation up to the final sums.
+// Variants: FP64 facet values (FP64 mode, and FP32-bulk with lane-group
+// shapes); FP32 facet deviations with FP64 sums (FP32-bulk without the
+// state's FP32 pairs); FP32 deviations with double-float sums and stage
+// (the FP32-bulk thread-per-cell path, dfloat.cuh).
 #include <cmath>
 #include <type_traits>
 
