@@ -544,7 +544,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "fp32-bulk (f32 QR/evaluation/deviation flux; f64 moments and refinement residual; double-float (f32 pair) reference flux, accumulation and RK)",
+            "dtype": "f32",
+            "precision": "FP32-bulk: f32 weights, QR, evaluation and deviation flux; f64 moments and "
+                         "refinement residual; double-float (f32 pair) reference flux, sums and RK update",
             "data": "synthetic", "config": dict(config, parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
             "fp64_gpu": {"value": value64, "ms_per_step": r64["ms"] / args.steps,
                          "speedup_fp32_bulk_vs_fp64": value / value64,
