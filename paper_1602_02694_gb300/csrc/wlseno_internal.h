@@ -138,7 +138,7 @@ cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double*
 struct ReconOut {
   double* coeffs;           // [N][m] or null
   double* fvals;            // [N][dim+1][nq] facet values, or null when fdev is set
-  unsigned long long* counters;  // [4]: flagged, rank deficient, nonfinite, spare
+  unsigned long long* counters;  // [4]: flagged, rank deficient, nonfinite, positivity fallbacks
   // FP32-bulk flux path: the facet values as FP32 deviations from the cell
   // average, value = ubar_i + fdev (written instead of fvals when set)
   float* fdev = nullptr;    // [N][dim+1][nq]
