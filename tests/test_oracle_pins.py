@@ -344,6 +344,33 @@ def test_reconstruction_order_smooth_periodic():
     assert min(orders) > 2.6, orders
 
 
+@pytest.mark.parametrize("p,ring,min_order", [(3, 2.0, 2.7), (5, 3.0, 4.5)])
+def test_reconstruction_order_1d(p, ring, min_order):
+    """The 1-D schemes (Sec. 4.2.3, Sec. 4.2.4 build p = 5 on five and seven
+    cells): degree p-1 reconstructions of smooth data on jittered periodic
+    lines are O(h^p) at the cell ends (Sec. 4.1), here observed >= p - 0.5
+    (p = 3 on the 2-ring, p = 5 on the 3-ring)."""
+    errs = []
+    hs = []
+    for n in (16, 32, 64):
+        mesh = synth.periodic_line_mesh(n, jitter=0.2, seed=3)
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=p, ring=ring, min_rows=int(2 * ring + 1))
+
+        def f(P):
+            return np.sin(2 * np.pi * P[:, 0]) + 0.5 * np.cos(4 * np.pi * P[:, 0])
+
+        ubar = synth.cell_averages(mesh, f, k=8)
+        err = 0.0
+        for i in range(prob.N):
+            dvec, _ = prob.reconstruct_cell(ubar, i)
+            for X in prob.geo.coords[i]:
+                err = max(err, abs(prob.eval_poly(dvec, i, X) - f(X[None, :])[0]))
+        errs.append(err)
+        hs.append(1.0 / n)
+    orders = [math.log(errs[k] / errs[k + 1]) / math.log(hs[k] / hs[k + 1]) for k in range(2)]
+    assert min(orders) >= min_order, orders
+
+
 # ---------------------------------------------------------------------------
 # residual (Eq. (fvm), Eq. (flux)): divergence theorem on exact data
 # ---------------------------------------------------------------------------
