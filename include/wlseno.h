@@ -105,9 +105,9 @@ typedef struct {
 
 /* Scheme parameters.
  * pde:        WLSENO_ADVECTION (F = a u), WLSENO_BURGERS (F = u^2/2 (1,..,1)),
- *             WLSENO_EULER (2-D compressible Euler, see below).
+ *             WLSENO_EULER (compressible Euler in 1-D, 2-D, 3-D, see below).
  * n_comp:     number of conserved components (1 for the scalar equations,
- *             3 for 1-D and 4 for 2-D Euler; checked against the mesh).
+ *             dim + 2 for Euler: 3, 4 or 5; checked against the mesh).
  * velocity:   advection velocity a (first dim entries used).
  * eps:        epsilon of the non-smoothness indicator, Eq. (smoothness
  *             indicator), e.g. 1e-2; h is the centre cell's mean edge length.
@@ -154,9 +154,9 @@ typedef struct {
  * balance_margin: the range test's margin as a share of the averages' range
  *             (>= 0; e.g. 0.02).
  *
- * WLSENO_EULER (1-D or 2-D): n_comp = dim + 2 conserved variables (rho,
- * rho u, E) or (rho, rho u, rho v, E), each reconstructed with its own
- * weights (componentwise WLS-ENO; characteristic-wise in 2-D); LF alpha
+ * WLSENO_EULER (1-D, 2-D, 3-D): n_comp = dim + 2 conserved variables (rho,
+ * rho u_1 .. rho u_dim, E), each reconstructed with its own weights
+ * (componentwise WLS-ENO; characteristic-wise optional in 2-D); LF alpha
  * per facet = max over its points and sides of |u.n| + c; a cell whose traces
  * give density or pressure <= 1e-12 at a facet point uses its averages at all
  * its facets (counted in wlseno_diagnostics.positivity_fallbacks). */

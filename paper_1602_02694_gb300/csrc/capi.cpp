@@ -428,7 +428,7 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   *out = nullptr;
   if (scheme->pde != WLSENO_ADVECTION && scheme->pde != WLSENO_BURGERS && scheme->pde != WLSENO_EULER)
     return WLSENO_ERR_INVALID_ARG;
-  if (scheme->pde == WLSENO_EULER ? (scheme->n_comp != 3 && scheme->n_comp != 4) || !(scheme->gamma > 1.0)
+  if (scheme->pde == WLSENO_EULER ? (scheme->n_comp < 3 || scheme->n_comp > 5) || !(scheme->gamma > 1.0)
                                   : scheme->n_comp != 1)
     return WLSENO_ERR_INVALID_ARG;
   if (scheme->precision != WLSENO_FP64 && scheme->precision != WLSENO_FP32_BULK)
@@ -494,9 +494,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   ctx->bal = BalanceWork{};
   wlseno_status st = build_host_setup(meshes, n_meshes, opts, &H, &err, bal_steps);
   if (st != WLSENO_OK) return fail(ctx, st, err);
-  if (ctx->scheme.pde == WLSENO_EULER && (H.dim > 2 || ctx->scheme.n_comp != H.dim + 2))
-    return fail(ctx, WLSENO_ERR_INVALID_ARG,
-                "the Euler path is built for 1-D (n_comp 3) and 2-D (n_comp 4) meshes");
+  if (ctx->scheme.pde == WLSENO_EULER && ctx->scheme.n_comp != H.dim + 2)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "Euler needs n_comp = dim + 2 (3, 4 or 5)");
   if (ctx->scheme.characteristic && H.dim != 2)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "characteristic-wise reconstruction is built for 2-D meshes");
   if ((H.dim == 1 && H.m != 3 && H.m != 5) || (H.dim == 2 && H.m != 6 && H.m != 10) ||

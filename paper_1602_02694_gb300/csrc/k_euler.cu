@@ -11,6 +11,7 @@
 //    the Shu-Osher combine for all four components;
 //  * the largest |u| + c per mesh for the CFL step.
 #include <cmath>
+#include <type_traits>
 
 #include "wlseno_internal.h"
 
@@ -184,6 +185,8 @@ cudaError_t launch_euler_positivity(const DeviceMesh& dm, double gamma, const do
     euler_positivity_kernel<1><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
   else if (dm.dim == 2)
     euler_positivity_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
+  else if (dm.dim == 3)
+    euler_positivity_kernel<3><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, fvals, counters);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -194,33 +197,34 @@ cudaError_t launch_euler_flux_stage(const DeviceMesh& dm, double gamma, int prec
                                     double a, double b, const double* dt_mesh, bool residual_only,
                                     double* out, unsigned long long* counters, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>((dm.N + 127) / 128);
-  if (dm.dim != 1 && dm.dim != 2) return cudaErrorInvalidValue;
+  if (dm.dim < 1 || dm.dim > 3) return cudaErrorInvalidValue;
   const int ro = residual_only ? 1 : 0;
   const bool f32 = precision == WLSENO_FP32_BULK;
-  if (dm.dim == 1) {
+  auto launch = [&](auto D) {
+    constexpr int DD = decltype(D)::value;
     if (f32)
-      euler_flux_stage_kernel<float, 1><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+      euler_flux_stage_kernel<float, DD><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
     else
-      euler_flux_stage_kernel<double, 1><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-  } else {
-    if (f32)
-      euler_flux_stage_kernel<float, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-    else
-      euler_flux_stage_kernel<double, 2><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
-  }
+      euler_flux_stage_kernel<double, DD><<<blocks, 128, 0, s>>>(dm, gamma, fvals, u, u0, a, b, dt_mesh, ro, out, counters);
+  };
+  if (dm.dim == 1) launch(std::integral_constant<int, 1>{});
+  else if (dm.dim == 2) launch(std::integral_constant<int, 2>{});
+  else launch(std::integral_constant<int, 3>{});
   return cudaGetLastError();
 }
 
 cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
                                unsigned long long* lmax_bits, int n_meshes, cudaStream_t s) {
-  if (dm.dim != 1 && dm.dim != 2) return cudaErrorInvalidValue;
+  if (dm.dim < 1 || dm.dim > 3) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(lmax_bits, 0, sizeof(unsigned long long) * n_meshes, s);
   if (e != cudaSuccess) return e;
   const unsigned blocks = static_cast<unsigned>((dm.N + 255) / 256);
   if (dm.dim == 1)
     euler_speed_kernel<1><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
-  else
+  else if (dm.dim == 2)
     euler_speed_kernel<2><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
+  else
+    euler_speed_kernel<3><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
   return cudaGetLastError();
 }
 
