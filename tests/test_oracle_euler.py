@@ -151,3 +151,21 @@ def test_characteristic_vortex_residual_converges_at_second_order():
         means.append(float(np.mean(np.abs(O.residual(prob, U) - dudt))))
     order = math.log2(means[0] / means[1])
     assert order >= 1.8, (means, order)
+
+
+def test_shock_tube_averages_are_exact():
+    """The 1-D shock-tube inputs: cells wholly on one side carry that side's
+    conserved state; the cell holding x0 carries the length-weighted mix;
+    mass and energy totals equal the exact integrals."""
+    nodes = np.array([0.0, 0.2, 0.45, 0.5, 0.8, 1.0])
+    mesh = synth.line_mesh(nodes)
+    U = synth.shock_tube_initial(mesh, x0=0.3, left=(1.0, 0.5, 1.0), right=(0.125, 0.0, 0.1), gamma=1.4)
+    left = np.array([1.0, 0.5, 1.0 / 0.4 + 0.5 * 0.25])
+    right = np.array([0.125, 0.0, 0.1 / 0.4])
+    assert np.allclose(U[:, 0], left, rtol=0, atol=1e-15)
+    frac = (0.3 - 0.2) / (0.45 - 0.2)
+    assert np.allclose(U[:, 1], frac * left + (1 - frac) * right, rtol=0, atol=1e-15)
+    for k in (2, 3, 4):
+        assert np.allclose(U[:, k], right, rtol=0, atol=1e-15)
+    lengths = np.diff(nodes)
+    assert abs(np.sum(lengths * U[0]) - (0.3 * 1.0 + 0.7 * 0.125)) <= 1e-15
