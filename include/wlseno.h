@@ -249,7 +249,9 @@ wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream);
  * this is the least-squares solution the paper's pivoted QR returns.  Other
  * cells are redone by Householder QR with column pivoting of W A S, the rank
  * rule of rank_tol and the basic solution (Sec. 3.3.2), or, in FP32-bulk
- * between kappa_flag and 1e5, refined once with the FP64 residual.
+ * between kappa_flag and 1e5, refined once with the FP64 residual.  With
+ * scheme.balanced the cells out of range are then re-solved on balanced
+ * stencils (see wlseno_scheme).
  * ubar:   [n_comp][n_cells] cell averages, host or device.
  * coeffs: [n_comp][n_cells][m] output, host or device: h-normalised Taylor
  *         coefficients d_kappa = h_i^|kappa| d^kappa u(x_i) (kappa ordered by
@@ -283,7 +285,8 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
  *         steps given to wlseno_set_mesh_dt;  == 0: each step uses
  *         dt = cfl * min_i r_i / lambda_max with r_i = dim |tau_i| / |d tau_i|
  *         and lambda_max the largest wave speed over the cells (advection |a|,
- *         Burgers sqrt(dim) max |ubar|), computed on the device per mesh.
+ *         Burgers sqrt(dim) max |ubar|, Euler max(|u| + c)), computed on the
+ *         device per mesh.
  * dt_out: optional host pointer receiving the last step's dt (of mesh 0); it
  *         synchronises the stream when non-NULL.
  * One step is captured as a CUDA graph (on the context's own stream) and
