@@ -769,8 +769,17 @@ def residual_euler(prob, ubar):
 def euler_char_basis(U, n, gamma):
     """Right eigenvectors R (columns) of d(F(U).n)/dU for 2-D Euler, in the
     order of the eigenvalues u.n - c, u.n (entropy), u.n (shear), u.n + c,
-    and L = R^-1."""
+    and L = R^-1; in 1-D the same without the shear wave (u n - c, u n,
+    u n + c; the decomposition Sec. 5.1.4 prints for n = 1)."""
     rho, vel, p = euler_primitive(np.asarray(U, dtype=np.float64), gamma)
+    if len(n) == 1:
+        (u,), (nx,) = vel, n
+        c = math.sqrt(gamma * p / rho)
+        H = (U[2] + p) / rho
+        R = np.array([[1.0, 1.0, 1.0],
+                      [u - c * nx, u, u + c * nx],
+                      [H - c * u * nx, 0.5 * u * u, H + c * u * nx]])
+        return R, np.linalg.inv(R)
     u, v = vel
     nx, ny = n
     c = math.sqrt(gamma * p / rho)
@@ -785,15 +794,15 @@ def euler_char_basis(U, n, gamma):
 
 
 def euler_char_poly(prob, ubar, i, f):
-    """Characteristic reconstruction of cell i for its facet f: (R, the four
-    fields' coefficient vectors)."""
+    """Characteristic reconstruction of cell i for its facet f: (R, the
+    dim + 2 fields' coefficient vectors)."""
     j, _ = prob.sib[i, f]
     ustar = 0.5 * (ubar[:, i] + ubar[:, j]) if j >= 0 else ubar[:, i]
     n = outward_normal(prob.geo.coords[i], f)
     R, L = euler_char_basis(ustar, n, prob.gamma)
     S = prob.stencils[i]
     w = {k: L @ ubar[:, k] for k in S}
-    return R, [prob.reconstruct_cell({k: w[k][c] for k in S}, i)[0] for c in range(4)]
+    return R, [prob.reconstruct_cell({k: w[k][c] for k in S}, i)[0] for c in range(len(ustar))]
 
 
 def residual_euler_char(prob, ubar):
@@ -801,15 +810,16 @@ def residual_euler_char(prob, ubar):
     fallback is the same reading (a cell with rho or p <= 1e-12 at any of its
     facet points uses its averages at all its facets)."""
     ubar = np.asarray(ubar, dtype=np.float64)
-    assert prob.dim == 2
+    assert prob.dim in (1, 2)
+    C = ubar.shape[0]
     traces = {}
     ok = np.ones(prob.N, dtype=bool)
     for i in range(prob.N):
         X = prob.geo.coords[i]
-        for f in range(3):
+        for f in range(prob.dim + 1):
             R, coef = euler_char_poly(prob, ubar, i, f)
             pts, _ = facet_rule(np.delete(X, f, axis=0))
-            vals = np.array([R @ np.array([prob.eval_poly(coef[c], i, x) for c in range(4)]) for x in pts])
+            vals = np.array([R @ np.array([prob.eval_poly(coef[c], i, x) for c in range(C)]) for x in pts])
             traces[i, f] = vals
             for U in vals:
                 rho, _, pr = euler_primitive(U, prob.gamma)
@@ -817,9 +827,9 @@ def residual_euler_char(prob, ubar):
                     ok[i] = False
     for i in range(prob.N):
         if not ok[i]:
-            for f in range(3):
+            for f in range(prob.dim + 1):
                 traces[i, f] = np.repeat(ubar[:, i][None, :], len(traces[i, f]), axis=0)
-    flux_out = np.zeros((4, prob.N))
+    flux_out = np.zeros((C, prob.N))
     for Lc, fL, Rc in facets(prob):
         X = prob.geo.coords[Lc]
         F = np.delete(X, fL, axis=0)
@@ -840,7 +850,7 @@ def residual_euler_char(prob, ubar):
             UR = traces[Rc, fR][order]
         alpha = max(max(euler_wave_speed(UL[q], n, prob.gamma), euler_wave_speed(UR[q], n, prob.gamma))
                     for q in range(len(w)))
-        g = np.zeros(4)
+        g = np.zeros(C)
         for q in range(len(w)):
             g += w[q] * 0.5 * (euler_normal_flux(UL[q], n, prob.gamma) + euler_normal_flux(UR[q], n, prob.gamma)
                                - alpha * (UR[q] - UL[q]))

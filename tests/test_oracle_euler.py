@@ -169,3 +169,36 @@ def test_shock_tube_averages_are_exact():
         assert np.allclose(U[:, k], right, rtol=0, atol=1e-15)
     lengths = np.diff(nodes)
     assert abs(np.sum(lengths * U[0]) - (0.3 * 1.0 + 0.7 * 0.125)) <= 1e-15
+
+
+def test_characteristic_basis_1d_diagonalises_the_normal_flux_jacobian():
+    """1-D (Sec. 5.1.4's decomposition): L dF.n/dU R = diag(u n - c, u n,
+    u n + c) for n = +1 and -1, the Jacobian by central differences."""
+    rng = np.random.default_rng(6)
+    for _ in range(6):
+        rho, u, p = rng.uniform(0.2, 2.0), rng.uniform(-1, 1), rng.uniform(0.1, 2.0)
+        U = np.array([rho, rho * u, p / (GAMMA - 1.0) + 0.5 * rho * u * u])
+        for sgn in (1.0, -1.0):
+            n = np.array([sgn])
+            J = np.empty((3, 3))
+            for k in range(3):
+                h = 1e-6 * max(1.0, abs(U[k]))
+                e = np.zeros(3)
+                e[k] = h
+                J[:, k] = (O.euler_normal_flux(U + e, n, GAMMA) - O.euler_normal_flux(U - e, n, GAMMA)) / (2 * h)
+            R, L = O.euler_char_basis(U, n, GAMMA)
+            c = math.sqrt(GAMMA * p / rho)
+            assert np.allclose(L @ J @ R, np.diag([u * sgn - c, u * sgn, u * sgn + c]), atol=1e-6)
+
+
+def test_characteristic_equals_componentwise_in_1d_for_data_independent_weights():
+    """As in 2-D: with data-independent weights the characteristic and
+    componentwise 1-D residuals agree to rounding (shock-tube data)."""
+    nodes = np.linspace(0.0, 1.0, 25)
+    mesh = synth.line_mesh(nodes)
+    U = synth.shock_tube_initial(mesh, x0=0.43)
+    a = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0, pde=O.EULER, eps=1e14, min_rows=5)
+    b = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0, pde=O.EULER, eps=1e14, min_rows=5,
+                  characteristic=True)
+    La, Lb = O.residual(a, U), O.residual(b, U)
+    assert np.max(np.abs(La - Lb)) <= 1e-10 * np.max(np.abs(La))
