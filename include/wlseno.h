@@ -125,9 +125,10 @@ typedef struct {
  *             pairs of FP32 numbers, about 48 bits -- for the scalar
  *             equations, whose FP64 results are hi + lo exactly).
  * gamma:      WLSENO_EULER only: ratio of specific heats (e.g. 1.4).
- * characteristic: WLSENO_EULER only, 0 or 1: reconstruct characteristic-wise
- *             (the characteristic decomposition of Sec. 5.1.4 and Sec. 5.2.4,
- *             per facet on triangles): for facet f of cell i the stencil
+ * characteristic: WLSENO_EULER only (1-D and 2-D meshes), 0 or 1: reconstruct
+ *             characteristic-wise (the characteristic decomposition of
+ *             Sec. 5.1.4 and Sec. 5.2.4, per facet on segments and
+ *             triangles): for facet f of cell i the stencil
  *             averages are projected onto the eigenvectors of the Jacobian of
  *             F(U).n_f at the mean of the averages of i and its neighbour
  *             across f, each field gets its own weights and least-squares
@@ -156,7 +157,7 @@ typedef struct {
  *
  * WLSENO_EULER (1-D, 2-D, 3-D): n_comp = dim + 2 conserved variables (rho,
  * rho u_1 .. rho u_dim, E), each reconstructed with its own weights
- * (componentwise WLS-ENO; characteristic-wise optional in 2-D); LF alpha
+ * (componentwise WLS-ENO; characteristic-wise optional in 1-D and 2-D); LF alpha
  * per facet = max over its points and sides of |u.n| + c; a cell whose traces
  * give density or pressure <= 1e-12 at a facet point uses its averages at all
  * its facets (counted in wlseno_diagnostics.positivity_fallbacks). */

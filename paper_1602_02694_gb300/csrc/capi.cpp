@@ -496,8 +496,8 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   if (st != WLSENO_OK) return fail(ctx, st, err);
   if (ctx->scheme.pde == WLSENO_EULER && ctx->scheme.n_comp != H.dim + 2)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "Euler needs n_comp = dim + 2 (3, 4 or 5)");
-  if (ctx->scheme.characteristic && H.dim != 2)
-    return fail(ctx, WLSENO_ERR_INVALID_ARG, "characteristic-wise reconstruction is built for 2-D meshes");
+  if (ctx->scheme.characteristic && H.dim > 2)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "characteristic-wise reconstruction is built for 1-D and 2-D meshes");
   if ((H.dim == 1 && H.m != 3 && H.m != 5) || (H.dim == 2 && H.m != 6 && H.m != 10) ||
       (H.dim == 3 && H.m != 10))
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "order p not compiled for this dimension");

@@ -1,6 +1,7 @@
-// Characteristic-wise WLS-ENO reconstruction for the 2-D Euler equations:
-// the characteristic decomposition the paper applies to its Euler runs
-// (Sec. 5.1.4, Sec. 5.2.4), in the per-facet form for triangles.
+// Characteristic-wise WLS-ENO reconstruction for the Euler equations in 1-D
+// and 2-D: the characteristic decomposition the paper applies to its Euler
+// runs (Sec. 5.1.4, Sec. 5.2.4), in the per-facet form for segments and
+// triangles.
 //
 // One thread per (cell i, facet f).  At the mean U* of the averages of i and
 // of its neighbour across f, the Jacobian of F(U).n_f has the eigenvalues
@@ -18,8 +19,13 @@
 // R: u(x_q) = ubar_i + R dw(x_q).  The eigenvector set for -n is that for n
 // up to order and sign, which leave each field's reconstruction unchanged, so
 // both cells of a facet use the facet's stored (lower-indexed cell's) normal.
-// Output: facet values [4][N][3*2], the layout of the componentwise path.
+// In 1-D (n = +-1) the shear wave is absent: R has the columns
+//   (1, u - c n, H - c u n), (1, u, u^2/2), (1, u + c n, H + c u n)
+// and L the first, second and fourth rows above without their v entries.
+// Output: facet values [d+2][N][(d+1)*nq], the layout of the componentwise
+// path.
 #include <cmath>
+#include <type_traits>
 
 #include "k_recon_tpc.cuh"
 #include "monomials.cuh"
@@ -35,12 +41,63 @@ __device__ __forceinline__ const float* csr_moments<float>(const DeviceMesh& dm)
 template <>
 __device__ __forceinline__ const double* csr_moments<double>(const DeviceMesh& dm) { return dm.A64; }
 
-template <typename T, int M>
+// The basis of the facet with normal n at the state us (d + 2 components).
+template <int DIM>
+__device__ __forceinline__ void char_basis(const double (&us)[DIM + 2], const double* n, double gamma,
+                                           double (&Ld)[DIM + 2][DIM + 2], double (&Rd)[DIM + 2][DIM + 2]) {
+  constexpr int C = DIM + 2;
+  const double rho = us[0];
+  double vel[DIM], ke = 0.0, un = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    vel[a] = us[1 + a] / rho;
+    ke += 0.5 * vel[a] * vel[a];
+    un += vel[a] * n[a];
+  }
+  const double p = (gamma - 1.0) * (us[C - 1] - rho * ke);
+  const double cs = sqrt(gamma * p / rho);
+  const double H = (us[C - 1] + p) / rho;
+  const double b1 = (gamma - 1.0) / (cs * cs), b2 = ke * b1;
+  if constexpr (DIM == 1) {
+    const double u = vel[0], nx = n[0];
+    const double L1[3][3] = {{0.5 * (b2 + un / cs), 0.5 * (-b1 * u - nx / cs), 0.5 * b1},
+                             {1.0 - b2, b1 * u, -b1},
+                             {0.5 * (b2 - un / cs), 0.5 * (-b1 * u + nx / cs), 0.5 * b1}};
+    const double R1[3][3] = {{1.0, 1.0, 1.0}, {u - cs * nx, u, u + cs * nx}, {H - cs * un, ke, H + cs * un}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        Ld[a][b] = L1[a][b];
+        Rd[a][b] = R1[a][b];
+      }
+  } else {
+    const double u = vel[0], v = vel[1], nx = n[0], ny = n[1];
+    const double ut = -u * ny + v * nx;
+    const double L2[4][4] = {{0.5 * (b2 + un / cs), 0.5 * (-b1 * u - nx / cs), 0.5 * (-b1 * v - ny / cs), 0.5 * b1},
+                             {1.0 - b2, b1 * u, b1 * v, -b1},
+                             {-ut, -ny, nx, 0.0},
+                             {0.5 * (b2 - un / cs), 0.5 * (-b1 * u + nx / cs), 0.5 * (-b1 * v + ny / cs), 0.5 * b1}};
+    const double R2[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                             {u - cs * nx, u, -ny, u + cs * nx},
+                             {v - cs * ny, v, nx, v + cs * ny},
+                             {H - cs * un, ke, ut, H + cs * un}};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        Ld[a][b] = L2[a][b];
+        Rd[a][b] = R2[a][b];
+      }
+  }
+}
+
+template <typename T, int DIM, int M>
 __global__ void __launch_bounds__(128)
 euler_char_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
                   double* __restrict__ fvals, unsigned long long* __restrict__ counters,
                   T flag_threshold) {
-  constexpr int DIM = 2, NF = 3, NQ = 2, NP = NF * NQ, C = 4;
+  constexpr int NF = DIM + 1, NQ = nq_of(DIM), NP = NF * NQ, C = DIM + 2;
   const int64_t N = dm.N;
   const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (tid >= N * NF) return;
@@ -57,22 +114,8 @@ euler_char_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ uba
   }
   // eigenvectors at U* in the direction of the facet's stored normal
   const double* g = dm.fgeo + (i * NF + f) * 4;
-  const double nx = g[0], ny = g[1];
-  const double rho = us[0], u = us[1] / rho, v = us[2] / rho;
-  const double ke = 0.5 * (u * u + v * v);
-  const double p = (gamma - 1.0) * (us[3] - rho * ke);
-  const double cs = sqrt(gamma * p / rho);
-  const double H = (us[3] + p) / rho;
-  const double un = u * nx + v * ny, ut = -u * ny + v * nx;
-  const double b1 = (gamma - 1.0) / (cs * cs), b2 = ke * b1;
-  const double Ld[C][C] = {{0.5 * (b2 + un / cs), 0.5 * (-b1 * u - nx / cs), 0.5 * (-b1 * v - ny / cs), 0.5 * b1},
-                           {1.0 - b2, b1 * u, b1 * v, -b1},
-                           {-ut, -ny, nx, 0.0},
-                           {0.5 * (b2 - un / cs), 0.5 * (-b1 * u + nx / cs), 0.5 * (-b1 * v + ny / cs), 0.5 * b1}};
-  const double Rd[C][C] = {{1.0, 1.0, 0.0, 1.0},
-                           {u - cs * nx, u, -ny, u + cs * nx},
-                           {v - cs * ny, v, nx, v + cs * ny},
-                           {H - cs * un, ke, ut, H + cs * un}};
+  double Ld[C][C], Rd[C][C];
+  char_basis<DIM>(us, g, gamma, Ld, Rd);
   T Lt[C][C];
 #pragma unroll
   for (int a = 0; a < C; ++a)
@@ -88,7 +131,9 @@ euler_char_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ uba
   const T* P = tpc_points<T>(dm) + (i * NP + f * NQ) * DIM;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const T y[DIM] = {P[q * DIM], P[q * DIM + 1]};
+    T y[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) y[a] = P[q * DIM + a];
     eval_monomials<T, DIM, M>(y, mono[q]);
   }
   T dw[NQ][C];
@@ -155,22 +200,24 @@ euler_char_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ uba
 cudaError_t launch_euler_char(const DeviceMesh& dm, const SchemeParams& sp, int precision,
                               const double* ubar, double* fvals, unsigned long long* counters,
                               cudaStream_t s) {
-  if (dm.dim != 2 || (dm.m != 6 && dm.m != 10)) return cudaErrorInvalidValue;
   const int threads = 128;
-  const unsigned blocks = static_cast<unsigned>((dm.N * 3 + threads - 1) / threads);
+  const unsigned blocks = static_cast<unsigned>((dm.N * (dm.dim + 1) + threads - 1) / threads);
   const bool f32 = precision == WLSENO_FP32_BULK;
   const double flag = f32 ? sp.kappa_flag : 1e6;
-  if (dm.m == 6) {
+  auto launch = [&](auto D, auto Mc) {
+    constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
     if (f32)
-      euler_char_kernel<float, 6><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters, static_cast<float>(flag));
+      euler_char_kernel<float, DD, MM><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters,
+                                                                  static_cast<float>(flag));
     else
-      euler_char_kernel<double, 6><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters, flag);
-  } else {
-    if (f32)
-      euler_char_kernel<float, 10><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters, static_cast<float>(flag));
-    else
-      euler_char_kernel<double, 10><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters, flag);
-  }
+      euler_char_kernel<double, DD, MM><<<blocks, threads, 0, s>>>(dm, sp, ubar, fvals, counters, flag);
+  };
+  using std::integral_constant;
+  if (dm.dim == 1 && dm.m == 3) launch(integral_constant<int, 1>{}, integral_constant<int, 3>{});
+  else if (dm.dim == 1 && dm.m == 5) launch(integral_constant<int, 1>{}, integral_constant<int, 5>{});
+  else if (dm.dim == 2 && dm.m == 6) launch(integral_constant<int, 2>{}, integral_constant<int, 6>{});
+  else if (dm.dim == 2 && dm.m == 10) launch(integral_constant<int, 2>{}, integral_constant<int, 10>{});
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
