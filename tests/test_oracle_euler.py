@@ -7,6 +7,7 @@ must approach their exact time derivative at the truncation order."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import wlseno_oracle as O
 from paper_1602_02694_gb300 import synth
@@ -202,3 +203,29 @@ def test_characteristic_equals_componentwise_in_1d_for_data_independent_weights(
                   characteristic=True)
     La, Lb = O.residual(a, U), O.residual(b, U)
     assert np.max(np.abs(La - Lb)) <= 1e-10 * np.max(np.abs(La))
+
+
+@pytest.mark.parametrize("dim", [1, 3])
+def test_constant_state_and_conservation_1d_3d(dim):
+    """As in 2-D: a constant state has a zero residual and random states
+    conserve every component over a periodic mesh (segments, tetrahedra)."""
+    if dim == 1:
+        mesh = synth.periodic_line_mesh(20, jitter=0.2, seed=7)
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0, pde=O.EULER, min_rows=5)
+    else:
+        mesh = synth.tet_mesh(3, seed=7)
+        prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0 / 3.0, pde=O.EULER, min_rows=15)
+    C = dim + 2
+    rng = np.random.default_rng(5)
+
+    def state(rho, vel, p):
+        return np.concatenate([[rho], rho * np.asarray(vel), [p / (GAMMA - 1) + 0.5 * rho * float(np.dot(vel, vel))]])
+
+    U = np.repeat(state(0.8, rng.uniform(-0.3, 0.3, dim), 0.9)[:, None], prob.N, axis=1)
+    assert np.max(np.abs(O.residual(prob, U))) < 1e-10
+    U = np.stack([state(rng.uniform(0.5, 1.5), rng.uniform(-0.5, 0.5, dim), rng.uniform(0.5, 1.5))
+                  for _ in range(prob.N)], axis=1)
+    L = O.residual(prob, U)
+    vol = prob.geo.volume
+    for c in range(C):
+        assert abs(np.sum(vol * L[c])) < 1e-13 * np.sum(vol * np.abs(L[c]))

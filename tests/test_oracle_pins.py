@@ -525,6 +525,42 @@ def test_balanced_stencil_selection_invariants():
         assert abs(plus - minus) <= 1 + abs(face_plus - face_minus), (plus, minus)
 
 
+def test_balanced_stencil_selection_invariants_3d():
+    """The same invariants on tetrahedra (the paper's motivating case: nearly
+    one-sided 3-D neighbourhoods)."""
+    mesh = synth.tet_mesh(4, seed=15)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0 / 3.0, pde=O.BURGERS, min_rows=15)
+    rng = np.random.default_rng(9)
+    for i in rng.choice(prob.N, 10, replace=False):
+        i = int(i)
+        d = np.zeros(prob.m)
+        g = rng.normal(size=3)
+        d[1:4] = g
+        S = O.balanced_stencil(prob, i, d)
+        n = len(prob.stencils[i])
+        assert S[0] == i and len(S) == n and len(set(S)) == len(S)
+        assert set(prob.face_nbrs[i]) <= set(S)
+        side = {j: float(np.dot(O.min_image(prob.geo.centroid[j] - prob.geo.centroid[i], prob.period), g)) > 0
+                for j in S[1:]}
+        plus = sum(side.values())
+        face_plus = sum(side[j] for j in prob.face_nbrs[i])
+        face_minus = len(prob.face_nbrs[i]) - face_plus
+        assert abs(plus - (len(S) - 1 - plus)) <= 1 + abs(face_plus - face_minus), (plus, len(S))
+        # on each side the chosen cells (beyond the facet neighbours) come
+        # before every candidate left out, by (squared distance, index)
+        steps = ["vertex"] * (int(math.ceil(prob.ring - 1e-9)) + 1)
+        cands = O.k_ring(i, steps, prob.nbr) - {i}
+        dx = {j: O.min_image(prob.geo.centroid[j] - prob.geo.centroid[i], prob.period) for j in cands}
+        key = {j: (float(np.dot(dx[j], dx[j])), j) for j in cands}
+        plus_side = {j: float(np.dot(dx[j], g)) > 0 for j in cands}
+        face = set(int(j) for j in prob.face_nbrs[i])
+        for sd in (True, False):
+            mine = [key[j] for j in S[1:] if plus_side[j] == sd and j not in face]
+            others = [key[j] for j in cands - set(S) if plus_side[j] == sd]
+            if mine and others:
+                assert max(mine) < min(others), (i, sd)
+
+
 def test_balanced_stencil_of_a_symmetric_1d_stencil_is_itself():
     """On a uniform 1-D grid the k-ring is already balanced about the
     centroid: the re-selection returns the same stencil for either sign of
