@@ -54,7 +54,8 @@ TRAFFIC_PER_LAUNCH = {("fp32_bulk", 0): 244.78e6 + 4.41e6, ("fp32_bulk", 1): 93.
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000,
+                    help="timed steps (default 1000: ~0.3 s, so that the 200 ms clock samples fall inside)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wlseno", choices=["wlseno", "reference"])
     ap.add_argument("--n", type=int, default=N_SIDE, help="squares per side (default 256)")
@@ -103,14 +104,18 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id=None):
+    def __init__(self, gpu_id=None, cmd=None):
         self.rows = []
+        self.times = []
         self.proc = None
         self.gpu_id = gpu_id
+        self.cmd = cmd
+        self.window = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
-        if self.gpu_id:
+        cmd = self.cmd or ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                           "-lms", "200"]
+        if self.gpu_id and not self.cmd:
             cmd += ["-i", self.gpu_id]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
@@ -125,6 +130,12 @@ class ClockSampler:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
                 self.rows.append(parts)
+                self.times.append(time.time())
+
+    def mark(self, t_begin, t_end):
+        """The wall-clock span of the timed region: stop() keeps the samples
+        read within it (plus one sampling interval), when there are any."""
+        self.window = (t_begin, t_end + 0.2)
 
     def stop(self):
         if self.proc is None:
@@ -136,17 +147,24 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        rows = self.rows
+        inside = rows
+        if self.window:
+            inside = [r for r, t in zip(self.rows, self.times) if self.window[0] <= t <= self.window[1]]
+            if inside:
+                rows = inside
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         reasons = set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for r in self.rows:
+        for r in rows:
             for k, name in enumerate(names):
                 if r[5 + k].lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(rows),
+                "samples_in_timed_region": len(inside) if self.window else None}
 
 
 # ----------------------------------------------------------------------------
@@ -330,10 +348,14 @@ def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    t_begin = time.time()
     ms = timed_steps(torch, ctx, u, steps, stream, flush)
     torch.cuda.synchronize(dev)
+    t_end = time.time()
     if dist:
         dist.barrier()
+    if sampler:
+        sampler.mark(t_begin, t_end)
     clocks = sampler.stop() if sampler else None
     del flush
     launches = ctx.diagnostics()["kernel_launches"] - launches0
@@ -566,7 +588,8 @@ def main():
             "moments_modes": modes,
             "refined_cells_per_stage": r32["flagged_per_stage"],
             "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
-                       "reasons": clocks.get("reasons", [])},
+                       "reasons": clocks.get("reasons", []),
+                       "samples_in_timed_region": clocks.get("samples_in_timed_region")},
             "peaks": {"source": "MEASURED_PEAKS.json" if not peaks.get("fallback") else "fallback",
                       "hbm_gbs": peaks.get("hbm_gbs")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
