@@ -285,7 +285,8 @@ def test_fp32_bulk_refinement_reaches_fp64_accuracy(dev):
 def test_full_size_sampled_parity(dev):
     """The benchmark workload itself (131,072 cells, p = 4, 2-ring, Burgers):
     FP64 coefficients and residual at sampled cells, FP32-bulk residual at the
-    same cells, and exact conservation of one full RK3 step in both modes."""
+    same cells (stored rows, and the bench's rows formed on the fly), and
+    exact conservation of one full RK3 step in every mode."""
     mesh = synth.tri_mesh(256, jitter=0.2, seed=1)
     ubar = synth.burgers_2d_initial(mesh)
     prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
@@ -293,10 +294,12 @@ def test_full_size_sampled_parity(dev):
     cells = sorted(set(rng.choice(prob.N, 24, replace=False).tolist()) | {0, prob.N - 1})
     u = torch.tensor(ubar, device=dev)
     res = {}
-    for precision, kflag in (("fp64", 1e3), ("fp32_bulk", 1e3), ("fp32_all", 1e-30), ("fp32_none", 1e30)):
+    # fp32_otf: the bench's own variant (moment rows formed on the fly)
+    for precision, kflag in (("fp64", 1e3), ("fp32_bulk", 1e3), ("fp32_all", 1e-30), ("fp32_none", 1e30),
+                             ("fp32_otf", 1e3)):
         ctx = Context(pde="burgers", precision=precision[:4] + ("_bulk" if precision != "fp64" else ""),
                       kappa_flag=kflag)
-        ctx.build_stencils(mesh, order_p=4, ring=2.0)
+        ctx.build_stencils(mesh, order_p=4, ring=2.0, moments_mode=1 if precision == "fp32_otf" else 0)
         ctx.precompute_moments()
         coef = torch.empty(prob.N * 10, dtype=torch.float64, device=dev)
         ctx.reconstruct(u, coef)
@@ -319,6 +322,8 @@ def test_full_size_sampled_parity(dev):
     # FP32-bulk: one FP64-residual refinement sweep recovers near-FP64 coefficients
     assert worst["fp32_all"] <= 1e-8 and worst["fp32_all"] <= 0.1 * worst["fp32_none"], worst
     assert worst["fp32_bulk"] <= worst["fp32_none"] * 1.0000001, worst
+    cmax = max(1.0, max(float(np.max(np.abs(c))) for c in coeffs.values()))
+    assert worst["fp32_otf"] <= 1e-3 * cmax, worst
     # residual at the sampled cells from their facets
     need = set(cells)
     for i in cells:
@@ -339,6 +344,7 @@ def test_full_size_sampled_parity(dev):
         scale = max(scale, abs(Li))
         assert abs(res["fp64"][1][i] - Li) <= TOL64 * max(1.0, abs(Li)), i
         assert abs(res["fp32_bulk"][1][i] - Li) <= 1e-5 * max(1.0, abs(Li)), i
+        assert abs(res["fp32_otf"][1][i] - Li) <= 1e-4 * max(1.0, abs(Li)), i
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
