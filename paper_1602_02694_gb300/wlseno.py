@@ -152,7 +152,14 @@ def _stream_of(*arrays):
 
 
 class Context:
-    """One wlseno_ctx: a scheme, the meshes' stencils and moments on one GPU."""
+    """One wlseno_ctx: a scheme, the meshes' stencils and moments on one GPU.
+
+    The keyword arguments fill wlseno_scheme: pde ("advection", "burgers",
+    "euler"), precision ("fp64" or "fp32_bulk"), n_comp (default 1, or 4 for
+    Euler; 3 and 5 for 1-D and 3-D Euler), characteristic (Euler in 1-D and
+    2-D), balanced and balance_margin (the balanced-stencil re-selection of
+    scalar equations), eps, alpha_c, rank_tol, kappa_flag, gamma, velocity.
+    Raises WlsenoError with the library's status and message."""
 
     def __init__(self, device: int = 0, pde="advection", velocity=(1.0, 1.0, 0.0), eps=1e-2,
                  alpha_c=1.5, rank_tol=1e-10, kappa_flag=1e3, precision="fp64", n_comp=None,
@@ -205,7 +212,10 @@ class Context:
     def build_stencils(self, meshes, order_p, ring, radius_cut=0.0, min_rows=0,
                        lanes_per_cell=0, rows_per_lane=0, moments_mode=0):
         """wlseno_build_stencils over one mesh or a list of meshes (objects with
-        .vertices [nv][d] float64, .cells [nc][d+1] int64 and .period [d])."""
+        .vertices [nv][d] float64, .cells [nc][d+1] int64 and .period [d]).
+        lanes_per_cell, rows_per_lane: kernel shape ((0, 0): the default);
+        moments_mode: FP32-bulk thread-per-cell only, 0 stored moment rows,
+        1 rows formed on the fly.  Returns the context's info dict."""
         if not isinstance(meshes, (list, tuple)):
             meshes = [meshes]
         arr = (wlseno_mesh * len(meshes))()
