@@ -75,3 +75,37 @@ def test_balanced_option_is_validated_before_any_cuda_call(lib):
             setattr(sch, k, v)
         h = ctypes.c_void_p()
         assert lib.wlseno_create(ctypes.byref(h), 0, ctypes.byref(sch)) == -1, change
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field
+    offsets (compiled and printed by the host C compiler)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"wlseno_mesh": W.wlseno_mesh, "wlseno_stencil_opts": W.wlseno_stencil_opts,
+               "wlseno_scheme": W.wlseno_scheme, "wlseno_info": W.wlseno_info,
+               "wlseno_diagnostics": W.wlseno_diagnostics}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "wlseno.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        parts = line.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
