@@ -109,3 +109,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_kernel_kind_and_status_tables_match_the_header():
+    text = open(HEADER).read()
+    n_kinds = int(re.search(r"WLSENO_N_KERNEL_KINDS\s*=\s*(\d+)", text).group(1))
+    assert len(W.KERNEL_KINDS) == n_kinds
+    kinds = dict((m.group(1).lower(), int(m.group(2)))
+                 for m in re.finditer(r"WLSENO_KERNEL_([A-Z]+)\s*=\s*(\d+)", text))
+    for k, name in enumerate(W.KERNEL_KINDS):
+        assert kinds[name] == k, name
+    assert int(re.search(r"WLSENO_EULER\s*=\s*(\d+)", text).group(1)) == W.EULER
+    assert int(re.search(r"WLSENO_FP32_BULK\s*=\s*(\d+)", text).group(1)) == W.FP32_BULK
