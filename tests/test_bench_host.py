@@ -1,0 +1,46 @@
+"""Host-side pieces of bench.py on the CPU: the oracle baseline's patch
+sub-meshes reproduce the whole mesh's oracle results for the patch cells
+bit for bit, and the algorithmic byte and flop counts follow their
+formulas for the bench workload."""
+import os
+import sys
+
+import numpy as np
+
+from oracle import wlseno_oracle as O
+from paper_1602_02694_gb300 import synth
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_patch_submesh_reproduces_the_whole_mesh_bitwise():
+    n, patch, pad = 24, 6, 6
+    mesh = synth.tri_mesh(n, jitter=0.2, seed=1)
+    u = synth.burgers_2d_initial(mesh)
+    i0 = j0 = 9
+    sub, local, glob = bench.patch_submesh(mesh, i0, j0, patch=patch, pad=pad)
+    whole = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.BURGERS)
+    part = O.Problem(sub.vertices, sub.cells, sub.period, p=4, ring=2.0, pde=O.BURGERS)
+    us = u[glob]
+    for c in local:
+        g = int(glob[c])
+        assert [int(glob[k]) for k in part.stencils[c]] == list(whole.stencils[g])
+        a = part.reconstruct_cell(us, c)[0]
+        b = whole.reconstruct_cell(u, g)[0]
+        assert np.array_equal(a, b), c
+        for f in range(3):
+            ca, fa = part.sib[c, f]
+            cb, fb = whole.sib[g, f]
+            assert int(glob[ca]) == cb and fa == fb
+
+
+def test_algorithmic_counts_of_the_bench_workload():
+    n, m, npts, dim = 37, 10, 6, 2
+    stored = bench.algorithmic_bytes_per_cell(n, m, npts, dim, 4)
+    fly = bench.algorithmic_bytes_per_cell(n, m, npts, dim, 4, on_the_fly=True)
+    tail = 4 * n + 8 + 8 + 4 * (dim + 1) + npts * dim * 4 + 8 * npts
+    assert stored == n * m * 4 + tail
+    assert fly == n * dim * 4 + (m - 1 - dim) * 4 + tail
+    assert fly < stored / 2.5
+    assert 13_000 < bench.algorithmic_flops_per_cell(n, m, npts) < 16_000
