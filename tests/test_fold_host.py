@@ -1,0 +1,81 @@
+"""The library's square-root-free Givens fold (csrc/k_recon_tpc.cuh, the
+thread-per-cell least-squares solver, FP64) compiled as host C++ and
+checked against library least squares: random weighted problems of the
+bench's shape (37 x 10) and of a square one give numpy's solution, and the
+conditioning estimate sqrt(qmax/qmin) is at most the condition number of
+the column-scaled weighted matrix W A S (Sec. 3.3.2), the bound the flag
+threshold relies on."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1602_02694_gb300", "csrc")
+M = 10
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cuda_inc = None
+    for cand in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if cand and os.path.exists(os.path.join(cand, "include", "cuda_runtime.h")):
+            cuda_inc = os.path.join(cand, "include")
+            break
+    if cxx is None or cuda_inc is None:
+        pytest.skip("needs a C++ compiler and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("fold") / "fold_probe")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-w", "-ffp-contract=off", os.path.join(ROOT, "tests", "fold_probe.cpp"),
+                    "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", cuda_inc, "-o", exe], check=True)
+    return exe
+
+
+def solve(probe, problems):
+    lines = []
+    for w, A, b in problems:
+        lines.append(str(len(w)))
+        for t in range(len(w)):
+            lines.append(" ".join(repr(float(v)) for v in [w[t], *A[t], b[t]]))
+    out = subprocess.run([probe], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                         check=True).stdout.split("\n")
+    res = []
+    for k in range(len(problems)):
+        x = np.array([float(v) for v in out[2 * k].split()[1:]])
+        qmax, qmin = (float(v) for v in out[2 * k + 1].split()[1:])
+        res.append((x, qmax, qmin))
+    return res
+
+
+def test_fold_solves_weighted_least_squares(probe):
+    rng = np.random.default_rng(3)
+    problems = []
+    for n in (37, 37, 37, 10, 19):
+        A = rng.normal(size=(n, M)) * np.exp(rng.uniform(-2, 2, M))[None, :]  # uneven column scales
+        w = np.exp(rng.uniform(-4, 0, n))                                     # weights over 4 decades
+        b = rng.normal(size=n)
+        problems.append((w, A, b))
+    for (w, A, b), (x, qmax, qmin) in zip(problems, solve(probe, problems)):
+        WA = w[:, None] * A
+        want = np.linalg.lstsq(WA, w * b, rcond=None)[0]
+        S = 1.0 / np.linalg.norm(WA, axis=0)
+        kappa = np.linalg.cond(WA * S[None, :])
+        assert np.max(np.abs(x - want)) <= 1e-9 * kappa * max(1.0, np.max(np.abs(want)))
+        assert np.sqrt(qmax / qmin) <= kappa * (1 + 1e-9)
+
+
+def test_zero_weight_rows_leave_the_solution_unchanged(probe):
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(20, M))
+    b = rng.normal(size=20)
+    w = np.ones(20)
+    w0 = w.copy()
+    w0[5:9] = 0.0
+    (x_all, _, _), (x_zero, _, _) = solve(probe, [(w, A, b), (w0, A, b)])
+    keep = np.ones(20, dtype=bool)
+    keep[5:9] = False
+    want = np.linalg.lstsq(A[keep], b[keep], rcond=None)[0]
+    assert np.max(np.abs(x_zero - want)) <= 1e-10 * max(1.0, np.max(np.abs(want)))
+    assert not np.allclose(x_all, x_zero)
