@@ -80,3 +80,13 @@ def test_double_float_sums_and_products(probe):
         # normalised: hi is the float nearest hi + lo
         assert float(np.float32(hi + lo)) == hi or lo == 0.0
     assert worst <= 8 * 2.0 ** -48, worst
+
+
+def test_exact_cancellation_and_zero(probe):
+    cases = [("add", (1.5, 2.0 ** -30), (-1.5, -(2.0 ** -30))), ("mul", (0.0, 0.0), (3.0, 1e-9)),
+             ("add", (0.0, 0.0), (0.0, 0.0))]
+    text = "\n".join(f"{op} {x[0].hex()} {x[1].hex()} {y[0].hex()} {y[1].hex()}" for op, x, y in cases)
+    out = subprocess.run([probe], input=text + "\n", capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in out[:3]:
+        hi, lo = (float.fromhex(t) for t in line.split())
+        assert hi == 0.0 and lo == 0.0

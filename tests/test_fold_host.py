@@ -5,6 +5,7 @@ bench's shape (37 x 10) and of a square one give numpy's solution, and the
 conditioning estimate sqrt(qmax/qmin) is at most the condition number of
 the column-scaled weighted matrix W A S (Sec. 3.3.2), the bound the flag
 threshold relies on."""
+import math
 import os
 import shutil
 import subprocess
@@ -79,3 +80,17 @@ def test_zero_weight_rows_leave_the_solution_unchanged(probe):
     want = np.linalg.lstsq(A[keep], b[keep], rcond=None)[0]
     assert np.max(np.abs(x_zero - want)) <= 1e-10 * max(1.0, np.max(np.abs(want)))
     assert not np.allclose(x_all, x_zero)
+
+
+def test_rank_deficient_system_is_flagged(probe):
+    """Two equal columns: the conditioning estimate blows up (the cell would
+    go to the pivoted path), while a well-conditioned copy stays small."""
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(37, M))
+    B = A.copy()
+    B[:, 7] = B[:, 3]
+    w = np.ones(37)
+    b = rng.normal(size=37)
+    (_, q1, q0), (_, p1, p0) = solve(probe, [(w, A, b), (w, B, b)])
+    assert math.sqrt(q1 / q0) < 1e2
+    assert not (p1 <= 1e12 * p0)  # beyond any flag threshold (1e6 squared)
