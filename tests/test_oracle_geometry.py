@@ -1,0 +1,166 @@
+"""Pins of the oracle's cell geometry and of the wave speeds in its CFL rule
+(Sec. 4.2.1 leaves the time step on unstructured meshes open; the reading
+is dt = CFL * min_i r_i / lambda_max with r_i = d|tau_i|/|d tau_i| the
+inradius of cell i and lambda_max the largest characteristic speed).
+
+Checked against textbook constructions that share no formula with the
+oracle: volumes by Heron's formula and the Cayley-Menger determinant (edge
+lengths only), inradii as the distance from the incentre (the vertices
+weighted by the opposite facet's measure) to a facet's line or plane, wave
+speeds as the largest |d(F.n)/du| (scalar equations) or the spectral radius
+of the finite-difference Jacobian of F.n (Euler) over sampled directions."""
+import itertools
+import math
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from oracle import wlseno_oracle as O
+from paper_1602_02694_gb300 import synth
+
+
+def heron(A, B, C):
+    a, b, c = np.linalg.norm(B - C), np.linalg.norm(C - A), np.linalg.norm(A - B)
+    s = 0.5 * (a + b + c)
+    return math.sqrt(max(s * (s - a) * (s - b) * (s - c), 0.0))
+
+
+def cayley_menger_volume(X):
+    D = np.ones((5, 5))
+    D[0, 0] = 0.0
+    for a in range(4):
+        for b in range(4):
+            D[a + 1, b + 1] = float(np.sum((X[a] - X[b]) ** 2))
+    return math.sqrt(max(np.linalg.det(D) / 288.0, 0.0))
+
+
+def triangle_inradius(A, B, C):
+    """Distance from the incentre to each side (all three returned)."""
+    a, b, c = np.linalg.norm(B - C), np.linalg.norm(C - A), np.linalg.norm(A - B)
+    I = (a * A + b * B + c * C) / (a + b + c)
+
+    def dist(P, Q):
+        e = Q - P
+        w = I - P
+        return abs(e[0] * w[1] - e[1] * w[0]) / np.linalg.norm(e)
+    return dist(B, C), dist(C, A), dist(A, B)
+
+
+def tet_inradius(X):
+    """Distance from the insphere centre to each of the four face planes."""
+    areas, normals = [], []
+    for k in range(4):
+        P = [X[j] for j in range(4) if j != k]
+        n = np.cross(P[1] - P[0], P[2] - P[0])
+        areas.append(0.5 * np.linalg.norm(n))
+        normals.append((P[0], n / np.linalg.norm(n)))
+    I = sum(areas[k] * X[k] for k in range(4)) / sum(areas)
+    return tuple(abs(float(np.dot(I - P0, n))) for P0, n in normals)
+
+
+def test_triangle_volumes_and_inradii_are_textbook():
+    mesh = synth.tri_mesh(6, seed=2)
+    geo = O.geometry(mesh.vertices, mesh.cells, mesh.period)
+    for c in range(mesh.cells.shape[0]):
+        A, B, C = geo.coords[c]
+        assert abs(geo.volume[c] - heron(A, B, C)) <= 1e-13
+        r = triangle_inradius(A, B, C)
+        assert max(r) - min(r) <= 1e-13
+        assert abs(geo.inradius[c] - r[0]) <= 1e-13
+        assert np.allclose(geo.centroid[c], (A + B + C) / 3.0, rtol=0, atol=1e-15)
+    # the periodic cells tile the unit square
+    assert abs(np.sum(geo.volume) - 1.0) <= 1e-12
+
+
+def test_tetrahedron_volumes_and_inradii_are_textbook():
+    mesh = synth.tet_mesh(3, seed=15)
+    geo = O.geometry(mesh.vertices, mesh.cells, mesh.period)
+    for c in range(mesh.cells.shape[0]):
+        X = geo.coords[c]
+        assert abs(geo.volume[c] - cayley_menger_volume(X)) <= 1e-12
+        r = tet_inradius(X)
+        assert max(r) - min(r) <= 1e-13
+        assert abs(geo.inradius[c] - r[0]) <= 1e-13
+    assert abs(np.sum(geo.volume) - 1.0) <= 1e-12
+
+
+def test_interval_inradius_is_half_its_length():
+    mesh = synth.periodic_line_mesh(16, jitter=0.3, seed=4)
+    geo = O.geometry(mesh.vertices, mesh.cells, mesh.period)
+    lengths = np.array([abs(x[1, 0] - x[0, 0]) for x in geo.coords])
+    assert np.allclose(geo.volume, lengths, rtol=0, atol=1e-15)
+    assert np.allclose(geo.inradius, 0.5 * lengths, rtol=0, atol=1e-15)
+
+
+def directions(dim):
+    """Unit vectors: every normalised nonzero integer vector in [-3, 3]^dim."""
+    out = []
+    for v in itertools.product(range(-3, 4), repeat=dim):
+        v = np.array(v, dtype=float)
+        if np.any(v):
+            out.append(v / np.linalg.norm(v))
+    return out
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_burgers_speed_is_the_largest_flux_derivative(dim):
+    prob = SimpleNamespace(pde=O.BURGERS, dim=dim, velocity=None)
+    rng = np.random.default_rng(dim)
+    ubar = rng.uniform(-2.0, 2.0, 50)
+    best = 0.0
+    for u in ubar:
+        for n in directions(dim):
+            eps = 1e-5
+            deriv = (np.dot(O.physical_flux(prob, u + eps), n) - np.dot(O.physical_flux(prob, u - eps), n)) / (2 * eps)
+            assert abs(O.normal_speed(prob, u, n) - abs(deriv)) <= 1e-8
+            best = max(best, abs(deriv))
+    lam = O.max_wave_speed(prob, ubar)
+    assert best <= lam * (1 + 1e-9)
+    assert abs(best - lam) <= 1e-8 * lam  # attained at n = (1, .., 1)/sqrt(d)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_advection_speed_is_the_largest_normal_velocity(dim):
+    vel = np.array([1.0, 0.5, 0.25][:dim])
+    prob = SimpleNamespace(pde=O.ADVECTION, dim=dim, velocity=vel)
+    lam = O.max_wave_speed(prob, np.zeros(3))
+    speeds = [abs(float(np.dot(vel, n))) for n in directions(dim)] + [abs(float(np.dot(vel, vel / np.linalg.norm(vel))))]
+    assert max(speeds) <= lam * (1 + 1e-12)
+    assert abs(max(speeds) - lam) <= 1e-12
+
+
+def euler_jacobian(U, n, gamma):
+    J = np.zeros((len(U), len(U)))
+    for k in range(len(U)):
+        e = np.zeros(len(U))
+        e[k] = 1e-6 * max(1.0, abs(U[k]))
+        J[:, k] = (O.euler_normal_flux(U + e, n, gamma) - O.euler_normal_flux(U - e, n, gamma)) / (2 * e[k])
+    return J
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_euler_speed_is_the_spectral_radius_of_the_flux_jacobian(dim):
+    gamma = 1.4
+    rng = np.random.default_rng(10 + dim)
+    states = []
+    for _ in range(6):
+        rho = rng.uniform(0.5, 2.0)
+        v = rng.uniform(-1.0, 1.0, dim)
+        p = rng.uniform(0.5, 2.0)
+        states.append(np.concatenate([[rho], rho * v, [p / (gamma - 1) + 0.5 * rho * v @ v]]))
+    for U in states:
+        for n in directions(dim)[::3] if dim > 1 else [np.array([1.0]), np.array([-1.0])]:
+            rad = float(np.max(np.abs(np.linalg.eigvals(euler_jacobian(U, n, gamma)))))
+            assert abs(O.euler_wave_speed(U, n, gamma) - rad) <= 1e-6 * rad
+    ubar = np.stack(states, axis=1)
+    prob = SimpleNamespace(pde=O.EULER, dim=dim, gamma=gamma, velocity=None)
+    lam = O.max_wave_speed(prob, ubar)
+    best = 0.0
+    for U in states:
+        v = U[1:-1] / U[0]
+        n = v / np.linalg.norm(v)
+        for m in directions(dim) + [n]:
+            best = max(best, O.euler_wave_speed(U, m, gamma))
+    assert best <= lam * (1 + 1e-12)
+    assert abs(best - lam) <= 1e-12 * lam
