@@ -164,3 +164,55 @@ def test_euler_speed_is_the_spectral_radius_of_the_flux_jacobian(dim):
             best = max(best, O.euler_wave_speed(U, m, gamma))
     assert best <= lam * (1 + 1e-12)
     assert abs(best - lam) <= 1e-12 * lam
+
+
+def test_segment_rule_is_two_point_gauss():
+    """Reading R9 in 2-D: exact for degree 3 along an edge (the mean of t^k
+    over [0, 1] is 1/(k+1)), not for degree 4."""
+    F = np.array([[0.3, -0.2], [1.1, 0.4]])
+    pts, w = O.facet_rule(F)
+    assert abs(np.sum(w) - 1.0) <= 1e-15
+    t = (pts[:, 0] - F[0, 0]) / (F[1, 0] - F[0, 0])
+    for k in range(4):
+        assert abs(float(np.dot(w, t ** k)) - 1.0 / (k + 1)) <= 1e-15
+    assert abs(float(np.dot(w, t ** 4)) - 0.2) > 1e-3
+
+
+def test_triangle_rule_is_exact_for_degree_two():
+    """Reading R9 in 3-D: the mean of l1^a l2^b l3^c over a triangle is
+    2 a! b! c! / (a+b+c+2)!; exact for a+b+c <= 2, not for 3."""
+    F = np.array([[0.1, 0.0, 0.2], [0.9, 0.3, -0.1], [0.2, 0.8, 0.5]])
+    pts, w = O.facet_rule(F)
+    T = np.column_stack([F[1] - F[0], F[2] - F[0]])
+    lam12 = np.linalg.lstsq(T, (pts - F[0]).T, rcond=None)[0]
+    lam = np.vstack([1.0 - lam12.sum(axis=0), lam12])
+    for a, b, c in itertools.product(range(4), repeat=3):
+        deg = a + b + c
+        if deg > 3:
+            continue
+        exact = 2.0 * math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(deg + 2)
+        got = float(np.dot(w, lam[0] ** a * lam[1] ** b * lam[2] ** c))
+        if deg <= 2:
+            assert abs(got - exact) <= 1e-15, (a, b, c)
+    assert abs(float(np.dot(w, lam[0] ** 3)) - 2.0 * 6 / math.factorial(5)) > 1e-3
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_outward_normals_close_every_cell(dim):
+    """Unit normals, orthogonal to their facet, pointing away from the
+    opposite vertex, and sum_f |F_f| n_f = 0 (the divergence theorem for a
+    constant field)."""
+    mesh = {1: lambda: synth.periodic_line_mesh(8, jitter=0.3, seed=2),
+            2: lambda: synth.tri_mesh(5, seed=6), 3: lambda: synth.tet_mesh(3, seed=8)}[dim]()
+    geo = O.geometry(mesh.vertices, mesh.cells, mesh.period)
+    for X in geo.coords:
+        total = np.zeros(dim)
+        for f in range(dim + 1):
+            n = O.outward_normal(X, f)
+            F = np.delete(X, f, axis=0)
+            assert abs(np.linalg.norm(n) - 1.0) <= 1e-14
+            for e in F[1:] - F[0]:
+                assert abs(float(np.dot(n, e))) <= 1e-13
+            assert float(np.dot(F[0] - X[f], n)) > 0.0
+            total += O.facet_measure(F) * n
+        assert np.max(np.abs(total)) <= 1e-13
