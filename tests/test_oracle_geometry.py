@@ -216,3 +216,38 @@ def test_outward_normals_close_every_cell(dim):
             assert float(np.dot(F[0] - X[f], n)) > 0.0
             total += O.facet_measure(F) * n
         assert np.max(np.abs(total)) <= 1e-13
+
+
+@pytest.mark.parametrize("make,n_boundary", [
+    (lambda: synth.tri_mesh(5, seed=6), 0),
+    (lambda: synth.tri_mesh(5, periodic=False, seed=6), 20),
+    (lambda: synth.tet_mesh(3, seed=8), 0),
+    (lambda: synth.tet_mesh(3, periodic=False, seed=8), 6 * 2 * 9),
+    (lambda: synth.periodic_line_mesh(7, jitter=0.2, seed=1), 0),
+])
+def test_half_facet_siblings_by_brute_force(make, n_boundary):
+    """The sibling of half-facet (c, f) (the facet opposite local vertex f)
+    is the one other half-facet with the same vertex set, found by comparing
+    every pair; boundary facets have none.  The facet list then holds each
+    interior facet once and each boundary facet once."""
+    mesh = make()
+    cells = mesh.cells
+    N, dp1 = cells.shape
+    keys = {}
+    for c in range(N):
+        for f in range(dp1):
+            keys.setdefault(frozenset(int(v) for k, v in enumerate(cells[c]) if k != f), []).append((c, f))
+    assert all(len(v) <= 2 for v in keys.values())
+    sib = O.sibling_half_facets(cells)
+    boundary = 0
+    for group in keys.values():
+        if len(group) == 1:
+            c, f = group[0]
+            assert tuple(sib[c, f]) == (-1, -1)
+            boundary += 1
+        else:
+            (a, fa), (b, fb) = group
+            assert tuple(sib[a, fa]) == (b, fb) and tuple(sib[b, fb]) == (a, fa)
+    assert boundary == n_boundary
+    prob = SimpleNamespace(N=N, dim=dp1 - 1, sib=sib)
+    assert len(O.facets(prob)) == (N * dp1 + boundary) // 2
