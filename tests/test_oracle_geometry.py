@@ -251,3 +251,27 @@ def test_half_facet_siblings_by_brute_force(make, n_boundary):
     assert boundary == n_boundary
     prob = SimpleNamespace(N=N, dim=dp1 - 1, sib=sib)
     assert len(O.facets(prob)) == (N * dp1 + boundary) // 2
+
+
+def test_radius_cut_stencils_by_brute_force():
+    """Reading R12's 3-D stencil: the 2/3-ring (the cells sharing an edge
+    with the centre) plus the cells sharing a vertex with it whose centroid
+    lies within 0.95 h_i, found here by comparing vertex sets directly."""
+    mesh = synth.tet_mesh(4, seed=5)
+    cells = mesh.cells
+    geo = O.geometry(mesh.vertices, cells, mesh.period)
+    stencils, _ = O.build_stencils(cells, 2.0 / 3.0, 3, radius_cut=0.95, centroid=geo.centroid, h=geo.h,
+                                   period=mesh.period)
+    sets = [set(int(v) for v in c) for c in cells]
+    sizes = []
+    for i in range(cells.shape[0]):
+        want = {j for j in range(cells.shape[0]) if len(sets[i] & sets[j]) >= 2}
+        for j in range(cells.shape[0]):
+            if sets[i] & sets[j] and j not in want:
+                dx = geo.centroid[j] - geo.centroid[i]
+                dx -= np.round(dx / mesh.period) * mesh.period
+                if np.linalg.norm(dx) <= 0.95 * geo.h[i]:
+                    want.add(j)
+        assert stencils[i][0] == i and stencils[i][1:] == sorted(want - {i})
+        sizes.append(len(want))
+    assert 29 <= min(sizes) and max(sizes) <= 52
