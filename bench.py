@@ -203,47 +203,96 @@ def patch_submesh(mesh, i0, j0, patch=PATCH, pad=PATCH_PAD):
     return sub, local, np.array(glob)
 
 
-def _oracle_patch_worker(task):
-    """One process: repeated RK stages of the oracle on one patch for
-    `seconds`; returns (cell-stage updates, elapsed).  Each timed stage
-    reconstructs the patch cells and their facet neighbours, integrates the
-    LF flux over every facet of the patch cells and updates the patch.  The
-    moment matrices are built before the clock starts (the GPU path
-    precomputes them too)."""
-    mesh, u0, i0, j0, seconds = task
-    from oracle import wlseno_oracle as O
-    sub, cells, glob = patch_submesh(mesh, i0, j0)
-    prob = O.Problem(sub.vertices, sub.cells, sub.period, p=P_ORDER, ring=RING, pde=O.BURGERS)
-    cellset = set(cells)
-    need = set(cells)
-    for c in cells:
-        need.update(prob.face_nbrs[c])
-    facets = set()
-    for c in cells:
-        for f in range(3):
-            c2, f2 = prob.sib[c, f]
-            facets.add((c, f, int(c2)) if (c2 < 0 or c < c2) else (int(c2), int(f2), c))
-    for c in need:
-        prob.A(c)
-    u = np.array(u0, dtype=np.float64)[glob]
-    dt = 1e-5
-    done = 0
-    t0 = time.perf_counter()
-    while True:
-        coeffs = {c: prob.reconstruct_cell(u, c)[0] for c in need}
-        acc = {c: 0.0 for c in cells}
-        for L, fL, R in facets:
-            g = O.facet_flux(prob, coeffs, L, fL, R)
-            if L in cellset:
-                acc[L] += g
-            if R in cellset:
-                acc[R] -= g
+class _PatchSweep:
+    """RK stages of the oracle on one patch, advanced a given number of
+    cell-stages at a time.  A sweep is one stage: the facet neighbours outside
+    the patch are reconstructed when it begins, then the patch cells in
+    order; each facet's LF flux is integrated as soon as both of its cells
+    are reconstructed, and the patch is updated when the sweep ends, so any
+    split of a sweep into steps does exactly one stage's work.  The moment
+    matrices are built before any timing (the GPU path precomputes them
+    too)."""
+
+    def __init__(self, mesh, u0, i0, j0, patch=None, pad=None):
+        from oracle import wlseno_oracle as O
+        self.O = O
+        sub, cells, glob = patch_submesh(mesh, i0, j0, patch=PATCH if patch is None else patch,
+                                         pad=PATCH_PAD if pad is None else pad)
+        self.prob = prob = O.Problem(sub.vertices, sub.cells, sub.period, p=P_ORDER, ring=RING, pde=O.BURGERS)
+        self.cells = list(cells)
+        cellset = set(cells)
+        need = set(cells)
         for c in cells:
-            u[c] -= dt * acc[c] / prob.geo.volume[c]
-        done += len(cells)
-        if time.perf_counter() - t0 >= seconds:
-            break
-    return done, time.perf_counter() - t0
+            need.update(prob.face_nbrs[c])
+        self.halo = sorted(need - cellset)
+        self.facets_of = {}
+        for c in cells:
+            fs = []
+            for f in range(3):
+                c2, f2 = prob.sib[c, f]
+                fs.append((c, f, int(c2)) if (c2 < 0 or c < c2) else (int(c2), int(f2), c))
+            self.facets_of[c] = fs
+        self.cellset = cellset
+        for c in need:
+            prob.A(c)
+        self.u = np.array(u0, dtype=np.float64)[glob]
+        self.dt = 1e-5
+        self.cursor = 0
+
+    def advance(self, k):
+        """k cell-stages (reconstruction, flux share and update of k patch
+        cells, continuing the current sweep and starting new ones)."""
+        prob, O = self.prob, self.O
+        for _ in range(k):
+            if self.cursor == 0:
+                self.coeffs = {h: prob.reconstruct_cell(self.u, h)[0] for h in self.halo}
+                self.acc = {c: 0.0 for c in self.cells}
+            c = self.cells[self.cursor]
+            self.coeffs[c] = prob.reconstruct_cell(self.u, c)[0]
+            for L, fL, R in self.facets_of[c]:
+                other = R if L == c else L
+                if other >= 0 and other not in self.coeffs:
+                    continue
+                g = O.facet_flux(prob, self.coeffs, L, fL, R)
+                if L in self.cellset:
+                    self.acc[L] += g
+                if R in self.cellset:
+                    self.acc[R] -= g
+            self.cursor += 1
+            if self.cursor == len(self.cells):
+                for c2 in self.cells:
+                    self.u[c2] -= self.dt * self.acc[c2] / prob.geo.volume[c2]
+                self.cursor = 0
+
+
+def _oracle_patch_worker(task):
+    """One process on one patch.  Without a step count: whole stages until
+    `seconds` have passed.  With one: one untimed stage to size the steps,
+    `warmup` untimed steps, then `steps` timed steps of k cell-stages each,
+    k chosen so that the timed steps take about `seconds`.  Returns
+    (cell-stage updates timed, elapsed, k)."""
+    mesh, u0, i0, j0, seconds, warmup, steps = task
+    sweep = _PatchSweep(mesh, u0, i0, j0)
+    n = len(sweep.cells)
+    if steps is None:
+        done = 0
+        t0 = time.perf_counter()
+        while True:
+            sweep.advance(n)
+            done += n
+            if time.perf_counter() - t0 >= seconds:
+                break
+        return done, time.perf_counter() - t0, n
+    t0 = time.perf_counter()
+    sweep.advance(n)
+    per_cell = (time.perf_counter() - t0) / n
+    k = max(1, int(round(seconds / (steps * per_cell))))
+    for _ in range(warmup):
+        sweep.advance(k)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sweep.advance(k)
+    return k * steps, time.perf_counter() - t0, k
 
 
 def host_cores():
@@ -253,26 +302,35 @@ def host_cores():
         return max(1, os.cpu_count() or 1)
 
 
-def oracle_cpu_rate(mesh, u0, seconds, workers=1):
+def oracle_cpu_rate(mesh, u0, seconds, workers=1, warmup=0, steps=None):
     """Oracle cell-stage updates/s on 20x20-square patches of the workload's
     mesh (800 cells each), one process per host core used (patches spread
-    over the mesh; processes started with spawn, after the GPU work).
-    Returns (rate, description, cores)."""
+    over the mesh; processes started with spawn, after the GPU work); with
+    `steps`, each process runs `warmup` untimed and `steps` timed steps of
+    a fixed number of cell-stages.  Returns (rate, description, cores)."""
     n = mesh.n
     starts = [((n // 2 - PATCH // 2) + 37 * w) % n for w in range(workers)]
-    tasks = [(mesh, u0, s, (s + 11 * w) % n, seconds) for w, s in enumerate(starts)]
+    tasks = [(mesh, u0, s, (s + 11 * w) % n, seconds, warmup, steps) for w, s in enumerate(starts)]
     if workers == 1:
         results = [_oracle_patch_worker(tasks[0])]
     else:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(workers) as pool:
             results = pool.map(_oracle_patch_worker, tasks)
-    rate = sum(d / el for d, el in results)
-    stages = sum(d for d, _ in results) // (2 * PATCH * PATCH)
-    desc = (f"oracle (numpy/scipy, FP64) in {workers} process(es), one per core: repeated RK stages on "
-            f"{PATCH}x{PATCH}-square patches ({2 * PATCH * PATCH} cells each, their facet neighbours "
-            f"reconstructed too) of the same mesh, {stages} patch-stages in {seconds:.0f} s; moments "
-            f"built before timing; rate summed over the concurrent processes")
+    rate = sum(d / el for d, el, _ in results)
+    cells = 2 * PATCH * PATCH
+    stages = sum(d for d, _, _ in results) / cells
+    head = (f"oracle (numpy/scipy, FP64) in {workers} process(es), one per core, each on a "
+            f"{PATCH}x{PATCH}-square patch ({cells} cells, their facet neighbours reconstructed at the "
+            f"start of every stage) of the same mesh; ")
+    if steps is None:
+        body = f"repeated whole RK stages, {stages:.0f} patch-stages in {seconds:.0f} s; "
+    else:
+        ks = sorted({k for _, _, k in results})
+        body = (f"after one untimed sizing stage and {warmup} untimed warm-up steps, {steps} timed steps of "
+                f"{'/'.join(str(k) for k in ks)} cell-stages per process ({stages:.1f} patch-stages in all, "
+                f"{max(el for _, el, _ in results):.1f} s); ")
+    desc = head + body + "moments built before timing; rate summed over the concurrent processes"
     return rate, desc, workers
 
 
@@ -510,7 +568,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        rate, desc, cores = oracle_cpu_rate(mesh, u0, max(2.0, args.cpu_seconds), host_cores())
+        rate, desc, cores = oracle_cpu_rate(mesh, u0, max(2.0, args.cpu_seconds), host_cores(),
+                                            warmup=args.warmup, steps=max(1, args.steps))
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": n_cells * 3 / rate * 1e3, "higher_is_better": True, "scaling": "weak",

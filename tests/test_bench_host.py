@@ -44,3 +44,36 @@ def test_algorithmic_counts_of_the_bench_workload():
     assert fly == n * dim * 4 + (m - 1 - dim) * 4 + tail
     assert fly < stored / 2.5
     assert 13_000 < bench.algorithmic_flops_per_cell(n, m, npts) < 16_000
+
+
+def test_patch_sweep_is_one_stage_however_it_is_split():
+    """The baseline's patch sweep: one sweep updates every patch cell by
+    dt times the oracle's residual of the sub-mesh, and splitting sweeps into
+    steps of any size changes nothing."""
+    n, patch, pad = 24, 6, 6
+    mesh = synth.tri_mesh(n, jitter=0.2, seed=1)
+    u0 = synth.burgers_2d_initial(mesh)
+    a = bench._PatchSweep(mesh, u0, 9, 9, patch=patch, pad=pad)
+    b = bench._PatchSweep(mesh, u0, 9, 9, patch=patch, pad=pad)
+    cells = a.cells
+    start = a.u.copy()
+    a.advance(len(cells))
+    for k in (5, 30, len(cells) - 35):
+        b.advance(k)
+    assert np.array_equal(a.u, b.u)
+    L = O.residual(a.prob, start)
+    want = start[cells] + a.dt * L[cells]
+    assert np.max(np.abs(a.u[cells] - want)) <= 1e-15 * np.max(np.abs(start))
+    a.advance(len(cells) + 17)
+    for k in (1, len(cells) + 16):
+        b.advance(k)
+    assert np.array_equal(a.u, b.u) and a.cursor == b.cursor == 17
+
+
+def test_reference_arm_runs_the_requested_steps(monkeypatch):
+    monkeypatch.setattr(bench, "PATCH", 4)
+    monkeypatch.setattr(bench, "PATCH_PAD", 6)
+    mesh = synth.tri_mesh(24, jitter=0.2, seed=1)
+    u0 = synth.burgers_2d_initial(mesh)
+    done, elapsed, k = bench._oracle_patch_worker((mesh, u0, 9, 9, 0.2, 2, 3))
+    assert k >= 1 and done == 3 * k and elapsed > 0.0
