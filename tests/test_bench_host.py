@@ -77,3 +77,12 @@ def test_reference_arm_runs_the_requested_steps(monkeypatch):
     u0 = synth.burgers_2d_initial(mesh)
     done, elapsed, k = bench._oracle_patch_worker((mesh, u0, 9, 9, 0.2, 2, 3))
     assert k >= 1 and done == 3 * k and elapsed > 0.0
+
+
+def test_cpu_baseline_times_whole_stages(monkeypatch):
+    monkeypatch.setattr(bench, "PATCH", 4)
+    monkeypatch.setattr(bench, "PATCH_PAD", 6)
+    mesh = synth.tri_mesh(24, jitter=0.2, seed=1)
+    u0 = synth.burgers_2d_initial(mesh)
+    done, elapsed, k = bench._oracle_patch_worker((mesh, u0, 9, 9, 0.05, 0, None))
+    assert k == 2 * 4 * 4 and done % k == 0 and done >= k and elapsed >= 0.05
