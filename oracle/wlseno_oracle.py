@@ -45,7 +45,9 @@ the design notes of the repository):
   * periodic meshes: each stencil cell is taken at its minimum-image copy.
   * transmissive boundary facets use u+ = u-.
 
-Parity of every function here is pinned in tests/test_oracle_pins.py.
+Parity of every function here is pinned: the scheme in tests/test_oracle_pins.py,
+Euler in tests/test_oracle_euler.py, the geometry, facet rules, adjacency,
+radius-cut stencils and CFL wave speeds in tests/test_oracle_geometry.py.
 """
 from __future__ import annotations
 
