@@ -275,3 +275,38 @@ def test_radius_cut_stencils_by_brute_force():
         assert stencils[i][0] == i and stencils[i][1:] == sorted(want - {i})
         sizes.append(len(want))
     assert 29 <= min(sizes) and max(sizes) <= 52
+
+
+def test_short_stencils_grow_by_whole_facet_layers():
+    """Reading R13 on a transmissive mesh: a stencil shorter than min_rows is
+    the smallest L such that the cells within L facet-adjacency steps of the
+    ring have at least min_rows cells (graph distances by scipy's BFS over a
+    facet graph built from raw vertex sets)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+
+    mesh = synth.tri_mesh(7, periodic=False, seed=12)
+    cells = mesh.cells
+    N = cells.shape[0]
+    sets = [set(int(v) for v in c) for c in cells]
+    rows, cols = [], []
+    for a in range(N):
+        for b in range(N):
+            if a != b and len(sets[a] & sets[b]) == 2:
+                rows.append(a)
+                cols.append(b)
+    D = shortest_path(csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(N, N)), unweighted=True)
+    for min_rows in (9, 15, 22):
+        stencils, _ = O.build_stencils(cells, 1.0, 2, min_rows=min_rows)
+        plain, _ = O.build_stencils(cells, 1.0, 2)
+        grown = 0
+        for i in range(N):
+            ring = plain[i]
+            dist = np.min(D[ring], axis=0)
+            L = 0
+            while np.sum(dist <= L) < min_rows and np.sum(dist <= L) < np.sum(np.isfinite(dist)):
+                L += 1
+            want = sorted(set(np.flatnonzero(dist <= L).tolist()) - {i})
+            assert stencils[i] == [i] + want, (min_rows, i)
+            grown += L > 0
+        assert grown > 0
