@@ -143,6 +143,20 @@ def _ptr(x, dtype=np.float64, writable=False):
     return x.ctypes.data, x
 
 
+def _numel(x):
+    return x.numel() if _is_torch(x) else int(x.size)
+
+
+def check_length(x, need, name):
+    """Raise ValueError when array x (torch or numpy, may be None) holds
+    fewer than `need` elements: the library takes plain pointers and would
+    read or write past its end."""
+    if x is None or not (_is_torch(x) or isinstance(x, np.ndarray)):
+        return  # not an array: the pointer marshalling raises TypeError
+    if _numel(x) < need:
+        raise ValueError(f"{name} has {_numel(x)} elements; this context needs {need}")
+
+
 def _stream_of(*arrays):
     for a in arrays:
         if a is not None and _is_torch(a) and a.is_cuda:
@@ -233,15 +247,31 @@ class Context:
             arr[k].period = p.ctypes.data
         opts = wlseno_stencil_opts(order_p, float(ring), float(radius_cut), min_rows,
                                    lanes_per_cell, rows_per_lane, moments_mode)
+        self._info = None
         self._check(self.lib.wlseno_build_stencils(self.h, arr, len(meshes), ctypes.byref(opts)),
                     "wlseno_build_stencils")
         self._info = self.info()
         return self._info
 
+    def _lengths(self, per_cell, **arrays):
+        """Check the arrays against the built context's sizes: n_comp x
+        n_cells x per_cell[name] elements each (before any build the library
+        itself reports the missing state)."""
+        inf = getattr(self, "_info", None)
+        if not inf:
+            return
+        base = inf["n_comp"] * inf["n_cells"]
+        for name, x in arrays.items():
+            check_length(x, base * per_cell.get(name, 1), name)
+
     def precompute_moments(self, stream=None):
         self._check(self.lib.wlseno_precompute_moments(self.h, stream), "wlseno_precompute_moments")
 
     def reconstruct(self, ubar, coeffs=None, facet_values=None, stream=None):
+        inf = getattr(self, "_info", None) or {}
+        self._lengths({"coeffs": inf.get("m", 1),
+                       "facet_values": (inf.get("dim", 0) + 1) * inf.get("quad_per_facet", 1)},
+                      ubar=ubar, coeffs=coeffs, facet_values=facet_values)
         pu, _ = _ptr(ubar)
         pc, _ = _ptr(coeffs, writable=True)
         pf, _ = _ptr(facet_values, writable=True)
@@ -249,6 +279,7 @@ class Context:
         self._check(self.lib.wlseno_reconstruct(self.h, pu, pc, pf, s), "wlseno_reconstruct")
 
     def flux_residual(self, ubar, residual, stream=None):
+        self._lengths({}, ubar=ubar, residual=residual)
         pu, _ = _ptr(ubar)
         pr, _ = _ptr(residual, writable=True)
         s = stream if stream is not None else _stream_of(ubar, residual)
@@ -257,6 +288,7 @@ class Context:
     def flux_residual_static(self, ubar, residual, stream=None):
         """wlseno_flux_residual_static: L(ubar) with no device allocation
         (fixed library scratch; device arrays only)."""
+        self._lengths({}, ubar=ubar, residual=residual)
         pu, _ = _ptr(ubar)
         pr, _ = _ptr(residual, writable=True)
         s = stream if stream is not None else _stream_of(ubar, residual)
@@ -265,6 +297,7 @@ class Context:
 
     def rk_step(self, ubar, dt=0.0, cfl=0.0, n_steps=1, want_dt=False, stream=None):
         """TVD-RK3 steps in place; returns the last dt when want_dt."""
+        self._lengths({}, ubar=ubar)
         pu, _ = _ptr(ubar, writable=True)
         out = ctypes.c_double(0.0)
         s = stream if stream is not None else _stream_of(ubar)
@@ -276,6 +309,7 @@ class Context:
     def autotune(self, ubar, reps=5, stream=None):
         """Pick the fastest reconstruction kernel shape on this data;
         returns (lanes_per_cell, rows_per_lane, mean launch microseconds)."""
+        self._lengths({}, ubar=ubar)
         pu, _ = _ptr(ubar)
         best = ctypes.c_double(0.0)
         s = stream if stream is not None else _stream_of(ubar)
@@ -287,9 +321,13 @@ class Context:
     def set_mesh_dt(self, dts):
         """Per-mesh fixed steps, used by rk_step / step_adjoint with dt < 0."""
         a = np.ascontiguousarray(dts, dtype=np.float64)
+        inf = getattr(self, "_info", None)
+        if inf:
+            check_length(a, inf["n_meshes"], "dts")
         self._check(self.lib.wlseno_set_mesh_dt(self.h, a.ctypes.data), "wlseno_set_mesh_dt")
 
     def step_adjoint(self, ubar_n, dt, gbar_next, gbar_n, stream=None):
+        self._lengths({}, ubar_n=ubar_n, gbar_next=gbar_next, gbar_n=gbar_n)
         pu, _ = _ptr(ubar_n)
         pg, _ = _ptr(gbar_next)
         po, _ = _ptr(gbar_n, writable=True)
