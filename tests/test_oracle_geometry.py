@@ -310,3 +310,47 @@ def test_short_stencils_grow_by_whole_facet_layers():
             assert stencils[i] == [i] + want, (min_rows, i)
             grown += L > 0
         assert grown > 0
+
+
+def _rough(mesh, seed):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, mesh.cells.shape[0])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_reconstruction_is_translation_invariant(dim):
+    """Moving a transmissive mesh leaves every h-normalised Taylor
+    coefficient about the centroid unchanged (the method sees only relative
+    positions).  Cells whose scaled system is rank deficient (short stencils
+    at the 3-D boundary) are skipped: which columns their basic solution
+    drops is decided by rounding-level differences of the pivot norms."""
+    mesh = synth.tri_mesh(8, periodic=False, seed=9) if dim == 2 else synth.tet_mesh(3, periodic=False, seed=9)
+    p, ring = (4, 2.0) if dim == 2 else (3, 2.0 / 3.0)
+    u = _rough(mesh, 3)
+    shift = np.array([0.37, -1.2, 2.5])[:dim]
+    a = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=p, ring=ring, pde=O.BURGERS)
+    b = O.Problem(mesh.vertices + shift, mesh.cells, mesh.period, p=p, ring=ring, pde=O.BURGERS)
+    full = 0
+    for i in range(a.N):
+        (da, ra), (db, rb) = a.reconstruct_cell(u, i), b.reconstruct_cell(u, i)
+        if ra < a.m or rb < a.m:
+            continue
+        full += 1
+        assert np.max(np.abs(da - db)) <= 1e-9 * max(1.0, np.max(np.abs(da))), i
+    assert full >= 0.8 * a.N
+
+
+def test_reflection_flips_the_odd_x_coefficients():
+    """x -> -x: the coefficient of (x - x_i)^a (y - y_i)^b changes by (-1)^a,
+    and the advection residual with the mirrored velocity is unchanged."""
+    mesh = synth.tri_mesh(8, periodic=False, seed=10)
+    u = _rough(mesh, 4)
+    mirror = mesh.vertices * np.array([-1.0, 1.0])
+    a = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.ADVECTION,
+                  velocity=(1.0, 0.5, 0.0))
+    b = O.Problem(mirror, mesh.cells, mesh.period, p=4, ring=2.0, pde=O.ADVECTION, velocity=(-1.0, 0.5, 0.0))
+    sign = np.array([(-1.0) ** kap[0] for kap in a.kappas])
+    for i in range(a.N):
+        da, db = a.reconstruct_cell(u, i)[0], b.reconstruct_cell(u, i)[0]
+        assert np.max(np.abs(db - sign * da)) <= 1e-9 * max(1.0, np.max(np.abs(da))), i
+    La, Lb = O.residual(a, u), O.residual(b, u)
+    assert np.max(np.abs(La - Lb)) <= 1e-9 * np.max(np.abs(La))
