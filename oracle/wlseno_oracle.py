@@ -36,6 +36,10 @@ the design notes of the repository):
     unknowns are h-normalised, d_kappa = h_i^|kappa| d^kappa u(x_i).
   * numerical rank r = #{k : |R_kk| > rank_tol * |R_11|}; coefficients of
     dropped columns are 0 (basic solution).
+  * column pivoting: at each step the lowest-index remaining column whose
+    squared trailing norm is within a relative 1e-6 of the largest (after
+    the column scaling all norms are 1, so the paper's rule alone leaves the
+    first pivot to rounding); trailing norms recomputed at every step.
   * facet quadrature: Gauss-Legendre with 2 points per edge in 2-D, the
     degree-2 three-point rule at barycentric (2/3,1/6,1/6) in 3-D.
   * Lax-Friedrichs alpha: |velocity| for advection; per facet the maximum
@@ -356,6 +360,49 @@ def wls_eno_weights(ubar_S, face_mask, h, eps=1e-2, alpha_c=1.5):
     return omega
 
 
+PIVOT_TOL = 1e-6
+
+
+def qr_column_pivoting(B, tau_piv=PIVOT_TOL):
+    """Householder QR with column pivoting, B[:, piv] = Q R (Sec. 3.3.2).
+    Pivot rule (reading R6; the paper does not break ties, and after the
+    column scaling every column has norm 1): at step k the pivot is the
+    lowest-index remaining column whose squared trailing norm is at least
+    (1 - tau_piv) times the largest one, the trailing norms recomputed from
+    the partly reduced matrix at every step.  Returns (R [min(n,m)][m], piv,
+    the Householder vectors v_k with Q_k = I - 2 v v^T / v^T v)."""
+    n, m = B.shape
+    W = np.array(B, dtype=np.float64)
+    piv = list(range(m))
+    vs = []
+    for k in range(min(n, m)):
+        T = W[k:, k:]
+        norms = np.einsum("ij,ij->j", T, T)
+        p = k + int(np.argmax(norms >= (1.0 - tau_piv) * norms.max()))  # first such column
+        if p != k:
+            W[:, [k, p]] = W[:, [p, k]]
+            piv[k], piv[p] = piv[p], piv[k]
+        v = W[k:, k].copy()
+        nrm = math.sqrt(float(norms[p - k]))
+        alpha = -nrm if v[0] >= 0.0 else nrm
+        v[0] -= alpha
+        vtv = float(np.dot(v, v))
+        if vtv > 0.0:
+            T -= v[:, None] * ((2.0 / vtv) * (v @ T))[None, :]
+        vs.append(v)
+    return np.triu(W[:min(n, m)]), piv, vs
+
+
+def apply_qt(vs, y):
+    """Q^T y with the Householder vectors of qr_column_pivoting."""
+    z = np.array(y, dtype=np.float64)
+    for k, v in enumerate(vs):
+        vtv = float(np.dot(v, v))
+        if vtv > 0.0:
+            z[k:] -= (2.0 / vtv) * float(np.dot(v, z[k:])) * v
+    return z
+
+
 def scaled_wls_solve(A, omega, rhs, rank_tol=1e-10):
     """Minimise ||W A S d - W rhs||_2 (Eq. (scaled_WLS)) with W = diag(omega),
     S = diag(1/||column of W A||), by QR with column pivoting
@@ -364,13 +411,13 @@ def scaled_wls_solve(A, omega, rhs, rank_tol=1e-10):
     WA = omega[:, None] * A
     s = 1.0 / np.linalg.norm(WA, axis=0)
     B = WA * s[None, :]
-    Q, R, piv = scipy.linalg.qr(B, mode="economic", pivoting=True)
+    R, piv, vs = qr_column_pivoting(B)
     diag = np.abs(np.diag(R))
     r = int(np.sum(diag > rank_tol * diag[0]))
-    c = Q[:, :r].T @ (omega * rhs)
+    c = apply_qt(vs, omega * rhs)[:r]
     y = scipy.linalg.solve_triangular(R[:r, :r], c, lower=False)
     dvec = np.zeros(A.shape[1])
-    dvec[piv[:r]] = y
+    dvec[np.asarray(piv[:r], dtype=int)] = y
     return s * dvec, r, R
 
 

@@ -635,3 +635,65 @@ def test_moment_rows_are_binomial_shifts_of_own_central_moments():
                                 term *= d[c] ** (kp[c] - al[c]) / math.factorial(kp[c] - al[c])
                             want += term
                     assert abs(A[t, k] - want) <= 1e-11 * max(1.0, abs(want)), (i, j, kp)
+
+
+# ---------------------------------------------------------------------------
+# QR with column pivoting (Sec. 3.3.2) and the pivot rule of reading R6
+# ---------------------------------------------------------------------------
+
+def _q_of(vs, n):
+    """Q from Q^T e_j, column by column."""
+    return np.column_stack([O.apply_qt(vs, e) for e in np.eye(n)]).T
+
+
+@pytest.mark.parametrize("n,m", [(9, 4), (37, 10), (5, 10), (10, 10)])
+def test_qrcp_factors_the_permuted_matrix(n, m):
+    """B[:, piv] = Q R with Q orthogonal and R upper triangular, and the
+    diagonal of R non-increasing up to the pivot window:
+    R_kk^2 >= (1 - 1e-6) R_(k+1)(k+1)^2."""
+    rng = np.random.default_rng(n * m)
+    B = rng.normal(size=(n, m)) * rng.uniform(0.1, 10.0, size=m)
+    R, piv, vs = O.qr_column_pivoting(B)
+    assert sorted(piv) == list(range(m))
+    Q = _q_of(vs, n)
+    k = min(n, m)
+    assert np.max(np.abs(Q.T @ Q - np.eye(n))) <= 1e-14
+    assert np.max(np.abs(Q[:, :k] @ R - B[:, piv])) <= 1e-13 * np.max(np.abs(B))
+    assert np.allclose(R, np.triu(R))
+    d = np.abs(np.diag(R))
+    assert all(d[j] ** 2 >= (1 - 1e-6) * d[j + 1] ** 2 for j in range(k - 1))
+
+
+def test_pivot_rule_takes_the_lowest_index_within_the_window():
+    """Reading R6: equal norms (every column of the scaled system has norm
+    1) pick the lowest index; a squared norm within 1e-6 of the largest
+    counts as a tie, one 1e-5 below does not."""
+    rng = np.random.default_rng(5)
+    B = rng.normal(size=(12, 4))
+    B /= np.linalg.norm(B, axis=0)
+    assert O.qr_column_pivoting(B)[1][0] == 0
+    C = B.copy()
+    C[:, 2] *= math.sqrt(1 + 5e-7)   # the largest, but inside the window
+    assert O.qr_column_pivoting(C)[1][0] == 0
+    C[:, 2] = B[:, 2] * math.sqrt(1 + 1e-5)  # outside the window
+    assert O.qr_column_pivoting(C)[1][0] == 2
+    # the window is relative to the largest squared norm at every step
+    D = np.diag([1.0, 3.0, 2.0, 3.0 * (1 - 4e-7)])
+    assert O.qr_column_pivoting(D)[1] == [1, 3, 2, 0]
+
+
+def test_basic_solution_of_a_short_system():
+    """n < m: rank n, and the basic solution is the exact fit on the first
+    n pivot columns (zero elsewhere), the definition of Sec. 3.3.2 with E
+    restricted to the first r columns."""
+    rng = np.random.default_rng(8)
+    A = rng.normal(size=(6, 10))
+    w = rng.uniform(0.5, 2.0, size=6)
+    b = rng.normal(size=6)
+    v, r, _ = O.scaled_wls_solve(A, w, b)
+    assert r == 6
+    s = 1.0 / np.linalg.norm(w[:, None] * A, axis=0)
+    _, piv, _ = O.qr_column_pivoting(w[:, None] * A * s)
+    keep = piv[:6]
+    assert np.all(v[[c for c in range(10) if c not in keep]] == 0.0)
+    assert np.allclose(A[:, keep] @ v[keep], b, atol=1e-12)
