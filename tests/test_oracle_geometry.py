@@ -353,3 +353,31 @@ def test_reflection_flips_the_odd_x_coefficients():
         assert np.max(np.abs(db - sign * da)) <= 1e-9 * max(1.0, np.max(np.abs(da))), i
     La, Lb = O.residual(a, u), O.residual(b, u)
     assert np.max(np.abs(La - Lb)) <= 1e-9 * np.max(np.abs(La))
+
+
+def test_burgers_facet_flux_is_consistent_monotone_and_antisymmetric():
+    """The facet flux of Eq. (flux) with the per-facet alpha of reading R10
+    on constant traces a (from L) and b (from R): F(a, a) = |f| (a^2/2) sum(n);
+    non-decreasing in a and non-increasing in b (a monotone flux, as a
+    Rusanov flux with alpha >= max |F'(u).n| is); and the same facet seen
+    from R gives minus the flux."""
+    mesh = synth.tri_mesh(4, seed=2)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.BURGERS)
+    rng = np.random.default_rng(12)
+
+    def flux(L, fL, R, a, b):
+        coeffs = {L: np.r_[a, np.zeros(prob.m - 1)], R: np.r_[b, np.zeros(prob.m - 1)]}
+        return O.facet_flux(prob, coeffs, L, fL, R)
+
+    for L, fL, R in O.facets(prob)[:12]:
+        fR = int(prob.sib[L, fL][1])
+        X = prob.geo.coords[L]
+        F = np.delete(X, fL, axis=0)
+        area, n = O.facet_measure(F), O.outward_normal(X, fL)
+        for _ in range(20):
+            a, b = rng.uniform(-2.0, 2.0, 2)
+            assert abs(flux(L, fL, R, a, a) - area * 0.5 * a * a * np.sum(n)) <= 1e-14
+            g = flux(L, fL, R, a, b)
+            assert flux(L, fL, R, a + 1e-3, b) >= g - 1e-14
+            assert flux(L, fL, R, a, b + 1e-3) <= g + 1e-14
+            assert abs(flux(R, fR, L, b, a) + g) <= 1e-14
