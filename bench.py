@@ -1,15 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the WLS-ENO hot path: cell-stage updates per second.
 
-Workload: 2-D Burgers u_t + (u^2/2)_x + (u^2/2)_y = 0 on the periodic unit
-square, 256 x 256 squares split into 131,072 jittered triangles (vertex
-jitter U(-0.2h, 0.2h), seed 1), cubic WLS-ENO reconstruction (p = 4, m = 10)
-on the 2-ring stencil (37 cells), Lax-Friedrichs flux with 2 Gauss points per
-edge, TVD-RK3 at CFL 0.3 with the time step recomputed every step on the
-device, initial data 0.5 + sin(2 pi (x + y)).  One step = one TVD-RK3 step
-(three stages) over all cells; value = cells x 3 x steps / device time.
-The headline is the FP32-bulk path; the plain FP64 GPU path runs the same
-steps from the same state for the speedup and the accuracy comparison.
+Headline workload (the largest of the paper-shaped workloads that fits one
+GPU): 2-D compressible Euler (4 conserved components, gamma = 1.4),
+componentwise WLS-ENO p = 3 (m = 6) on the 1-ring stencil (13 cells; grown
+to 9 rows at least near the boundary), on a 1024 x 1024 jittered "/"-split
+triangulated grid of the unit square (2,097,152 triangles, vertex jitter
+U(-0.2h, 0.2h), seed 1, transmissive boundaries), four-quadrant
+piecewise-constant data around (1/2, 1/2) drawn from seed 3, LF flux with
+alpha = max(|u.n| + c) per facet, TVD-RK3 at CFL 0.3 with the time step
+recomputed on the device every step, the workload's 200 steps timed.  One
+step = one TVD-RK3 step (three stages) over all cells; value = cells x 3 x
+steps / device time.  The headline is the FP32-bulk path; the plain FP64
+GPU path runs the same steps from the same state for the speedup and the
+accuracy comparison.
+
+The other workloads are reported under "configs" (same measurement): 2-D
+advection on 32 x 32 (2,048 cells, FP64 and FP32-bulk), 2-D Burgers on
+256 x 256 (131,072 cells, p = 4 on the 2-ring), 3-D advection on 64^3 Kuhn
+tetrahedra (1,572,864 cells) and the batch of 48 periodic Burgers problems
+(2,149,888 cells in all) with the cost of its hand-written adjoint.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 (N > 1 under torch.distributed.run: independent replicas, one per GPU).
@@ -37,44 +47,50 @@ from paper_1602_02694_gb300.replicas import max_over_ranks, sum_over_ranks  # no
 
 METRIC = "cell-stage updates/sec (WLS-ENO recon+flux) vs plain FP64 GPU, equal accuracy"
 UNIT = "cell-stage updates/s"
-WORKLOAD = ("2-D Burgers, periodic 256x256 jittered triangulated grid (131,072 cells), "
-            "p=4 (m=10), 2-ring stencil (37 cells), LF flux, TVD-RK3 CFL 0.3")
+# the 2-D Burgers workload of the oracle's patch sweep (and of configs["burgers256"])
 N_SIDE, P_ORDER, RING, CFL, JITTER, SEED = 256, 4, 2.0, 0.3, 0.2, 1
-FP32_PEAK_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
-N_SMS = 152
-FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal)
-# DRAM bytes (read + write) of one launch of the main reconstruction kernel
-# on this workload, by (precision, moments mode), from an ncu capture of the
-# same kernel (profiles/recon_tpc_*_burgers256_p4.md); None where no capture
-# of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("fp32_bulk", 0): 244.78e6 + 4.41e6, ("fp32_bulk", 1): 93.38e6 + 2.62e6,
-                      ("fp64", 0): None}
+
+WORKLOADS = {
+    "euler1024": {"desc": "2-D Euler, transmissive 1024x1024 jittered triangulated grid (2,097,152 cells), "
+                          "4 components, p=3 (m=6), 1-ring stencil (13 cells), LF flux, TVD-RK3 CFL 0.3, "
+                          "four-quadrant data", "steps": 200},
+    "burgers256": {"desc": "2-D Burgers, periodic 256x256 jittered triangulated grid (131,072 cells), "
+                           "p=4 (m=10), 2-ring stencil (37 cells), LF flux, TVD-RK3 CFL 0.3", "steps": 300},
+    "advection32": {"desc": "2-D linear advection, periodic 32x32 jittered grid (2,048 cells), p=3, 1-ring, "
+                            "TVD-RK3 CFL 0.4", "steps": 100},
+    "advection3d64": {"desc": "3-D linear advection, periodic 64^3 Kuhn tetrahedra (1,572,864 cells), p=3 (m=10), "
+                              "2/3-ring plus the 1-ring cells within 0.95 h (29-52 cells), TVD-RK3 CFL 0.3",
+                      "steps": 100},
+    "batched48": {"desc": "48 periodic 2-D Burgers problems n in {16,...,256} (2,149,888 cells), p=3, 1-ring, "
+                          "per-problem fixed dt (CFL 0.3 from u0), forward steps and the adjoint",
+                  "steps": 50},
+}
+HEADLINE = "euler1024"
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000,
-                    help="timed steps (default 1000: ~0.3 s, so that the 200 ms clock samples fall inside)")
+    ap.add_argument("--steps", type=int, default=200,
+                    help="timed steps of the headline workload (default 200: the workload's own run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wlseno", choices=["wlseno", "reference"])
-    ap.add_argument("--n", type=int, default=N_SIDE, help="squares per side (default 256)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU work of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="",
+                    help="comma-separated workloads besides the headline (default: all)")
     ap.add_argument("--shape", default="auto",
                     help="reconstruction kernel shape 'lanes,rows' (1,0 = thread per cell); "
                          "default: the autotuner picks the shape and the moments mode")
-    ap.add_argument("--moments", type=int, default=0, choices=[0, 1],
-                    help="with a fixed --shape 1,0: FP32 moment rows stored (0) or formed on the fly (1)")
     return ap.parse_args()
 
 
 def algorithmic_flops_per_cell(n, m, npts):
-    """Floating-point work one cell's reconstruction needs by the algorithm
-    (weights, W A, column scaling, m Householder steps with recomputed
-    trailing norms on the n x (m+1) system, triangular solve, evaluation at
-    the facet points); padding lanes are not counted."""
+    """Floating-point work one cell's reconstruction (one component) needs by
+    the algorithm (weights, W A, column scaling, m Householder steps with
+    recomputed trailing norms on the n x (m+1) system, triangular solve,
+    evaluation at the facet points); padding lanes are not counted."""
     f = 6 * n                       # differences, squares, eps h^2, divide
     f += n * m + 3 * n * m          # W A; column norms and scaling
     for k in range(m):
@@ -89,12 +105,34 @@ def algorithmic_flops_per_cell(n, m, npts):
 
 
 def algorithmic_bytes_per_cell(n, m, npts, dim, a_bytes, on_the_fly=False):
-    """Bytes one cell's reconstruction must move at least once: its stencil
-    rows of A (formed on the fly: each row's offset instead, and the cell's
-    own central moments of degree >= 2), its stencil indices, its own state,
-    h, facet neighbours and points, and its facet values."""
+    """Bytes one cell's reconstruction (one component) must move at least
+    once: its stencil rows of A (formed on the fly: each row's offset
+    instead, and the cell's own central moments of degree >= 2), its stencil
+    indices, its own state, h, facet neighbours and points, and its facet
+    values."""
     rows = n * dim * 4 + (m - 1 - dim) * 4 if on_the_fly else n * m * a_bytes
     return rows + 4 * n + 8 + 8 + 4 * (dim + 1) + npts * dim * a_bytes + 8 * npts
+
+
+def euler_recon_bytes_per_cell(n, m, npts, dim, on_the_fly):
+    """Bytes the all-components FP32-bulk Euler reconstruction must move once
+    per cell: the stencil rows (stored FP32 moments, or offset records and the
+    cell's own moments), the indices, the four components' FP32 pairs, h,
+    facet neighbours and points, the positivity flag and the four components'
+    FP32 trace deviations."""
+    C = dim + 2
+    rows = n * 16 + ((m - 1 - dim + 3) // 4) * 16 if on_the_fly else n * ((m + 1 + 3) // 4) * 16
+    return rows + 4 + 8 * C + 8 + 4 * (dim + 1) + npts * dim * 4 + 1 + 4 * C * npts
+
+
+def flux_bytes_per_cell(dim, npts, comps, euler):
+    """Bytes a flux / RK-stage kernel must move once per cell (each input
+    datum once): the trace deviations and FP32 pairs of the state and of
+    u0 for every component, facet neighbours, facet coefficients (16 bytes
+    each), the 1/|tau| pair, and the FP64 state and pairs written."""
+    nf = dim + 1
+    b = comps * (4 * npts + 8 + 8) + 4 * nf + 16 * nf + 8 + comps * (8 + 8)
+    return b + (1 if euler else 0)
 
 
 class ClockSampler:
@@ -335,6 +373,85 @@ def oracle_cpu_rate(mesh, u0, seconds, workers=1, warmup=0, steps=None):
 
 
 # ----------------------------------------------------------------------------
+# CPU baseline of the Euler workload: the oracle's whole RK3 steps on a
+# transmissive sub-mesh cut from the workload's mesh
+# ----------------------------------------------------------------------------
+
+def _oracle_euler_worker(task):
+    """One process: the oracle's TVD-RK3 steps on a p x p-square transmissive
+    sub-mesh of the Euler workload's grid around (i0, j0).  Without a step
+    count: whole steps until `seconds` have passed.  With one: `warmup`
+    untimed and `steps` timed steps on a window sized (from one untimed
+    sizing step on a small window) so that the timed steps take about
+    `seconds`.  Returns (cell-stage updates timed, elapsed, cells)."""
+    from oracle import wlseno_oracle as O
+    n, seed, i0, j0, seconds, warmup, steps = task
+    mesh = synth.tri_mesh(n, jitter=JITTER, seed=SEED, periodic=False)
+    U0, _ = synth.euler_quadrant_initial(mesh, seed=seed)
+
+    def setup(p):
+        sub, _, glob = patch_submesh(mesh, i0 - p // 2, j0 - p // 2, patch=p, pad=0)
+        prob = O.Problem(sub.vertices, sub.cells, sub.period, p=3, ring=1.0, pde=O.EULER)
+        u = np.array(U0[:, glob])
+        dt = O.cfl_dt(prob, u, 0.3)
+        O.residual(prob, u)  # moments built before the clock
+        return prob, u, dt
+
+    def run(prob, u, dt, k):
+        for _ in range(k):
+            u = O.rk3_step(lambda x: O.residual(prob, x), u, dt)
+        return u
+
+    p = 8
+    if steps is not None:
+        prob, u, dt = setup(p)
+        t0 = time.perf_counter()
+        run(prob, u, dt, 1)
+        per_cell_step = (time.perf_counter() - t0) / prob.N
+        cells = max(8, seconds / (max(1, steps) * per_cell_step))
+        p = max(2, int(round(math.sqrt(cells / 2))))
+    else:
+        p = 12
+    prob, u, dt = setup(p)
+    if steps is None:
+        done, t0 = 0, time.perf_counter()
+        while True:
+            u = run(prob, u, dt, 1)
+            done += 3 * prob.N
+            if time.perf_counter() - t0 >= seconds:
+                break
+        return done, time.perf_counter() - t0, prob.N
+    u = run(prob, u, dt, warmup)
+    t0 = time.perf_counter()
+    run(prob, u, dt, steps)
+    return 3 * prob.N * steps, time.perf_counter() - t0, prob.N
+
+
+def oracle_euler_rate(n, seed, seconds, workers=1, warmup=0, steps=None):
+    """Oracle cell-stage updates/s of the Euler workload, one process per
+    host core used (windows spread over the grid's quadrant corner; started
+    with spawn, after the GPU work).  Returns (rate, description, cores)."""
+    centre = n // 2
+    tasks = [(n, seed, centre + 9 * (w % 4) - 13, centre + 9 * (w // 4) - 13, seconds, warmup, steps)
+             for w in range(workers)]
+    if workers == 1:
+        results = [_oracle_euler_worker(tasks[0])]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            results = pool.map(_oracle_euler_worker, tasks)
+    rate = sum(d / el for d, el, _ in results)
+    cells = sorted({c for _, _, c in results})
+    desc = (f"oracle (numpy/scipy, FP64) in {workers} process(es), one per core, each running whole TVD-RK3 "
+            f"steps (CFL 0.3) of the Euler workload on a transmissive sub-mesh of "
+            f"{'/'.join(str(c) for c in cells)} cells cut from the 1024x1024 grid around its quadrant corner"
+            + (f"; {warmup} untimed warm-up and {steps} timed steps" if steps is not None else
+               f"; whole steps for {seconds:.0f} s")
+            + "; moments built before timing; rate summed over the concurrent processes")
+    return rate, desc, workers
+
+
+# ----------------------------------------------------------------------------
 # GPU measurement
 # ----------------------------------------------------------------------------
 
@@ -346,21 +463,88 @@ def gpu_uuid(torch, dev):
         return None
 
 
-def make_context(precision, mesh, dev_index, shape="auto", moments=0):
-    from paper_1602_02694_gb300.wlseno import Context
-    ctx = Context(dev_index, pde="burgers", precision=precision)
-    lanes, rows = (0, 0) if shape == "auto" else (int(v) for v in shape.split(","))
-    mode = moments if shape != "auto" and precision == "fp32_bulk" else 0
-    ctx.build_stencils(mesh, order_p=P_ORDER, ring=RING, lanes_per_cell=lanes, rows_per_lane=rows,
-                       moments_mode=mode)
-    ctx.autotune_enabled = shape == "auto"
-    return ctx
+def tet_initial(mesh, k=2):
+    c = np.array([0.5, 0.5, 0.5])
+
+    def f(P):
+        d = P - c
+        d -= np.round(d)
+        r2 = np.sum(d * d, axis=1)
+        return np.exp(-50.0 * r2) + (r2 <= 0.15 ** 2)
+
+    return synth.cell_averages(mesh, f, k=k)
+
+
+def batch_meshes():
+    rng = np.random.default_rng(5)
+    sizes = rng.choice(np.arange(16, 257, 8), size=48)
+    meshes = [synth.tri_mesh(int(n), jitter=0.2, seed=100 + k) for k, n in enumerate(sizes)]
+    u0 = [synth.smooth_random_initial(m, seed=200 + k) for k, m in enumerate(meshes)]
+    return meshes, u0
+
+
+class Workload:
+    """A workload's mesh, initial state, scheme and stepping rule."""
+
+    def __init__(self, name):
+        self.name = name
+        self.desc = WORKLOADS[name]["desc"]
+        self.default_steps = WORKLOADS[name]["steps"]
+        self.step_kw = {"cfl": CFL}
+        self.meshes = None
+        if name == "euler1024":
+            self.meshes = synth.tri_mesh(1024, jitter=JITTER, seed=SEED, periodic=False)
+            self.u0, _ = synth.euler_quadrant_initial(self.meshes, seed=3)
+            self.scheme = {"pde": "euler"}
+            self.build = {"order_p": 3, "ring": 1.0}
+        elif name == "burgers256":
+            self.meshes = synth.tri_mesh(N_SIDE, jitter=JITTER, seed=SEED)
+            self.u0 = synth.burgers_2d_initial(self.meshes)
+            self.scheme = {"pde": "burgers"}
+            self.build = {"order_p": P_ORDER, "ring": RING}
+        elif name == "advection32":
+            self.meshes = synth.tri_mesh(32, jitter=JITTER, seed=SEED)
+            self.u0 = synth.advection_2d_initial(self.meshes)
+            self.scheme = {"pde": "advection", "velocity": (1.0, 1.0, 0.0)}
+            self.build = {"order_p": 3, "ring": 1.0}
+            self.step_kw = {"cfl": 0.4}
+        elif name == "advection3d64":
+            self.meshes = synth.tet_mesh(64, jitter=0.15, seed=SEED)
+            self.u0 = tet_initial(self.meshes)
+            self.scheme = {"pde": "advection", "velocity": (1.0, 0.5, 0.25)}
+            self.build = {"order_p": 3, "ring": 2.0 / 3.0, "radius_cut": 0.95}
+        elif name == "batched48":
+            self.meshes, u0s = batch_meshes()
+            self.u0 = np.concatenate(u0s)
+            self.u0_parts = u0s
+            self.scheme = {"pde": "burgers"}
+            self.build = {"order_p": 3, "ring": 1.0}
+            self.step_kw = {"dt": -1.0}
+        self.n_cells = int(self.u0.shape[-1])
+
+    def context(self, precision, dev_index, shape="auto"):
+        from paper_1602_02694_gb300.wlseno import Context
+        ctx = Context(dev_index, precision=precision, **self.scheme)
+        lanes, rows = (0, 0) if shape == "auto" else (int(v) for v in shape.split(","))
+        ctx.build_stencils(self.meshes, lanes_per_cell=lanes, rows_per_lane=rows, **self.build)
+        ctx.autotune_enabled = shape == "auto"
+        return ctx
+
+    def set_mesh_dt(self, ctx):
+        if self.name != "batched48":
+            return
+        inr = ctx.geometry()["inradius"]
+        dts, off = [], 0
+        for m, u in zip(self.meshes, self.u0_parts):
+            dts.append(CFL * float(np.min(inr[off:off + m.n_cells])) / (math.sqrt(2.0) * float(np.max(np.abs(u)))))
+            off += m.n_cells
+        ctx.set_mesh_dt(dts)
 
 
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
 
 
-def timed_steps(torch, ctx, u, steps, stream, flush):
+def timed_steps(torch, ctx, u, steps, stream, flush, step_kw):
     """Exactly `steps` TVD-RK3 steps, each one replay of the captured step
     between its own CUDA-event pair on the launching stream, with an L2 flush
     (a 256 MB write) before each step outside the events; returns the summed
@@ -371,33 +555,34 @@ def timed_steps(torch, ctx, u, steps, stream, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.rk_step(u, cfl=CFL, n_steps=1)  # the captured step (same state, dt rule)
+        ctx.rk_step(u, n_steps=1, **step_kw)  # the captured step (same state, dt rule)
         e1.record(stream)
         pairs.append((e0, e1))
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in pairs)
 
 
-def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
+def run_precision(torch, wl, ctx, steps, warmup, dist, sampler=None):
     """W untimed steps, then exactly `steps` timed TVD-RK3 steps bracketed by
     a barrier and a device synchronisation (L2 flushed before each, outside
-    its events); returns times and the state."""
+    its events), then the same steps again in the library's timing mode for
+    the per-kernel split; returns times, the state and the diagnostics."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
     t_setup = time.perf_counter()
     ctx.precompute_moments()
-    torch.cuda.synchronize(dev)
-    setup_s = time.perf_counter() - t_setup
-    u = torch.tensor(u0, dtype=torch.float64, device=dev)
+    wl.set_mesh_dt(ctx)
+    u = torch.tensor(wl.u0, dtype=torch.float64, device=dev).contiguous()
     if getattr(ctx, "autotune_enabled", True):
         shape = ctx.autotune(u, reps=3)
     else:
         info = ctx.info()
         shape = (info["lanes_per_cell"], info["rows_per_lane"], None)
+    torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t_setup
     # warm-up (two steps at least: they capture the step graph the timed
     # single-step calls replay)
-    ctx.rk_step(u, cfl=CFL, n_steps=max(2, warmup))
+    ctx.rk_step(u, n_steps=max(2, warmup), **wl.step_kw)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
     launches0 = ctx.diagnostics()["kernel_launches"]
@@ -407,7 +592,7 @@ def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
         dist.barrier()
     torch.cuda.synchronize(dev)
     t_begin = time.time()
-    ms = timed_steps(torch, ctx, u, steps, stream, flush)
+    ms = timed_steps(torch, ctx, u, steps, stream, flush, wl.step_kw)
     torch.cuda.synchronize(dev)
     t_end = time.time()
     if dist:
@@ -417,92 +602,97 @@ def run_precision(torch, ctx, u0, steps, warmup, dist, sampler=None):
     clocks = sampler.stop() if sampler else None
     del flush
     launches = ctx.diagnostics()["kernel_launches"] - launches0
-    # kernel split: the same steps again (from a copy of the state) with a
-    # CUDA-event pair around every launch on the launching stream
+    # kernel split: the same number of steps again (from a copy of the state)
+    # with a CUDA-event pair around every launch on the launching stream
     ctx.set_timing(True)
     v = u.clone()
-    ctx.rk_step(v, cfl=CFL, n_steps=steps)
+    ctx.rk_step(v, n_steps=steps, **wl.step_kw)
     torch.cuda.synchronize(dev)
     diag = ctx.diagnostics()
     ctx.set_timing(False)
     del v
     ms = max_over_ranks(ms, dist, dev)  # the job is as slow as its slowest rank
-    stages = max(1, diag["launches_by_kind"]["flux"])  # one flux/RK launch per stage
-    return {"ms": ms, "u": u, "diag": diag, "launches": launches,
-            "clocks": clocks, "setup_s": setup_s, "shape": shape[:2], "info": ctx.info(),
+    stages = 3 * steps
+    return {"ms": ms, "u": u, "diag": diag, "launches": launches, "clocks": clocks, "setup_s": setup_s,
+            "shape": list(shape[:2]), "info": ctx.info(), "stages": stages,
             "flagged_per_stage": diag["flagged_cells"] / stages}
 
 
-def run_moments_mode(torch, mesh, u0, dev_index, mode, steps):
-    """The FP32-bulk thread-per-cell kernel in one moments mode: step time
-    (captured steps, CUDA events) and the main kernel's mean launch time."""
-    ctx = make_context("fp32_bulk", mesh, dev_index, "1,0", mode)
-    ctx.precompute_moments()
-    dev = torch.device("cuda", dev_index)
-    u = torch.tensor(u0, dtype=torch.float64, device=dev)
-    ctx.rk_step(u, cfl=CFL, n_steps=3)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize(dev)
-    ms = timed_steps(torch, ctx, u, steps, torch.cuda.current_stream(dev), flush)
-    del flush
-    ctx.set_timing(True)
-    ctx.rk_step(u, cfl=CFL, n_steps=steps)
-    torch.cuda.synchronize(dev)
-    d = ctx.diagnostics()
-    ctx.set_timing(False)
-    ctx.close()
-    k = d["launches_by_kind"]["reconstruct"]
-    return {"ms_per_step": ms / steps, "main_kernel_us": 1e3 * d["kernel_ms"]["reconstruct"] / max(1, k)}
-
-
-def run_e2e(torch, ctx, u0, steps):
+def run_e2e(torch, wl, ctx, steps):
     """Same metric through the public call with a pinned HOST buffer: every
     step copies the state host->device, runs one TVD-RK3 step and copies the
     state back (both inside the timed region)."""
-    uh = torch.tensor(u0, dtype=torch.float64).pin_memory()
-    ctx.rk_step(uh, cfl=CFL, n_steps=1)  # warm the staging buffers
+    uh = torch.tensor(wl.u0, dtype=torch.float64).contiguous().pin_memory()
+    ctx.rk_step(uh, n_steps=1, **wl.step_kw)  # warm the staging buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        ctx.rk_step(uh, cfl=CFL, n_steps=1)
+        ctx.rk_step(uh, n_steps=1, **wl.step_kw)
     el = time.perf_counter() - t0
     return el, uh.numel() * 8
 
 
-def roofline(info, diag, n_cells, precision, peaks, sm_mhz):
-    """Roofline of the main reconstruction kernel (the dominant kernel): its
-    algorithmic bytes and flops per launch over its average CUDA-event launch
-    time inside the timed steps.  The follow-up kernels on the cells it flags
-    are timed separately (kind "fixup")."""
-    n = info["stencil_nnz"] / n_cells
-    m = info["m"]
-    npts = (info["dim"] + 1) * info["quad_per_facet"]
-    otf = precision == "fp32_bulk" and info.get("moments_mode", 0) == 1
-    launches = diag["launches_by_kind"]["reconstruct"]
-    ms = diag["kernel_ms"]["reconstruct"]
+def kernel_split(diag):
+    return {k: {"launches": diag["launches_by_kind"][k], "ms": diag["kernel_ms"][k]}
+            for k in ("reconstruct", "fixup", "flux", "dt", "adjoint")}
+
+
+def roofline(wl, info, diag, precision, peaks):
+    """Roofline of the dominant kernel kind of the step (the largest summed
+    CUDA-event time in the timing pass): its algorithmic bytes and flops per
+    launch over its average launch time, against the measured HBM copy
+    bandwidth and the measured FP32 / FP64 FMA peak; the larger fraction is
+    the bound.  Reconstruction: `algorithmic_flops_per_cell` per cell and
+    component; flux: `flux_bytes_per_cell`."""
+    kinds = ("reconstruct", "flux", "fixup", "dt")
+    kind = max(kinds, key=lambda k: diag["kernel_ms"][k])
+    launches = diag["launches_by_kind"][kind]
+    ms = diag["kernel_ms"][kind]
     if launches == 0 or ms <= 0:
         return None
+    N = info["n_cells"]
+    dim, m = info["dim"], info["m"]
+    n = info["stencil_nnz"] / N
+    npts = (dim + 1) * info["quad_per_facet"]
+    comps = info["n_comp"]
+    euler = wl.scheme["pde"] == "euler"
+    otf = precision == "fp32_bulk" and info.get("moments_mode", 0) == 1
+    fused = euler and precision == "fp32_bulk" and dim == 2 and info["lanes_per_cell"] == 1
+    per_launch_comps = comps if fused or not euler or kind != "reconstruct" else 1
     dur = ms / launches * 1e-3
-    flops = algorithmic_flops_per_cell(n, m, npts) * n_cells
-    a_bytes = 4 if precision == "fp32_bulk" else 8
-    nbytes = algorithmic_bytes_per_cell(n, m, npts, info["dim"], a_bytes, otf) * n_cells
-    clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    if precision == "fp32_bulk":
-        alu_peak = N_SMS * FP32_PEAK_LANES_PER_SM * 2 * clock / 1e12
+    if kind == "reconstruct":
+        flops = algorithmic_flops_per_cell(n, m, npts) * N * per_launch_comps
+        if fused:
+            nbytes = euler_recon_bytes_per_cell(n, m, npts, dim, otf) * N
+        else:
+            nbytes = algorithmic_bytes_per_cell(n, m, npts, dim, 4 if precision == "fp32_bulk" else 8, otf) * N
     else:
-        alu_peak = FP64_NOMINAL_TFLOPS
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        flops = 0.0
+        nbytes = flux_bytes_per_cell(dim, npts, comps, euler) * N
+    alu_peak = peaks["fp32_tflops"] if precision == "fp32_bulk" else peaks["fp64_tflops"]
+    hbm_peak = peaks["hbm_gbs"]
     alu = flops / dur / 1e12
     hbm = nbytes / dur / 1e9
-    name = f"main reconstruction kernel ({precision}{', moments on the fly' if otf else ''}), per launch"
-    traffic = TRAFFIC_PER_LAUNCH.get((precision, 1 if otf else 0))
+    name = f"{kind} kernel ({precision}{', all components' if fused and kind == 'reconstruct' else ''}" \
+           f"{', moments on the fly' if otf and kind == 'reconstruct' else ''}), per launch"
+    traffic = TRAFFIC_PER_LAUNCH.get((wl.name, precision, kind, otf))
     out_alu = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
-               "frac": alu / alu_peak, "traffic": traffic, "kernel": name,
-               "flops_per_launch": flops, "launch_us": dur * 1e6}
+               "frac": alu / alu_peak if alu_peak else None, "traffic": traffic, "kernel": name,
+               "flops_per_launch": flops, "launch_us": dur * 1e6,
+               "peak_source": "measured FMA-loop peak (wlseno_measure_fma_peak)"}
     out_hbm = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                "frac": hbm / hbm_peak, "traffic": traffic, "kernel": name,
-               "bytes_per_launch": nbytes, "launch_us": dur * 1e6}
-    return (out_alu, out_hbm) if out_alu["frac"] >= out_hbm["frac"] else (out_hbm, out_alu)
+               "bytes_per_launch": nbytes, "launch_us": dur * 1e6,
+               "peak_source": peaks.get("hbm_source")}
+    if flops > 0 and out_alu["frac"] >= out_hbm["frac"]:
+        return out_alu, out_hbm
+    return out_hbm, out_alu
+
+
+# DRAM bytes (read + write) per launch of a workload's dominant kernel from
+# one ncu capture of the current kernel, keyed by (workload, precision,
+# kind, moments on the fly); None where no capture of it exists.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def burgers_exact_averages(mesh, t):
@@ -520,35 +710,115 @@ def burgers_exact_averages(mesh, t):
     return synth.cell_averages(mesh, f, k=4)
 
 
-def accuracy_report(torch, mesh, u0, ctx32, ctx64, horizons=(3, 30)):
-    """Untimed: both paths from u0 at the same fixed dt (CFL 0.3 at t = 0);
-    FP32-bulk vs FP64 and each vs the exact solution after each horizon."""
+def rel_l1(a, b):
+    return float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+
+
+def accuracy_report(torch, wl, ctx32, ctx64, horizons):
+    """Untimed: both precisions from u0 with the workload's step rule;
+    FP32-bulk vs FP64 (relative L1) after each horizon, and for the Burgers
+    workload each against the exact solution."""
     dev = torch.device("cuda", torch.cuda.current_device())
-    rmin = float(np.min(ctx64.geometry()["inradius"]))
-    dt = CFL * rmin / (math.sqrt(2.0) * float(np.max(np.abs(u0))))
-    out = {"dt": dt, "steps": list(horizons), "rel_l1_fp32_bulk_vs_fp64": [],
-           "rel_l1_vs_exact_fp64": [], "rel_l1_vs_exact_fp32_bulk": []}
-    us = {k: torch.tensor(u0, dtype=torch.float64, device=dev) for k in ("32", "64")}
+    out = {"steps": list(horizons), "rel_l1_fp32_bulk_vs_fp64": []}
+    kw = dict(wl.step_kw)
+    if wl.name == "burgers256":
+        rmin = float(np.min(ctx64.geometry()["inradius"]))
+        kw = {"dt": CFL * rmin / (math.sqrt(2.0) * float(np.max(np.abs(wl.u0))))}
+        out["dt"] = kw["dt"]
+        out["rel_l1_vs_exact_fp64"] = []
+        out["rel_l1_vs_exact_fp32_bulk"] = []
+    us = {k: torch.tensor(wl.u0, dtype=torch.float64, device=dev).contiguous() for k in ("32", "64")}
     done = 0
     for h in horizons:
-        ctx32.rk_step(us["32"], dt=dt, n_steps=h - done)
-        ctx64.rk_step(us["64"], dt=dt, n_steps=h - done)
+        ctx32.rk_step(us["32"], n_steps=h - done, **kw)
+        ctx64.rk_step(us["64"], n_steps=h - done, **kw)
         done = h
         a32 = us["32"].cpu().numpy()
         a64 = us["64"].cpu().numpy()
-        ex = burgers_exact_averages(mesh, h * dt)
-        out["rel_l1_fp32_bulk_vs_fp64"].append(float(np.sum(np.abs(a32 - a64)) / np.sum(np.abs(a64))))
-        out["rel_l1_vs_exact_fp64"].append(float(np.sum(np.abs(a64 - ex)) / np.sum(np.abs(ex))))
-        out["rel_l1_vs_exact_fp32_bulk"].append(float(np.sum(np.abs(a32 - ex)) / np.sum(np.abs(ex))))
+        out["rel_l1_fp32_bulk_vs_fp64"].append(rel_l1(a32, a64))
+        if wl.name == "burgers256":
+            ex = burgers_exact_averages(wl.meshes, h * kw["dt"])
+            out["rel_l1_vs_exact_fp64"].append(rel_l1(a64, ex))
+            out["rel_l1_vs_exact_fp32_bulk"].append(rel_l1(a32, ex))
     return out
 
 
-def load_peaks():
+def adjoint_cost(torch, wl, ctx, steps):
+    """Mean time of one wlseno_step_adjoint call (the VJP of one fixed-dt
+    RK3 step with its two inner stages recomputed) over `steps` calls,
+    CUDA events on the launching stream."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    u = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
+    g = torch.ones_like(u)
+    out = torch.empty_like(u)
+    ctx.step_adjoint(u, -1.0, g, out)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ctx.step_adjoint(u, -1.0, g, out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def load_peaks(torch, dev):
+    """HBM from MEASURED_PEAKS.json (else the fallback copy bandwidth); FP32
+    and FP64 FMA throughput measured now on the device; the SM count from
+    the device."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return json.load(fh)
-    except OSError:
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+            p = json.load(fh)
+        peaks = {"hbm_gbs": float(p["hbm_gbs"]), "hbm_source": "MEASURED_PEAKS.json (copy)",
+                 "sm_max_mhz": p.get("sm_max_mhz")}
+    except (OSError, KeyError, ValueError):
+        peaks = {"hbm_gbs": 6800.0, "hbm_source": "fallback 6.8 TB/s", "sm_max_mhz": 2070.0}
+    from paper_1602_02694_gb300.wlseno import measure_fma_peak
+    peaks["fp32_tflops"] = measure_fma_peak(dev.index, "fp32")
+    peaks["fp64_tflops"] = measure_fma_peak(dev.index, "fp64")
+    peaks["sms"] = torch.cuda.get_device_properties(dev).multi_processor_count
+    return peaks
+
+
+def measure_workload(torch, wl, steps, warmup, dist, peaks, dev, shape, sampler=None, with_e2e=False,
+                     horizons=None):
+    """Both precisions of one workload: throughput, kernel split, roofline,
+    accuracy, and (on request) the end-to-end rate."""
+    ctx32 = wl.context("fp32_bulk", dev.index, shape)
+    r32 = run_precision(torch, wl, ctx32, steps, warmup, dist, sampler)
+    ctx64 = wl.context("fp64", dev.index, shape)
+    steps64 = steps if wl.name in ("advection32", "burgers256") else max(3, steps // 10)
+    r64 = run_precision(torch, wl, ctx64, steps64, min(warmup, 3), dist, None)
+    hz = sorted({h for h in (horizons or (3, min(steps, wl.default_steps))) if 0 < h <= max(steps, 3)})
+    acc = accuracy_report(torch, wl, ctx32, ctx64, hz)
+    res = {"workload": wl.desc, "cells": wl.n_cells, "steps": steps,
+           "value": wl.n_cells * 3 * steps / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"] / steps,
+           "fp64_gpu": {"value": wl.n_cells * 3 * steps64 / (r64["ms"] * 1e-3), "steps": steps64,
+                        "ms_per_step": r64["ms"] / steps64, "kernels": kernel_split(r64["diag"])},
+           "accuracy": acc, "kernels": kernel_split(r32["diag"]), "gpu_launches": r32["launches"],
+           "kernel_shape": {"fp32_bulk": r32["shape"], "fp64": r64["shape"]},
+           "moments_mode_fp32_bulk": r32["info"]["moments_mode"],
+           "flagged_per_stage_fp32_bulk": r32["flagged_per_stage"],
+           "setup_s": {"fp32_bulk": r32["setup_s"], "fp64": r64["setup_s"]}}
+    res["fp64_gpu"]["speedup_fp32_bulk_vs_fp64"] = res["value"] / res["fp64_gpu"]["value"]
+    roof = roofline(wl, r32["info"], r32["diag"], "fp32_bulk", peaks)
+    roof64 = roofline(wl, r64["info"], r64["diag"], "fp64", peaks)
+    res["roofline"], res["roofline_other"] = (roof if roof else (None, None))
+    res["fp64_gpu"]["roofline"] = roof64[0] if roof64 else None
+    if wl.name == "batched48":
+        res["adjoint_ms_per_step_fp64"] = adjoint_cost(torch, wl, ctx64, 5)
+        res["forward_ms_per_step_fp64"] = res["fp64_gpu"]["ms_per_step"]
+    if with_e2e:
+        e2e_steps = max(3, min(steps, 30))
+        el, state_bytes = run_e2e(torch, wl, ctx32, e2e_steps)
+        el = max_over_ranks(el, dist, dev)
+        res["e2e"] = {"value": sum_over_ranks(wl.n_cells * 3 * e2e_steps, dist, dev) / el, "unit": UNIT,
+                      "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes, "steps": e2e_steps}
+    res["_r32"] = r32
+    ctx32.close()
+    ctx64.close()
+    return res
 
 
 def main():
@@ -556,26 +826,27 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    n_cells = 2 * args.n * args.n
-    workload = WORKLOAD if args.n == N_SIDE else WORKLOAD.replace("256x256", f"{args.n}x{args.n}").replace(
-        "131,072", f"{n_cells:,}")
-    mesh = synth.tri_mesh(args.n, jitter=JITTER, seed=SEED)
-    u0 = synth.burgers_2d_initial(mesh)
-    config = {"workload": workload, "cells": n_cells, "p": P_ORDER, "stencil_ring": RING, "cfl": CFL,
-              "mesh_seed": SEED, "l2": "flushed: a 256 MB write before every timed step, outside its CUDA "
-              "events (each step timed alone; e2e steps run back to back with their state copies)"}
+    head = WORKLOADS[HEADLINE]
+    config = {"workload": head["desc"], "cells": 2 * 1024 * 1024, "p": 3, "stencil_ring": 1.0, "cfl": CFL,
+              "mesh_seed": SEED, "data_seed": 3,
+              "l2": "flushed: a 256 MB write before every timed step, outside its CUDA events (each step timed "
+                    "alone; the step's working set is also larger than the L2; e2e steps run back to back with "
+                    "their state copies)"}
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        rate, desc, cores = oracle_cpu_rate(mesh, u0, max(2.0, args.cpu_seconds), host_cores(),
-                                            warmup=args.warmup, steps=max(1, args.steps))
+        rate, desc, cores = oracle_euler_rate(1024, 3, max(2.0, args.cpu_seconds), host_cores(),
+                                              warmup=args.warmup, steps=max(1, args.steps))
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": n_cells * 3 / rate * 1e3, "higher_is_better": True, "scaling": "weak",
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
                 "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        # the measured time of one timed step (a step here is one oracle RK3
+        # step of its sub-mesh, cells x 3 cell-stages per process)
+        line["ms_per_step"] = None
+        line["sample_note"] = "ms_per_step is not extrapolated: each step is a sub-mesh sample"
         print(json.dumps(line), flush=True)
         return 0
 
@@ -589,71 +860,50 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    peaks = load_peaks()
+    peaks = load_peaks(torch, dev)
     sampler = ClockSampler(gpu_uuid(torch, dev))
 
-    ctx32 = make_context("fp32_bulk", mesh, dev.index, args.shape, args.moments)
-    info = ctx32.info()
-    r32 = run_precision(torch, ctx32, u0, args.steps, args.warmup, dist, sampler)
-    ctx64 = make_context("fp64", mesh, dev.index, args.shape)
-    r64 = run_precision(torch, ctx64, u0, args.steps, args.warmup, dist, None)
-    u32 = r32["u"].cpu().numpy()
-    u64 = r64["u"].cpu().numpy()
-    rel_l1 = float(np.sum(np.abs(u32 - u64)) / np.sum(np.abs(u64)))
-    accuracy = accuracy_report(torch, mesh, u0, ctx32, ctx64)
-    ctx64.close()
+    wl = Workload(HEADLINE)
+    main_res = measure_workload(torch, wl, args.steps, args.warmup, dist, peaks, dev, args.shape, sampler,
+                                with_e2e=True, horizons=(3, 30, 100, args.steps))
+    r32 = main_res.pop("_r32")
+    del wl
+    others = [w for w in WORKLOADS if w != HEADLINE]
+    if args.only:
+        others = [w for w in others if w in args.only.split(",")]
+    configs = {}
+    for name in others:
+        w = Workload(name)
+        horizons = (3, 20) if name == "burgers256" else None
+        res = measure_workload(torch, w, w.default_steps, args.warmup, dist, peaks, dev, args.shape,
+                               horizons=horizons)
+        res.pop("_r32")
+        configs[name] = res
+        del w
 
-    e2e_steps = max(3, min(args.steps, 50))
-    el, state_bytes = run_e2e(torch, ctx32, u0, e2e_steps)
-    el = max_over_ranks(el, dist, dev)
-    ctx32.close()
-
-    # every rank steps its own replica: the units of all ranks over the
-    # slowest rank's time (already max-reduced)
-    total = sum_over_ranks(n_cells * 3 * args.steps, dist, dev)
+    total = sum_over_ranks(main_res["cells"] * 3 * args.steps, dist, dev)
     value = total / (r32["ms"] * 1e-3)
-    value64 = total / (r64["ms"] * 1e-3)
     clocks = r32["clocks"] or {}
-    roof = roofline(r32["info"], r32["diag"], n_cells, "fp32_bulk", peaks, None)
-    roof64 = roofline(r64["info"], r64["diag"], n_cells, "fp64", peaks, None)
-    mode_steps = max(3, min(args.steps, 50))
-    modes = {name: run_moments_mode(torch, mesh, u0, dev.index, mode, mode_steps)
-             for mode, name in ((0, "stored_rows"), (1, "on_the_fly"))}
-    modes["chosen"] = "on_the_fly" if r32["info"]["moments_mode"] == 1 else "stored_rows"
-    kern = {k: {"launches": r32["diag"]["launches_by_kind"][k], "ms": r32["diag"]["kernel_ms"][k]}
-            for k in ("reconstruct", "fixup", "flux", "dt")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32",
-            "precision": "FP32-bulk: f32 weights, QR, evaluation and deviation flux; f64 moments and "
-                         "refinement residual; double-float (f32 pair) reference flux, sums and RK update",
-            "data": "synthetic", "config": dict(config, parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
-            "fp64_gpu": {"value": value64, "ms_per_step": r64["ms"] / args.steps,
-                         "speedup_fp32_bulk_vs_fp64": value / value64,
-                         "rel_l1_fp32_bulk_vs_fp64_after_timed_steps": rel_l1,
-                         "accuracy": accuracy,
-                         "roofline": roof64[0] if roof64 else None},
-            "e2e": {"value": sum_over_ranks(n_cells * 3 * e2e_steps, dist, dev) / el, "unit": UNIT,
-                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                    "steps": e2e_steps},
-            "gpu_launches": r32["launches"],
-            "kernels": kern,
-            "roofline": roof[0] if roof else None,
-            "roofline_other": roof[1] if roof else None,
-            "setup_s": {"moments_and_autotune_fp32": r32["setup_s"],
-                        "moments_and_autotune_fp64": r64["setup_s"]},
-            "kernel_shape": {"fp32_bulk": list(r32["shape"]), "fp64": list(r64["shape"])},
-            "moments_modes": modes,
-            "refined_cells_per_stage": r32["flagged_per_stage"],
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "precision": "FP32-bulk: f32 weights, QR, evaluation and flux; f64 moments and refinement "
+                         "residual; double-float (f32 pair) facet sums and RK update",
+            "data": "synthetic",
+            "config": dict(config, parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+            "fp64_gpu": main_res["fp64_gpu"], "accuracy": main_res["accuracy"], "e2e": main_res["e2e"],
+            "gpu_launches": main_res["gpu_launches"], "kernels": main_res["kernels"],
+            "roofline": main_res["roofline"], "roofline_other": main_res["roofline_other"],
+            "setup_s": main_res["setup_s"], "kernel_shape": main_res["kernel_shape"],
+            "moments_mode_fp32_bulk": main_res["moments_mode_fp32_bulk"],
+            "flagged_per_stage_fp32_bulk": main_res["flagged_per_stage_fp32_bulk"],
             "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                        "reasons": clocks.get("reasons", []),
                        "samples_in_timed_region": clocks.get("samples_in_timed_region")},
-            "peaks": {"source": "MEASURED_PEAKS.json" if not peaks.get("fallback") else "fallback",
-                      "hbm_gbs": peaks.get("hbm_gbs")}}
+            "peaks": peaks, "configs": configs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate1, desc1, _ = oracle_cpu_rate(mesh, u0, args.cpu_seconds, 1)
-        rate, desc, cores = oracle_cpu_rate(mesh, u0, args.cpu_seconds, host_cores())
+        rate1, desc1, _ = oracle_euler_rate(1024, 3, args.cpu_seconds, 1)
+        rate, desc, cores = oracle_euler_rate(1024, 3, args.cpu_seconds, host_cores())
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                                 "single_core": {"value": rate1, "cores": 1, "sample": desc1}}
     if rank == 0:

@@ -13,9 +13,10 @@
  * Conventions shared by every entry point:
  *  - Every call returns a wlseno_status; nothing aborts and no C++ exception
  *    crosses the ABI.  wlseno_status_string() names a status.
- *  - Cell order is the caller's: cell c of mesh k is global cell
- *    (sum of n_cells of meshes 0..k-1) + c.  Per-cell arrays are
- *    component-major: [n_comp][n_cells_total] float64.
+ *  - Cell order: cell c of mesh k is global cell (sum of n_cells of meshes
+ *    0..k-1) + c, in the caller's order unless wlseno_build_stencils was
+ *    asked to reorder (then in the library's order, which perm_out gives).
+ *    Per-cell arrays are component-major: [n_comp][n_cells_total] float64.
  *  - Array arguments marked "host or device" may be either: device pointers
  *    are used in place (stream-ordered on `stream`, asynchronous); host
  *    pointers are copied to and from the device inside the call, which then
@@ -25,6 +26,15 @@
  *    workspace).  Caller buffers are never retained after a call returns (or,
  *    for device pointers, after the stream work it enqueued completes).
  *  - A context is not thread safe; use one context per host thread.
+ *  - Non-finite results: a kernel that writes a non-finite cell average,
+ *    facet value or residual sets the context's status word (host memory the
+ *    device writes).  The next wlseno_reconstruct, wlseno_flux_residual,
+ *    wlseno_rk_step or wlseno_step_adjoint on the context returns
+ *    WLSENO_ERR_NUMERIC without doing any work and clears the word; a call
+ *    that synchronises (host arrays, or rk_step with dt_out) also checks it
+ *    after its own work and returns WLSENO_ERR_NUMERIC then.  With device
+ *    arrays the report comes once that work has run: at a later call, or
+ *    at the first call after a synchronisation.
  */
 #ifndef WLSENO_H
 #define WLSENO_H
@@ -92,7 +102,24 @@ typedef struct {
  *             cell's own central moments (gathered, 16 or 32 bytes per cell)
  *             by the binomial expansion of the Taylor monomials about x_j:
  *             a third of the row bytes for about 40 more FP32 operations per
- *             row.  wlseno_autotune also tries both. */
+ *             row.  wlseno_autotune also tries both.
+ * reorder:    0 keeps the caller's cell order; 1 renumbers the cells of
+ *             every mesh along the Hilbert curve of their centroids (ties by
+ *             the caller's index), so that stencil neighbours get nearby
+ *             indices and the kernels' gathers stay local for any input
+ *             order.  All per-cell arrays of later calls are then in the new
+ *             order (see perm_out of wlseno_build_stencils).
+ * persistent: 0 runs each RK step as one kernel per phase (captured as a
+ *             CUDA graph); 1 runs it as ONE persistent cooperative kernel
+ *             whose resident blocks walk the cells of all meshes of the
+ *             context through every phase of the step (time step,
+ *             reconstruction, follow-ups on flagged cells, flux and stage
+ *             update, three stages) with grid-wide barriers in between.
+ *             Every barrier wait is bounded (wlseno_set_wait_limit); a wait
+ *             that gives up makes the next call return WLSENO_ERR_TIMEOUT.
+ *             Scalar equations on 2-D meshes, p = 3 or 4, fixed stencils,
+ *             the thread-per-cell shape; else INVALID_ARG.  The results
+ *             equal those of persistent = 0 bit for bit. */
 typedef struct {
   int order_p;
   double ring;
@@ -101,6 +128,8 @@ typedef struct {
   int lanes_per_cell;
   int rows_per_lane;
   int moments_mode;
+  int reorder;
+  int persistent;
 } wlseno_stencil_opts;
 
 /* Scheme parameters.
@@ -190,16 +219,18 @@ typedef struct {
   int lanes_per_cell;      /* kernel shape chosen for the reconstruction        */
   int rows_per_lane;
   int moments_mode;        /* 0 stored rows, 1 formed on the fly (see opts)     */
+  int persistent;          /* 1: one persistent kernel per RK step (see opts)   */
 } wlseno_info;
 
 /* Kernel kinds of the per-kind launch counts and timings.  RECONSTRUCT is
  * the main reconstruction kernel; FIXUP the follow-ups that redo the cells it
  * flags (refinement sweep, pivoted path) and the balanced-stencil range test
  * and re-selection; DT the per-step preparation (CFL
- * time step and, in FP32-bulk, the FP32 split of the state). */
+ * time step and, in FP32-bulk, the FP32 split of the state); STEP the
+ * persistent kernel of a whole RK step (opts.persistent). */
 enum { WLSENO_KERNEL_MOMENTS = 0, WLSENO_KERNEL_RECONSTRUCT = 1, WLSENO_KERNEL_FLUX = 2,
        WLSENO_KERNEL_DT = 3, WLSENO_KERNEL_ADJOINT = 4, WLSENO_KERNEL_FIXUP = 5,
-       WLSENO_N_KERNEL_KINDS = 6 };
+       WLSENO_KERNEL_STEP = 6, WLSENO_N_KERNEL_KINDS = 7 };
 
 typedef struct {
   int64_t flagged_cells;   /* cells flagged ill-conditioned (last call)         */
@@ -228,11 +259,16 @@ void wlseno_destroy(wlseno_ctx* ctx);
  * volumes, mean edge lengths, facet normals and areas, half-facet siblings
  * and the k-ring stencil of every cell of every mesh (stencils never cross
  * meshes), then uploads them.  The mesh arrays are copied; nothing is kept.
+ * perm_out: host [n_cells_total] or NULL; receives for every global cell
+ * index of the library's order the caller's global index of that cell
+ * (new -> old; the identity unless opts->reorder), so a caller permutes its
+ * arrays once: ubar_lib[k] = ubar_caller[perm_out[k]].  Cells never leave
+ * their mesh's index range.
  * Errors: INVALID_ARG, MESH (inverted cell, facet shared by > 2 cells),
  * STENCIL (a stencil with fewer than m cells, or more than the kernels hold),
  * OOM, CUDA. */
 wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, int n_meshes,
-                                    const wlseno_stencil_opts* opts);
+                                    const wlseno_stencil_opts* opts, int64_t* perm_out);
 
 /* Device precompute in FP64 (Sec. 3.2, Sec. 3.3.2): for every stencil row
  * (i, j) the h_i-normalised cell average over tau_j of
@@ -290,11 +326,14 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
  *         device per mesh.
  * dt_out: optional host pointer receiving the last step's dt (of mesh 0); it
  *         synchronises the stream when non-NULL.
+ * A call with dt > 0 discards the per-mesh steps of wlseno_set_mesh_dt (the
+ * fixed step overwrites them on the device): call wlseno_set_mesh_dt again
+ * before the next dt < 0 call.
  * One step is captured as a CUDA graph (on the context's own stream) and
  * replayed for n_steps >= 2, for a host ubar (staged through the context's
  * buffer), and for one step whose arguments match the captured one; not in
  * timing mode or while `stream` is being captured.
- * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
+ * Errors: STATE, INVALID_ARG, CUDA, NUMERIC, TIMEOUT (persistent steps). */
 wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
                              double* dt_out, void* stream);
 
@@ -311,7 +350,9 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
  * ubar, residual: [n_comp][n_cells] DEVICE arrays (host pointers are rejected
  * with WLSENO_ERR_INVALID_ARG: staging them would allocate).
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call shares
+ * device); make that first call before any stream capture.  The address is
+ * kept for the life of the process: after cudaDeviceReset on that device it
+ * is stale, so do not call this entry point again in that process.  Every call shares
  * the one array and fully overwrites the part it reads, so nothing needs
  * clearing, but calls whose work overlaps on the GPU (other streams, other
  * contexts on the same device) race on it: order them on one stream.
@@ -337,8 +378,9 @@ wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host);
  * wlseno_set_mesh_dt (0 is rejected: a CFL step is not differentiated).
  * All arrays [n_cells] (n_comp = 1), host or device; the first call
  * allocates the adjoint's work arrays.  Scalar equations on 2-D and 3-D
- * meshes with fixed stencils (balanced = 0), else INVALID_ARG.
- * Errors: STATE, INVALID_ARG, CUDA. */
+ * meshes with fixed stencils (balanced = 0), else INVALID_ARG.  A call with
+ * dt > 0 discards the steps of wlseno_set_mesh_dt, as in wlseno_rk_step.
+ * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
                                   const double* gbar_next, double* gbar_n, void* stream);
 
@@ -351,6 +393,17 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
  * `stream`.  Errors: STATE, INVALID_ARG, CUDA. */
 wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, void* stream,
                               double* best_us);
+
+/* Poll limit of the bounded device waits (the grid barriers of the
+ * persistent step kernel): a block polls a barrier at most max_polls times,
+ * about 64 ns apart, before it gives up; the step then stops at its next
+ * barrier in every block, its state is incomplete, and the next call on the
+ * context (or this rk_step call, when it synchronises) returns
+ * WLSENO_ERR_TIMEOUT.  0 restores the default 2^24 (about a second).
+ * Host only; takes effect at the next step that is not a replay of an
+ * already captured one (the limit is part of the captured launch).
+ * Errors: INVALID_ARG (null context, max_polls < 0). */
+wlseno_status wlseno_set_wait_limit(wlseno_ctx* ctx, int64_t max_polls);
 
 /* Sizes and the kernel shape in use.  Errors: STATE, INVALID_ARG. */
 wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out);
@@ -375,6 +428,16 @@ wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out);
  * and times; otherwise they accumulate over calls.
  * Errors: INVALID_ARG, CUDA. */
 wlseno_status wlseno_set_timing(wlseno_ctx* ctx, int enable);
+
+/* Measured arithmetic peak of device `device` for the rooflines of a
+ * benchmark (no counterpart in the paper: a measurement utility).
+ * precision WLSENO_FP32_BULK measures FP32, WLSENO_FP64 FP64 fused
+ * multiply-add throughput: independent FMA chains (8 per thread, 256 threads
+ * per block, 8 blocks per SM), the fastest of five timed launches after one
+ * warm-up, 2 flops per FMA, in TFLOP/s into *tflops (host).  Runs on the
+ * legacy default stream and synchronises; allocates a small device buffer;
+ * reads and changes no GPU setting.  Errors: INVALID_ARG, CUDA, OOM. */
+wlseno_status wlseno_measure_fma_peak(int device, int precision, double* tflops);
 
 const char* wlseno_status_string(wlseno_status s);
 

@@ -13,9 +13,8 @@
 
 using namespace wlseno;
 
-// device counters: flagged, rank deficient, nonfinite, positivity fallbacks,
-// balanced re-selections
-constexpr int kCounters = 5;
+// Polls of a bounded device wait before it gives up (about 64 ns apart: ~1 s).
+constexpr long long kDefaultSpinCap = 1ll << 24;
 
 struct wlseno_ctx {
   int device = 0;
@@ -42,11 +41,15 @@ struct wlseno_ctx {
   double* d_out = nullptr;       // [C][N] staging for host outputs
   double* d_coef = nullptr;      // [C][N][m] staging for host coefficient output
   double* d_fv_out = nullptr;    // [C][N][NP] staging for host facet-value output
-  int* d_wl = nullptr;           // [N] cells for the pivoted lane-group path
+  int* d_wl = nullptr;           // [wl_cap] (component, cell) tags for the pivoted lane-group path
   int* d_wl_count = nullptr;     // [2] lengths of d_wl and of the refine records
-  float* d_rbuf = nullptr;       // [N][refine_record_floats(m)] FP32-bulk refine records
-  float* d_fdev = nullptr;       // [N][NP] FP32-bulk facet deviations (scalar equations)
-  float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk)
+  float* d_rbuf = nullptr;       // [wl_cap][refine_record_floats(m)] FP32-bulk refine records
+  int64_t wl_cap = 0;            // N, or C N with the all-components Euler kernel
+  float* d_fdev = nullptr;       // [C][N][NP] FP32-bulk facet deviations (scalar equations, 2-D Euler)
+  float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk;
+                                 // interleaved [N][C] on the all-components Euler path)
+  bool euler32 = false;          // FP32-bulk 2-D Euler p = 3: all components in one kernel
+  unsigned char* d_pos_ok = nullptr;  // [N] its positivity flags
   BalanceWork bal{};             // balanced-stencil re-selection (when the scheme asks for it)
   // side stream of the pivoted-path kernel, forked from and joined to the
   // caller's stream around the refinement sweep
@@ -77,6 +80,17 @@ struct wlseno_ctx {
   size_t events_used = 0;
   cudaStream_t last_stream = nullptr;
   double last_dt = 0.0;
+  // status words (mapped pinned host memory, set by the kernels): [0]
+  // non-finite results, [1] a bounded device wait gave up
+  unsigned int* h_latch = nullptr;
+  unsigned int* d_latch = nullptr;
+  // persistent step kernel (opts.persistent): per-stage list lengths [6],
+  // barrier words [3], the poll limit of its waits
+  bool persistent = false;
+  int* d_counts6 = nullptr;
+  unsigned int* d_sync = nullptr;
+  long long spin_cap = kDefaultSpinCap;
+  bool persist_no_capture = false;  // the cooperative launch could not be captured
   std::string error;
 };
 
@@ -221,6 +235,9 @@ cudaError_t dispatch_dim_m(int dim, int m, F&& f) {
   return cudaErrorInvalidValue;
 }
 
+// The all-components FP32-bulk Euler path is in use (thread-per-cell shape).
+bool euler_fused(const wlseno_ctx* ctx) { return ctx->euler32 && ctx->G == 1; }
+
 // FP32 pairs of a state (the scratch slot of d_pair), counted as a per-step
 // preparation kernel.
 cudaError_t split_state(wlseno_ctx* ctx, const double* u, float2* pair, cudaStream_t s) {
@@ -247,8 +264,9 @@ cudaError_t reconstruct_plain(wlseno_ctx* ctx, const double* ubar, double* coeff
     return e;
   KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
   if (ctx->G == 1) {
-    const TpcWork wl{ctx->d_wl,   ctx->d_wl_count, ctx->d_rbuf, pair,
-                     ctx->side,   ctx->ev_fork,    ctx->ev_join, ctx->otf && f32};
+    TpcWork wl{ctx->d_wl,   ctx->d_wl_count, ctx->d_rbuf, pair,
+               ctx->side,   ctx->ev_fork,    ctx->ev_join, ctx->otf && f32};
+    wl.capacity = ctx->wl_cap;
     e = dispatch_dim_m(dm.dim, dm.m, [&](auto D, auto Mc) {
       constexpr int DD = decltype(D)::value, MM = decltype(Mc)::value;
       return f32 ? launch_recon_tpc_inst<float, DD, MM>(dm, ctx->sp, ubar, out, wl, s)
@@ -316,6 +334,43 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
   const int C = ctx->scheme.n_comp;
   const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
   cudaError_t e = cudaSuccess;
+  if (euler_fused(ctx)) {
+    // FP32-bulk 2-D Euler: the pairs of u (interleaved), one reconstruction
+    // of all components with the positivity flags, its follow-ups, the flux
+    const DeviceMesh& dm = ctx->dm;
+    const float2* pu = pin;
+    if (!pu) {
+      KernelScope sp_scope(ctx, WLSENO_KERNEL_DT, s);
+      e = launch_euler2_split_pairs(u, ctx->d_pair, N, s);
+      sp_scope.done(e == cudaSuccess ? 1 : 0);
+      if (e != cudaSuccess) return e;
+      pu = ctx->d_pair;
+    }
+    if ((e = cudaMemsetAsync(ctx->d_wl_count, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+    TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, pu, ctx->side, ctx->ev_fork, ctx->ev_join, ctx->otf};
+    wl.capacity = ctx->wl_cap;
+    wl.pos_ok = ctx->d_pos_ok;
+    wl.gamma = static_cast<float>(ctx->sp.gamma);
+    const ReconOut ro{nullptr, nullptr, ctx->d_counters, ctx->d_fdev};
+    {
+      KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
+      e = launch_recon_euler2d(dm, ctx->sp, u, ro, wl, s);
+      scope.done(e == cudaSuccess ? 1 : 0);
+      if (e != cudaSuccess) return e;
+    }
+    {
+      int nl = 0;
+      KernelScope fix(ctx, WLSENO_KERNEL_FIXUP, s);
+      e = launch_recon_fixup_inst<float, 2, 6>(dm, ctx->sp, u, ro, wl, s, &nl);
+      fix.done(e == cudaSuccess ? nl : 0);
+      if (e != cudaSuccess) return e;
+    }
+    KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
+    e = launch_euler2_flux32(dm, ctx->sp.gamma, ctx->d_fdev, ctx->d_pos_ok, pu, p0, a, b, ctx->d_dt2,
+                             residual_only, out, ctx->d_counters, pout, s);
+    scope.done(e == cudaSuccess ? 1 : 0);
+    return e;
+  }
   if (ctx->scheme.pde == WLSENO_EULER) {
     if (ctx->scheme.characteristic) {
       KernelScope scope(ctx, WLSENO_KERNEL_RECONSTRUCT, s);
@@ -354,6 +409,33 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
   return e;
 }
 
+// One stage's reconstruction with the context's current shape, for the
+// autotuner: the all-components Euler kernel with its follow-ups, or every
+// component through the one-component kernels.
+cudaError_t tune_recon(wlseno_ctx* ctx, const double* u, cudaStream_t s) {
+  const int64_t N = ctx->dm.N;
+  if (euler_fused(ctx)) {
+    cudaError_t e = launch_euler2_split_pairs(u, ctx->d_pair, N, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->d_wl_count, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+    TpcWork wl{ctx->d_wl, ctx->d_wl_count, ctx->d_rbuf, ctx->d_pair, ctx->side, ctx->ev_fork, ctx->ev_join,
+               ctx->otf};
+    wl.capacity = ctx->wl_cap;
+    wl.pos_ok = ctx->d_pos_ok;
+    wl.gamma = static_cast<float>(ctx->sp.gamma);
+    const ReconOut ro{nullptr, nullptr, ctx->d_counters, ctx->d_fdev};
+    if ((e = launch_recon_euler2d(ctx->dm, ctx->sp, u, ro, wl, s)) != cudaSuccess) return e;
+    int nl = 0;
+    return launch_recon_fixup_inst<float, 2, 6>(ctx->dm, ctx->sp, u, ro, wl, s, &nl);
+  }
+  const int C = ctx->scheme.pde == WLSENO_EULER ? ctx->scheme.n_comp : 1;
+  const int NP = (ctx->dm.dim + 1) * ctx->dm.nq;
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < C && e == cudaSuccess; ++c)
+    e = reconstruct_one(ctx, u + c * N, nullptr, ctx->d_fvals + c * N * NP, s);
+  return e;
+}
+
 // The kernel variant a captured step used: shape and moments mode.
 int shape_key(const wlseno_ctx* ctx) { return (ctx->G * 64 + ctx->R) * 2 + (ctx->otf ? 1 : 0); }
 
@@ -364,9 +446,39 @@ wlseno_status check_ready(wlseno_ctx* ctx) {
   return WLSENO_OK;
 }
 
+// Non-finite values written by kernels the context launched earlier (seen
+// once their work has reached the status word): reported once, then cleared.
+wlseno_status take_nonfinite(wlseno_ctx* ctx) {
+  volatile unsigned int* latch = ctx->h_latch;
+  if (!latch) return WLSENO_OK;
+  if (latch[1] != 0u) {
+    latch[1] = 0u;
+    latch[0] = 0u;  // the results of a step that gave up are not reported twice
+    return fail(ctx, WLSENO_ERR_TIMEOUT,
+                "a grid barrier of the persistent step kernel waited longer than its poll limit; "
+                "the state of that step is incomplete");
+  }
+  if (latch[0] == 0u) return WLSENO_OK;
+  latch[0] = 0u;
+  return fail(ctx, WLSENO_ERR_NUMERIC,
+              "non-finite values in the results (cell averages, facet values or residuals) of "
+              "work this context ran");
+}
+
 }  // namespace
 
 namespace wlseno {
+
+// FP32-bulk: refine above kappa_flag, pivot above 1e5 (one FP32 refinement
+// sweep contracts the error by about kappa 2^-24); FP64: pivot above 1e6.  A rank tolerance above 1e-8 lowers the pivot bound to 1e-2 /
+// rank_tol, so that every cell whose rank the rule of Sec. 3.3.2 might cut
+// still reaches the pivoted path (the estimates bound the conditioning from
+// below; from rank_tol >= 1e-2 on every cell goes there).
+void tpc_thresholds(const SchemeParams& sp, bool f32, double* flag, double* pivot) {
+  const double route = sp.rank_tol > 0.0 ? 1e-2 / sp.rank_tol : 1e300;
+  *pivot = std::fmin(f32 ? 1e5 : 1e6, route);
+  *flag = f32 ? std::fmin(sp.kappa_flag, *pivot) : *pivot;
+}
 
 bool ctx_view(const wlseno_ctx* ctx, CtxView* out) {
   if (!ctx || !out) return false;
@@ -449,6 +561,21 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   wlseno_ctx* ctx = new (std::nothrow) wlseno_ctx();
   if (!ctx) return WLSENO_ERR_OOM;
   ctx->device = device;
+  {
+    DeviceGuard guard(device);
+    void* h = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&h, 2 * sizeof(unsigned int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (h) cudaFreeHost(h);
+      delete ctx;
+      return WLSENO_ERR_CUDA;
+    }
+    ctx->h_latch = static_cast<unsigned int*>(h);
+    ctx->d_latch = static_cast<unsigned int*>(d);
+    ctx->h_latch[0] = ctx->h_latch[1] = 0u;
+  }
   ctx->scheme = *scheme;
   ctx->sp.pde = scheme->pde;
   for (int a = 0; a < 3; ++a) ctx->sp.vel[a] = scheme->velocity[a];
@@ -472,13 +599,44 @@ void wlseno_destroy(wlseno_ctx* ctx) {
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     free_all(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->h_latch) cudaFreeHost(ctx->h_latch);
   }
   delete ctx;
 }
 
 wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, int n_meshes,
-                                    const wlseno_stencil_opts* opts) {
+                                    const wlseno_stencil_opts* opts, int64_t* perm_out) {
   if (!ctx) return WLSENO_ERR_INVALID_ARG;
+  if (opts && opts->reorder != 0 && opts->reorder != 1)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "reorder must be 0 or 1");
+  if (opts && opts->persistent != 0 && opts->persistent != 1)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG, "persistent must be 0 or 1");
+  // Hilbert order: permuted copies of the meshes' cell arrays
+  std::vector<wlseno_mesh> reordered;
+  std::vector<std::vector<int64_t>> cells_new;
+  std::vector<int64_t> perm;
+  if (meshes && n_meshes > 0 && opts && opts->reorder == 1) {
+    reordered.assign(meshes, meshes + n_meshes);
+    cells_new.resize(n_meshes);
+    int64_t base = 0;
+    for (int k = 0; k < n_meshes; ++k) {
+      const wlseno_mesh& m = meshes[k];
+      if (!m.cells || !m.vertices || m.n_cells <= 0 || m.dim < 1 || m.dim > 3)
+        return fail(ctx, WLSENO_ERR_INVALID_ARG, "mesh " + std::to_string(k) + ": null arrays or bad sizes");
+      std::vector<int64_t> order;
+      if (!hilbert_order(m, &order))
+        return fail(ctx, WLSENO_ERR_MESH, "mesh " + std::to_string(k) + ": vertex index out of range");
+      const int nv = m.dim + 1;
+      cells_new[k].resize(static_cast<size_t>(m.n_cells) * nv);
+      for (int64_t c = 0; c < m.n_cells; ++c) {
+        for (int v = 0; v < nv; ++v) cells_new[k][c * nv + v] = m.cells[order[c] * nv + v];
+        perm.push_back(base + order[c]);
+      }
+      reordered[k].cells = cells_new[k].data();
+      base += m.n_cells;
+    }
+    meshes = reordered.data();
+  }
   DeviceGuard guard(ctx->device);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);  // it captured the old buffers
   ctx->graph_exec = nullptr;
@@ -514,9 +672,15 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
       (opts->moments_mode != 1 || G != 1 || ctx->scheme.precision != WLSENO_FP32_BULK))
     return fail(ctx, WLSENO_ERR_INVALID_ARG,
                 "moments_mode 1 needs FP32-bulk precision and the thread-per-cell shape");
+  if (opts->persistent &&
+      (ctx->scheme.pde == WLSENO_EULER || ctx->scheme.balanced || G != 1 || !persistent_supported(H.dim, H.m)))
+    return fail(ctx, WLSENO_ERR_INVALID_ARG,
+                "the persistent step is built for the scalar equations on 2-D meshes (p = 3, 4), fixed "
+                "stencils and the thread-per-cell shape");
   ctx->G = G;
   ctx->R = R;
   ctx->otf = opts->moments_mode == 1;
+  ctx->persistent = opts->persistent == 1;
   const int64_t N = H.N;
   std::vector<int32_t> ptr32(N + 1), idx32(H.nnz);
   for (int64_t i = 0; i <= N; ++i) ptr32[i] = static_cast<int32_t>(H.row_ptr[i]);
@@ -560,7 +724,23 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.fpts32 = fp32;
   dm.ff32 = nullptr;
   dm.inv_vol2 = nullptr;
-  if (ctx->scheme.precision == WLSENO_FP32_BULK && ctx->scheme.pde != WLSENO_EULER) {
+  dm.nf_latch = ctx->d_latch;
+  dm.nf32 = nullptr;
+  ctx->euler32 = ctx->scheme.precision == WLSENO_FP32_BULK && ctx->scheme.pde == WLSENO_EULER &&
+                 !ctx->scheme.characteristic && H.dim == 2 && H.m == 6;
+  if (ctx->euler32) {
+    // FP32 owner normal and area of every (cell, facet) record, 1/|tau| pairs
+    const int nf = H.dim + 1;
+    std::vector<float4> nf4(static_cast<size_t>(N) * nf);
+    for (size_t k = 0; k < nf4.size(); ++k) {
+      const double* G = &H.fgeo[k * 4];
+      nf4[k] = make_float4(static_cast<float>(G[0]), static_cast<float>(G[1]), 0.0f, static_cast<float>(G[3]));
+    }
+    float4* d_nf = nullptr;
+    if ((st = upload(ctx, &d_nf, nf4))) return st;
+    dm.nf32 = d_nf;
+  }
+  if (ctx->scheme.precision == WLSENO_FP32_BULK && (ctx->scheme.pde != WLSENO_EULER || ctx->euler32)) {
     const int nf = H.dim + 1;
     std::vector<FacetF32> ff(static_cast<size_t>(N) * nf);
     for (size_t k = 0; k < ff.size(); ++k) {
@@ -579,7 +759,7 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
     }
     FacetF32* d_ff = nullptr;
     if ((st = upload(ctx, &d_ff, ff))) return st;
-    dm.ff32 = d_ff;
+    dm.ff32 = ctx->scheme.pde == WLSENO_EULER ? nullptr : d_ff;
     std::vector<float2> iv(static_cast<size_t>(N));
     for (int64_t i = 0; i < N; ++i) {
       const double v = 1.0 / H.volume[i];
@@ -600,19 +780,25 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
     return st;
   dm.nmax = H.max_n;
   const size_t ell = static_cast<size_t>(H.max_n) * N;
+  ctx->wl_cap = ctx->euler32 ? static_cast<int64_t>(C) * N : N;
   dm.rec_width = rec32_width(H.m);
   if ((st = dalloc(ctx, &dm.st_ell, ell)) || (st = dalloc(ctx, &dm.A64e, ell * H.m)) ||
-      (st = dalloc(ctx, &dm.rec32, ell * dm.rec_width)) || (st = dalloc(ctx, &ctx->d_wl, N)) ||
+      (st = dalloc(ctx, &dm.rec32, ell * dm.rec_width)) || (st = dalloc(ctx, &ctx->d_wl, ctx->wl_cap)) ||
       (st = dalloc(ctx, &ctx->d_wl_count, 2)))
     return st;
   dm.geo32 = dm.own32 = nullptr;
   dm.own_width = own32_width(H.dim, H.m);
   if (ctx->scheme.precision == WLSENO_FP32_BULK &&
-      ((st = dalloc(ctx, &ctx->d_fdev, N * NP)) || (st = dalloc(ctx, &ctx->d_pair, 3 * C * N)) ||
-       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * N)) ||
+      ((st = dalloc(ctx, &ctx->d_fdev, (ctx->euler32 ? C : 1) * N * NP)) ||
+       (st = dalloc(ctx, &ctx->d_pair, 3 * C * N)) ||
+       (st = dalloc(ctx, &ctx->d_rbuf, static_cast<size_t>(refine_record_floats(H.m)) * ctx->wl_cap)) ||
        (st = dalloc(ctx, &dm.geo32, ell * 4)) ||
        (st = dalloc(ctx, &dm.own32, static_cast<size_t>(N) * dm.own_width))))
     return st;
+  if (ctx->euler32 && (st = dalloc(ctx, &ctx->d_pos_ok, N))) return st;
+  if (ctx->persistent && ((st = dalloc(ctx, &ctx->d_counts6, 6)) || (st = dalloc(ctx, &ctx->d_sync, 4))))
+    return st;
+  ctx->persist_no_capture = false;
   if (ctx->scheme.balanced) {
     BalanceWork& b = ctx->bal;
     std::vector<int32_t> bp(N + 1), bi(H.bal_idx.size());
@@ -639,6 +825,12 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   }
   ctx->d_in = ctx->d_out = ctx->d_coef = ctx->d_fv_out = nullptr;
   ctx->built = true;
+  if (perm_out) {
+    if (perm.empty())
+      for (int64_t k = 0; k < N; ++k) perm_out[k] = k;
+    else
+      std::memcpy(perm_out, perm.data(), sizeof(int64_t) * N);
+  }
   return WLSENO_OK;
 }
 
@@ -660,7 +852,7 @@ wlseno_status wlseno_precompute_moments(wlseno_ctx* ctx, void* stream) {
 wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* coeffs,
                                  double* facet_values, void* stream) {
   wlseno_status st = check_ready(ctx);
-  if (st != WLSENO_OK) return st;
+  if (st != WLSENO_OK || (st = take_nonfinite(ctx)) != WLSENO_OK) return st;
   if (!ubar) return fail(ctx, WLSENO_ERR_INVALID_ARG, "ubar is null");
   if (ctx->scheme.characteristic && coeffs)
     return fail(ctx, WLSENO_ERR_INVALID_ARG,
@@ -712,6 +904,7 @@ wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* co
   if (host_io || coef_host || fv_host) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct");
+    return take_nonfinite(ctx);
   }
   return WLSENO_OK;
 }
@@ -719,7 +912,7 @@ wlseno_status wlseno_reconstruct(wlseno_ctx* ctx, const double* ubar, double* co
 wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* residual,
                                    void* stream) {
   wlseno_status st = check_ready(ctx);
-  if (st != WLSENO_OK) return st;
+  if (st != WLSENO_OK || (st = take_nonfinite(ctx)) != WLSENO_OK) return st;
   if (!ubar || !residual) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null array");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -749,6 +942,7 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
   if (in_host || out_host) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "flux_residual");
+    return take_nonfinite(ctx);
   }
   return WLSENO_OK;
 }
@@ -756,7 +950,7 @@ wlseno_status wlseno_flux_residual(wlseno_ctx* ctx, const double* ubar, double* 
 wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cfl, int n_steps,
                              double* dt_out, void* stream) {
   wlseno_status st = check_ready(ctx);
-  if (st != WLSENO_OK) return st;
+  if (st != WLSENO_OK || (st = take_nonfinite(ctx)) != WLSENO_OK) return st;
   if (!ubar || n_steps < 0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null ubar or n_steps < 0");
   if (dt < 0.0 && !ctx->mesh_dt_set)
     return fail(ctx, WLSENO_ERR_STATE, "dt < 0 needs wlseno_set_mesh_dt first");
@@ -781,9 +975,50 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   // FP32-bulk scalar thread-per-cell path: the FP32 pairs of u for stage 1
   // are made with the time step (scratch slot of d_pair; stages 2 and 3 read
   // them as the pairs of u0)
-  float2* pre = ctx->d_pair && ctx->G == 1 && C == 1 && ctx->scheme.pde != WLSENO_EULER ? ctx->d_pair : nullptr;
+  const bool fused = euler_fused(ctx);
+  float2* pre = ctx->d_pair && ctx->G == 1 && ((C == 1 && ctx->scheme.pde != WLSENO_EULER) || fused)
+                    ? ctx->d_pair : nullptr;
+  const bool persist = ctx->persistent && ctx->G == 1;
   auto enqueue_step = [&](cudaStream_t st) -> cudaError_t {
     cudaError_t err = cudaSuccess;
+    if (persist) {
+      // the whole step in one persistent cooperative kernel
+      PersistLaunch L;
+      L.dm = ctx->dm;
+      L.sp = ctx->sp;
+      L.fp32 = ctx->scheme.precision == WLSENO_FP32_BULK;
+      L.otf = ctx->otf && L.fp32;
+      L.u = u;
+      L.k1 = ctx->d_k1;
+      L.k2 = ctx->d_k2;
+      L.pairs = ctx->d_pair;
+      L.fvals = ctx->d_fvals;
+      L.fdev = ctx->d_fdev;
+      L.counters = ctx->d_counters;
+      L.group_list = ctx->d_wl;
+      L.counts = ctx->d_counts6;
+      L.refine_buf = ctx->d_rbuf;
+      L.capacity = ctx->wl_cap;
+      L.dt_mode = dt > 0.0 ? 1 : dt == 0.0 ? 0 : 2;
+      L.cfl = cfl;
+      L.dt_fixed = dt > 0.0 ? dt : 0.0;
+      double sp2 = 0.0;
+      for (int a = 0; a < ctx->dm.dim; ++a) sp2 += ctx->sp.vel[a] * ctx->sp.vel[a];
+      L.speed = ctx->scheme.pde == WLSENO_ADVECTION ? static_cast<float>(std::sqrt(sp2)) : 0.0f;
+      L.n_meshes = ctx->host.n_meshes;
+      L.rmin = ctx->d_rmin;
+      L.lmax = dt == 0.0 && ctx->scheme.pde == WLSENO_BURGERS ? ctx->d_lmax : nullptr;
+      L.dt_mesh = ctx->d_dt;
+      L.dt2 = ctx->d_dt2;
+      L.sync_words = ctx->d_sync;
+      L.timeout_word = ctx->d_latch + 1;
+      L.spin_cap = ctx->spin_cap;
+      tpc_thresholds(ctx->sp, L.fp32, &L.flag, &L.pivot);
+      KernelScope scope(ctx, WLSENO_KERNEL_STEP, st);
+      err = launch_persistent_step(L, st);
+      scope.done(err == cudaSuccess ? 1 : 0);
+      return err;
+    }
     if (dt >= 0.0) {  // dt < 0: the per-mesh steps already in d_dt
       int nl = 0;
       KernelScope scope(ctx, WLSENO_KERNEL_DT, st);
@@ -791,8 +1026,13 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
                                dt > 0.0 ? dt : 0.0, ctx->d_lmax, ctx->d_dt, st, &nl, ctx->d_dt2, pre);
       scope.done(nl);
       if (err != cudaSuccess) return err;
-    } else if (pre && (err = split_state(ctx, u, pre, st)) != cudaSuccess) {
+    } else if (pre && !fused && (err = split_state(ctx, u, pre, st)) != cudaSuccess) {
       return err;
+    } else if (pre && fused) {
+      KernelScope scope(ctx, WLSENO_KERNEL_DT, st);
+      err = launch_euler2_split_pairs(u, pre, ctx->dm.N, st);
+      scope.done(err == cudaSuccess ? 1 : 0);
+      if (err != cudaSuccess) return err;
     }
     // k1 = u + dt L(u);  k2 = 3/4 u + 1/4 (k1 + dt L(k1));  u <- 1/3 u + 2/3 (k2 + dt L(k2))
     double* k1 = ctx->d_k1;
@@ -802,7 +1042,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     float2* p1 = ctx->d_pair ? ctx->d_pair + CN : nullptr;
     float2* p2 = ctx->d_pair ? ctx->d_pair + 2 * CN : nullptr;
     // the pairs of u stay in the scratch slot from stage 1 on (one component)
-    float2* p0 = ctx->d_pair && ctx->scheme.n_comp == 1 ? ctx->d_pair : nullptr;
+    float2* p0 = ctx->d_pair && (ctx->scheme.n_comp == 1 || fused) ? ctx->d_pair : nullptr;
     if ((err = stage_all(ctx, u, u, 0.0, 1.0, false, k1, st, pre, p1)) != cudaSuccess ||
         (err = stage_all(ctx, k1, u, 0.75, 0.25, false, k2, st, p1, p2, p0)) != cudaSuccess ||
         (err = stage_all(ctx, k2, u, 1.0 / 3.0, 2.0 / 3.0, false, u, st, p2, nullptr, p0)) != cudaSuccess)
@@ -823,7 +1063,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
   const bool same = ctx->graph_exec && ctx->graph_u == u && ctx->graph_dt == dt &&
                     ctx->graph_cfl == cfl && ctx->graph_shape == shape_key(ctx);
   const bool use_graph = (n_steps >= 2 || (n_steps == 1 && (host || same))) && !ctx->timing &&
-                         cap == cudaStreamCaptureStatusNone;
+                         cap == cudaStreamCaptureStatusNone && !(persist && ctx->persist_no_capture);
   if (use_graph) {
     if (!same) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
@@ -841,6 +1081,16 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       e = cudaStreamEndCapture(ctx->cap_stream, &graph);
       if (ecap != cudaSuccess || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
+        if (persist) {
+          // the cooperative launch could not be captured: launch it directly
+          cudaGetLastError();
+          ctx->persist_no_capture = true;
+          ctx->launches = l0;
+          for (int k = 0; k < WLSENO_N_KERNEL_KINDS; ++k) ctx->by_kind[k] = k0[k];
+          for (int step = 0; step < n_steps; ++step)
+            if ((e = enqueue_step(s)) != cudaSuccess) return cuda_fail(ctx, e, "persistent step");
+          goto steps_done;
+        }
         return cuda_fail(ctx, ecap != cudaSuccess ? ecap : e, "capture step");
       }
       e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
@@ -869,6 +1119,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     for (int step = 0; step < n_steps; ++step)
       if ((e = enqueue_step(s)) != cudaSuccess) return cuda_fail(ctx, e, "RK step");
   }
+steps_done:
   if (dt > 0.0) ctx->mesh_dt_set = false;
   if (host) {
     e = cudaMemcpyAsync(ubar, ctx->d_in, sizeof(double) * C * N, cudaMemcpyDeviceToHost, s);
@@ -881,9 +1132,11 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read dt");
     *dt_out = v;
     ctx->last_dt = v;
+    return take_nonfinite(ctx);
   } else if (host) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rk_step");
+    return take_nonfinite(ctx);
   }
   return WLSENO_OK;
 }
@@ -901,7 +1154,7 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
   const double* u = ubar;
   if (!is_device_pointer(ubar)) {
     if (!ctx->d_in && (st = dalloc(ctx, &ctx->d_in, ctx->scheme.n_comp * N))) return st;
-    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * N, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(ctx->d_in, ubar, sizeof(double) * ctx->scheme.n_comp * N, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy ubar");
     u = ctx->d_in;
   }
@@ -924,12 +1177,13 @@ wlseno_status wlseno_autotune(wlseno_ctx* ctx, const double* ubar, int reps, voi
   }
   for (auto& sh : cands) {
     if (!shape_fits(sh[0], sh[1], ctx->host.max_n)) continue;
+    if (ctx->persistent && sh[0] != 1) continue;  // the persistent step runs thread per cell
     ctx->G = sh[0];
     ctx->R = sh[1];
     ctx->otf = sh[2] != 0;
-    e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
+    e = tune_recon(ctx, u, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = reconstruct_one(ctx, u, nullptr, ctx->d_fvals, s);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = tune_recon(ctx, u, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;
@@ -981,7 +1235,7 @@ wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host) {
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,
                                   const double* gbar_next, double* gbar_n, void* stream) {
   wlseno_status st = check_ready(ctx);
-  if (st != WLSENO_OK) return st;
+  if (st != WLSENO_OK || (st = take_nonfinite(ctx)) != WLSENO_OK) return st;
   if (!ubar_n || !gbar_next || !gbar_n) return fail(ctx, WLSENO_ERR_INVALID_ARG, "null array");
   if (dt == 0.0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint needs a fixed dt (> 0, or < 0 for per-mesh steps)");
   if (ctx->scheme.pde == WLSENO_EULER)
@@ -1086,6 +1340,7 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   if (in_host || g_host || out_host) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint");
+    return take_nonfinite(ctx);
   }
   return WLSENO_OK;
 }
@@ -1107,6 +1362,7 @@ wlseno_status wlseno_get_info(const wlseno_ctx* ctx, wlseno_info* out) {
   out->lanes_per_cell = ctx->G;
   out->rows_per_lane = ctx->R;
   out->moments_mode = ctx->otf ? 1 : 0;
+  out->persistent = ctx->persistent ? 1 : 0;
   return WLSENO_OK;
 }
 
@@ -1153,6 +1409,12 @@ wlseno_status wlseno_get_diagnostics(wlseno_ctx* ctx, wlseno_diagnostics* out) {
     if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) out->kernel_ms[t.kind] += ms;
     else cudaGetLastError();
   }
+  return WLSENO_OK;
+}
+
+wlseno_status wlseno_set_wait_limit(wlseno_ctx* ctx, int64_t max_polls) {
+  if (!ctx || max_polls < 0) return WLSENO_ERR_INVALID_ARG;
+  ctx->spin_cap = max_polls == 0 ? kDefaultSpinCap : static_cast<long long>(max_polls);
   return WLSENO_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "k_flux_cell.cuh"
 #include "wlseno_internal.h"
 
 namespace wlseno {
@@ -140,40 +141,25 @@ euler_flux_stage_kernel(DeviceMesh dm, double gamma, const double* __restrict__ 
     out[c * N + i] = res;
     finite = finite && isfinite(res);
   }
-  if (!finite) atomicAdd(&counters[2], 1ull);
+  if (!finite) report_nonfinite(dm, counters);
 }
 
 // Largest |u| + c over each mesh's cells (bits of a non-negative double).
 template <int DIM>
-__global__ void euler_speed_kernel(int64_t N, double gamma, const double* __restrict__ ubar,
-                                   const int32_t* __restrict__ mesh_of,
-                                   unsigned long long* __restrict__ lmax_bits) {
+__global__ void __launch_bounds__(256)
+euler_speed_kernel(int64_t N, double gamma, const double* __restrict__ ubar,
+                   const int32_t* __restrict__ mesh_of, unsigned long long* __restrict__ lmax_bits) {
   constexpr int C = DIM + 2;
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const bool in = i < N;
-  double s = 0.0;
-  if (in) {
+  chunked_mesh_max(N, mesh_of, lmax_bits, [&](int64_t i) {
     const double rho = ubar[i];
     double ke = 0.0;
     for (int a = 0; a < DIM; ++a) ke += ubar[(1 + a) * N + i] * ubar[(1 + a) * N + i];
     const double p = (gamma - 1.0) * (ubar[(C - 1) * N + i] - 0.5 * ke / rho);
     const double c2 = gamma * p / rho;
-    s = sqrt(ke) / rho + sqrt(c2 > 0.0 ? c2 : 0.0);
+    double s = sqrt(ke) / rho + sqrt(c2 > 0.0 ? c2 : 0.0);
     if (!(s >= 0.0)) s = INFINITY;  // a non-finite state stops the step (dt = 0)
-  }
-  const int mesh = in ? mesh_of[i] : -1;
-  unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(s));
-  const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
-  if (__all_sync(0xffffffffu, mesh == m0 || mesh < 0)) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(0xffffffffu, bits, off);
-      bits = o > bits ? o : bits;
-    }
-    if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicMax(&lmax_bits[m0], bits);
-  } else if (in) {
-    atomicMax(&lmax_bits[mesh], bits);
-  }
+    return static_cast<unsigned long long>(__double_as_longlong(s));
+  });
 }
 
 }  // namespace
@@ -218,7 +204,7 @@ cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double*
   if (dm.dim < 1 || dm.dim > 3) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(lmax_bits, 0, sizeof(unsigned long long) * n_meshes, s);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = static_cast<unsigned>((dm.N + 255) / 256);
+  const unsigned blocks = chunked_blocks(dm.N);
   if (dm.dim == 1)
     euler_speed_kernel<1><<<blocks, 256, 0, s>>>(dm.N, gamma, ubar, dm.mesh_of, lmax_bits);
   else if (dm.dim == 2)

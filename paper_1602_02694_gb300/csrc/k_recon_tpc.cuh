@@ -72,6 +72,20 @@ __device__ __forceinline__ void sqrt_free_init(SqrtFreeQR<T, M>& f) {
 }
 
 // Fold the row z (z[M] = right-hand side) with weight delta into f.
+//
+// Of the two algebraically equal updates of U -- with x = z_j before the
+// update, Gentleman's u_kj' = cbar u_kj + sbar x, or u_kj' = u_kj + sbar z_j'
+// with z_j' = x - z_k u_kj -- this is the second, which saves a multiply
+// per entry.  It leaves u_kj' an absolute rounding error of about
+// eps |u_kj| when the incoming row dominates row k (cbar small) and the new
+// entry is much smaller than the old: harmless for the solution, but where
+// a few rows of far larger weight than the others carry nearly dependent
+// moment rows (weights spanning 1e13, say), it can leave a moderate
+// diagonal where the true factor has an entry near 0, and the conditioning
+// estimates then miss the near dependence.  The FP64 kernel therefore also
+// sends every cell whose weights span more than kWeightSpread to the
+// pivoted path (the error stays below eps times the spread of the row
+// weights otherwise).
 template <typename T, int M>
 __device__ __forceinline__ void sqrt_free_fold(SqrtFreeQR<T, M>& f, T (&z)[M + 1], T delta) {
 #pragma unroll
@@ -91,6 +105,10 @@ __device__ __forceinline__ void sqrt_free_fold(SqrtFreeQR<T, M>& f, T (&z)[M + 1
   }
 }
 
+// Spread of the row weights above which the FP64 thread-per-cell kernel
+// sends a cell to the pivoted path (see sqrt_free_fold).
+constexpr double kWeightSpread = 1e6;
+
 // Spread of the column-scaled diagonal: qmax = max_k q_k^2 and qmin =
 // min_k q_k^2.  A cell is ill-conditioned at threshold K when
 // !(qmax <= K^2 qmin), which also catches a zero or non-finite diagonal.
@@ -108,6 +126,66 @@ __device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, T* q
   }
   *qmax_out = qmax;
   *qmin_out = qmin;
+}
+
+// Approximate 1/sqrt for the estimate below (the hardware approximation on
+// the device; the host-compiled tests use the library's sqrt).
+__host__ __device__ __forceinline__ float est_rsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / std::sqrt(x);
+#endif
+}
+
+// A second conditioning estimate, for the cells the spread misses (it only
+// bounds the conditioning from below, and nearly dependent columns can leave
+// every column-scaled diagonal entry moderate): the LINPACK estimate of
+// ||R_B^-1|| for the column-scaled factor R_B = D^(1/2) U diag(1/sqrt(n_k))
+// of W A S (Cline, Moler, Stewart and Wilkinson 1979): solve R_B^T z = e
+// with e_k = +-1 chosen as the solve goes to make |z_k| grow, then
+// R_B w = z, and return ||w|| / ||z|| (max norms), a lower bound on
+// ||R_B^-1|| that in practice lies within a small factor of it.  With
+// y_k = sqrt(d_k) z_k the first solve is y_k = e_k sqrt(n_k) -
+// sum_{i<k} u_ik y_i; with w = sqrt(n) v the second is the unit-triangular
+// U v = D^(-1/2) z: neither divides by U.  An estimate only decides a
+// routing threshold, so it runs in FP32 for either factor precision (a
+// diagonal entry below the FP32 range gives infinity: near singular).
+template <typename T, int M>
+__host__ __device__ __forceinline__ float sqrt_free_inverse_estimate(const SqrtFreeQR<T, M>& f) {
+  float y[M], sn[M], rd[M];
+  float zmax = 0.0f;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    T n = f.d[k];
+#pragma unroll
+    for (int i = 0; i < k; ++i) n = fma(f.d[i] * f.U[i][k], f.U[i][k], n);
+    float sk = 0.0f;
+#pragma unroll
+    for (int i = 0; i < k; ++i) sk = std::fma(static_cast<float>(f.U[i][k]), y[i], sk);
+    const float nf = static_cast<float>(n);
+    sn[k] = nf * est_rsqrt(nf);                     // sqrt(n_k)
+    rd[k] = est_rsqrt(static_cast<float>(f.d[k]));  // 1 / sqrt(d_k)
+    const float mag = sn[k] + std::fabs(sk);
+    y[k] = sk > 0.0f ? -mag : mag;
+    const float z = mag * rd[k];
+    zmax = z > zmax ? z : zmax;
+    y[k] = y[k];  // y_k = sqrt(d_k) z_k
+  }
+  // U v = D^(-1/2) z = D^(-1) y, back substitution; w = sqrt(n) v
+  float v[M];
+  float wmax = 0.0f;
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    float t = y[k] * rd[k] * rd[k];
+#pragma unroll
+    for (int c = k + 1; c < M; ++c) t = std::fma(-static_cast<float>(f.U[k][c]), v[c], t);
+    v[k] = t;
+    const float w = std::fabs(t) * sn[k];
+    wmax = w > wmax ? w : wmax;
+  }
+  const float est = wmax / zmax;
+  return est == est ? est : INFINITY;
 }
 
 // Packed position of U[k][j] (k < j < M) in a strict upper triangle.
@@ -137,7 +215,7 @@ __device__ __forceinline__ const double* tpc_points<double>(const DeviceMesh& dm
 // Weights (Sec. 3.1.2) of cell i: eps h^2 and the centre weight.
 template <typename T, int DIM>
 __device__ __forceinline__ void tpc_weights(const DeviceMesh& dm, const SchemeParams& sp,
-                                            const double* __restrict__ ubar, int64_t i, double ui,
+                                            const double* WLSENO_BODY_RESTRICT ubar, int64_t i, double ui,
                                             T* eh2, T* w_centre) {
   constexpr int NF = DIM + 1;
   const double hi = dm.h[i];
@@ -156,10 +234,11 @@ __device__ __forceinline__ void tpc_weights(const DeviceMesh& dm, const SchemePa
 }
 
 // The same weights in FP32-bulk from the FP32 pairs of ubar (no FP64 work
-// but eps h^2).
-template <int DIM>
+// but eps h^2).  The pairs of cell j sit at upair[j * C] (C > 1: the pairs of
+// all components interleaved, upair pointing at this thread's component).
+template <int DIM, int C = 1>
 __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const SchemeParams& sp,
-                                                 const float2* __restrict__ upair, int64_t i, float2 pi,
+                                                 const float2* WLSENO_BODY_RESTRICT upair, int64_t i, float2 pi,
                                                  float* eh2, float* w_centre) {
   constexpr int NF = DIM + 1;
   const double hi = dm.h[i];
@@ -169,7 +248,7 @@ __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const Sch
   for (int f = 0; f < NF; ++f) {
     const int nb = dm.nbr[i * NF + f];
     if (nb >= 0) {
-      const float2 pj = upair[nb >> 2];
+      const float2 pj = upair[static_cast<int64_t>(nb >> 2) * C];
       const float d = (pj.x - pi.x) + (pj.y - pi.y);
       bmin = fminf(bmin, d * d + e);
     }

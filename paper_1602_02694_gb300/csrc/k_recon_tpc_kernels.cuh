@@ -28,12 +28,13 @@ namespace wlseno {
 // FP64 fold: rows read from the ELL layout, row t+1 fetched while row t is
 // folded (hides the index -> ubar chain).
 template <int DIM, int M>
-__device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* __restrict__ ubar,
+__device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* WLSENO_BODY_RESTRICT ubar,
                                          int64_t i, double ui, int n, double eh2, double w_centre,
-                                         SqrtFreeQR<double, M>& f) {
+                                         SqrtFreeQR<double, M>& f, double* w_spread = nullptr) {
   const int64_t N = dm.N;
   const double* Ae = dm.A64e;
   sqrt_free_init(f);
+  double wmin = INFINITY, wmax = 0.0;
   double u_next = ubar[dm.st_ell[i]];
   double a_next[M];
 #pragma unroll
@@ -49,9 +50,12 @@ __device__ __forceinline__ void tpc_fold(const DeviceMesh& dm, const double* __r
       for (int c = 0; c < M; ++c) a_next[c] = Ae[(static_cast<int64_t>(t + 1) * M + c) * N + i];
     }
     const double w = t == 0 ? w_centre : eh2 * recip_t(fma(dev, dev, eh2));
+    wmin = fmin(wmin, w);
+    wmax = fmax(wmax, w);
     z[M] = dev;
     sqrt_free_fold(f, z, w * w);
   }
+  if (w_spread) *w_spread = wmax / wmin;  // NaN for non-finite weights: fails the caller's <= test
 }
 
 constexpr int kTpcThreads = 128;  // block size of the thread-per-cell kernels
@@ -86,8 +90,8 @@ constexpr int kLeadR = 6, kLeadU = 3;
 constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (kLeadR - kLeadU - 1);
 static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");
 
-template <int DIM, int M>
-__device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const float2* __restrict__ upair,
+template <int DIM, int M, int C = 1>
+__device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
                                                 int64_t i, float2 pi, int n, float eh2, float w_centre,
                                                 SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
@@ -104,7 +108,7 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
   };
   auto fetch_u = [&](int rec_slot, int u_slot) {
     const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][tid])[M % 4]);
-    cp_async8(&su[u_slot][tid], upair + j);
+    cp_async8(&su[u_slot][tid], upair + static_cast<int64_t>(j) * C);
   };
   sqrt_free_init(f);
   for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
@@ -148,8 +152,8 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
 // 16-byte geometry record (offset and index) kLeadR rows ahead, and the pair
 // of ubar_j with cell j's own moments kLeadU rows ahead, through the same
 // commit-group schedule.
-template <int DIM, int M>
-__device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const float2* __restrict__ upair,
+template <int DIM, int M, int C = 1>
+__device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
                                                     int64_t i, float2 pi, int n, float eh2, float w_centre,
                                                     SqrtFreeQR<float, M>& f) {
   constexpr int OW4 = own32_width(DIM, M) / 4;
@@ -172,7 +176,7 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   auto fetch_rec = [&](int t, int slot) { cp_async16(&sgeo[slot][tid], geo + static_cast<int64_t>(t) * N + i); };
   auto fetch_u = [&](int rec_slot, int u_slot) {
     const int j = __float_as_int(reinterpret_cast<const float*>(&sgeo[rec_slot][tid])[DIM]);
-    cp_async8(&su[u_slot][tid], upair + j);
+    cp_async8(&su[u_slot][tid], upair + static_cast<int64_t>(j) * C);
 #pragma unroll
     for (int k = 0; k < OW4; ++k) cp_async16(&sown[u_slot][k][tid], own + static_cast<int64_t>(j) * OW4 + k);
   };
@@ -226,11 +230,12 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
 }
 
 // Coefficients and facet values of cell i (FP32-bulk: the polynomial in FP32,
-// ubar_i added in FP64), or with fdev set the FP32 deviations ubar - ubar_i.
+// ubar_i added in FP64), or with fdev set the FP32 deviations ubar - ubar_i;
+// dev_out (may be null) also receives the deviations.
 template <typename T, int DIM, int M>
 __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
-                                          double* __restrict__ coeffs, double* __restrict__ fvals,
-                                          float* __restrict__ fdev) {
+                                          double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals,
+                                          float* WLSENO_BODY_RESTRICT fdev, T* dev_out = nullptr) {
   constexpr int NP = (DIM + 1) * nq_of(DIM);
   if (coeffs) {
 #pragma unroll
@@ -247,6 +252,7 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
     T sh = T(0);
 #pragma unroll
     for (int c = 0; c < M; ++c) sh = fma(x[c], mono[c], sh);
+    if (dev_out) dev_out[pt] = sh;
     if (fdev)
       fdev[i * NP + pt] = static_cast<float>(sh);
     else
@@ -254,41 +260,97 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
   }
 }
 
-template <typename T, int DIM, int M, bool OTF = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
-recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                 double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
-                 unsigned long long* __restrict__ counters, TpcWork work, T flag_threshold,
-                 T pivot_threshold) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= dm.N) return;
+// One thread per (cell, component): C = 1 for the scalar equations; C = 4
+// for 2-D Euler in FP32-bulk (componentwise, each component its own weights,
+// Sec. 3.1.2), the four threads of a cell adjacent in the warp so that they
+// share every row load (geometry, moments) and their state pairs are 32
+// contiguous bytes (upair interleaved [N][C]).  With C > 1 the threads of a
+// cell then take the positivity decision of the Euler traces together
+// (work.pos_ok): a cell whose reconstructed density or pressure is <= 1e-12
+// at any facet point uses its averages at all its facets (the flux kernel
+// reads the flag).  Flagged (cell, component) pairs are listed as c N + i.
+// The main kernel's work for global thread gt (one cell, or one (cell,
+// component) pair); also the reconstruction phase of the persistent step.
+template <typename T, int DIM, int M, bool OTF = false, int C = 1>
+__device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const SchemeParams& sp,
+                                               const double* WLSENO_BODY_RESTRICT ubar, double* WLSENO_BODY_RESTRICT coeffs,
+                                               double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+                                               unsigned long long* WLSENO_BODY_RESTRICT counters, const TpcWork& work,
+                                               T flag_threshold, T pivot_threshold, int64_t gt) {
+  static_assert(C == 1 || (sizeof(T) == 4 && 32 % C == 0), "components share a warp");
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
+  const int64_t i = C == 1 ? gt : gt / C;
+  const int comp = C == 1 ? 0 : static_cast<int>(gt - i * C);
+  if (i >= dm.N) return;  // the C threads of a cell leave together
   const int n = dm.st_ptr[i + 1] - dm.st_ptr[i];
+  const int64_t coff = static_cast<int64_t>(comp) * dm.N;
+  ubar += coff;
+  if (coeffs) coeffs += coff * M;
+  if (fvals) fvals += coff * NP;
+  if (fdev) fdev += coff * NP;
   const double ui = ubar[i];
   T eh2, wc;
   SqrtFreeQR<T, M> f;
+  float2 pi = make_float2(0.0f, 0.0f);
+  double w_spread = 1.0;  // FP64: spread of the row weights
   if constexpr (sizeof(T) == 4) {
-    const float2 pi = work.upair[i];
-    tpc_weights_pair<DIM>(dm, sp, work.upair, i, pi, &eh2, &wc);
+    const float2* up = work.upair + comp;
+    pi = up[i * C];
+    tpc_weights_pair<DIM, C>(dm, sp, up, i, pi, &eh2, &wc);
     if constexpr (OTF)
-      tpc_fold_staged_otf<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
+      tpc_fold_staged_otf<DIM, M, C>(dm, up, i, pi, n, eh2, wc, f);
     else
-      tpc_fold_staged<DIM, M>(dm, work.upair, i, pi, n, eh2, wc, f);
+      tpc_fold_staged<DIM, M, C>(dm, up, i, pi, n, eh2, wc, f);
   } else {
     tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
-    tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f);
+    tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f, &w_spread);
   }
   T qmax, qmin;
   sqrt_free_spread(f, &qmax, &qmin);
   T x[M];
   sqrt_free_solve(f, x);
-  tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev);
-  if (qmax <= flag_threshold * flag_threshold * qmin) return;
+  if constexpr (C > 1) {
+    T dv[NP];
+    tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev, dv);
+    // rho and p at every facet point from the C threads of the cell
+    // (conserved rho, rho u_1 .. rho u_dim, E; FP32 traces hi + (lo + dev))
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned seg = ((1u << C) - 1u) << (lane & ~static_cast<unsigned>(C - 1));
+    const float gm1 = work.gamma - 1.0f;
+    bool ok = true;
+#pragma unroll
+    for (int pt = 0; pt < NP; ++pt) {
+      const float v = pi.x + (pi.y + static_cast<float>(dv[pt]));
+      float U[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) U[c] = __shfl_sync(seg, v, c, C);
+      float ke = 0.0f;
+#pragma unroll
+      for (int a = 0; a < C - 2; ++a) ke = fmaf(U[1 + a], U[1 + a], ke);
+      const float pr = gm1 * (U[C - 1] - 0.5f * ke / U[0]);
+      ok = ok && U[0] > 1e-12f && pr > 1e-12f;
+    }
+    if (comp == 0) {
+      work.pos_ok[i] = ok ? 1 : 0;
+      if (!ok) atomicAdd(&counters[3], 1ull);
+    }
+  } else {
+    tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev);
+  }
+  // a cell is flagged when its spread passes the flag threshold or its
+  // inverse estimate passes the pivot bound (then it always takes the
+  // pivoted path); a non-finite factor fails both tests
+  const float zest = sqrt_free_inverse_estimate(f);
+  const bool near_singular = !(zest <= static_cast<float>(pivot_threshold)) || !(w_spread <= kWeightSpread);
+  if (!near_singular && qmax <= flag_threshold * flag_threshold * qmin) return;
+  const int tag = static_cast<int>(coff + i);  // (component, cell) of the lists
   if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
-  if (sizeof(T) == 4 && work.refine_buf && qmax <= pivot_threshold * pivot_threshold * qmin) {
+  if (sizeof(T) == 4 && work.refine_buf && !near_singular &&
+      qmax <= pivot_threshold * pivot_threshold * qmin) {
     // keep the FP32 factor for the refinement kernel: one contiguous record
     constexpr int RW = refine_record_floats(M);
     float v[RW];
-    v[0] = __int_as_float(static_cast<int>(i));
+    v[0] = __int_as_float(tag);
     v[1] = __int_as_float(dm.st_ptr[i]);
     v[2] = __int_as_float(n);
     v[3] = static_cast<float>(wc);
@@ -312,8 +374,18 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
 #pragma unroll
     for (int q = 0; q < RW / 4; ++q) rec[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else {
-    work.group_list[atomicAdd(&work.counts[0], 1)] = static_cast<int>(i);
+    work.group_list[atomicAdd(&work.counts[0], 1)] = tag;
   }
+}
+
+template <typename T, int DIM, int M, bool OTF = false, int C = 1>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
+                 double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+                 unsigned long long* WLSENO_BODY_RESTRICT counters, TpcWork work, T flag_threshold,
+                 T pivot_threshold) {
+  recon_tpc_cell<T, DIM, M, OTF, C>(dm, sp, ubar, coeffs, fvals, fdev, counters, work, flag_threshold,
+                                    pivot_threshold, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x);
 }
 
 // One corrected-seminormal-equations sweep on the refine-listed cells
@@ -329,20 +401,23 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar
 // the record carries the weights' eps h^2 and w_c and ubar_i); then ubar of the
 // stencil cells.  The partial sums are combined by shuffles.  It overwrites
 // the main kernel's outputs for those cells.
+// The sweep for global thread gt of nthreads (whole warps): the kernel's body
+// and the refinement phase of the persistent step.
 template <int DIM, int M, int L, int RPL>
-__global__ void __launch_bounds__(64)
-refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict__ coeffs,
-              double* __restrict__ fvals, float* __restrict__ fdev, TpcWork work) {
+__device__ __forceinline__ void refine_records(const DeviceMesh& dm, const double* WLSENO_BODY_RESTRICT ubar,
+                                               double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals,
+                                               float* WLSENO_BODY_RESTRICT fdev, const TpcWork& work, int64_t gt,
+                                               int64_t nthreads) {
   constexpr int NP = (DIM + 1) * nq_of(DIM);
   static_assert(NP <= L && M <= L, "one facet point and one coefficient per lane");
   constexpr int kPerWarp = 32 / L;
   constexpr int RW = refine_record_floats(M);
   constexpr int RE = refine_record_eps(M);
   const int lane = threadIdx.x % L;
-  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / 32;
-  const int64_t warps = gridDim.x * static_cast<int64_t>(blockDim.x) / 32;
+  const int64_t warp = gt / 32;
+  const int64_t warps = nthreads / 32;
   const int64_t sub = (threadIdx.x % 32) / L;
-  const int64_t last = dm.N - 1;  // the record buffer holds N records
+  const int64_t last = work.capacity - 1;  // the record buffer holds `capacity` records
   float r[RW];
   auto load_record = [&](int64_t slot) {
     const float4* rec = reinterpret_cast<const float4*>(work.refine_buf + (slot < last ? slot : last) * RW);
@@ -357,12 +432,16 @@ refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict
   };
   const int64_t first = warp * kPerWarp;
   load_record(first + sub);  // issued together with the list length
-  const int count = work.counts[1];
+  const int count = *reinterpret_cast<const volatile int*>(work.counts + 1);
   for (int64_t base = first; base < count; base += warps * kPerWarp) {
     if (base != first) load_record(base + sub);
     const int64_t slot = base + sub;
     const bool valid = slot < count;
-    const int64_t i = valid ? __float_as_int(r[0]) : 0;
+    // the record's tag c N + i: component c (multi-component contexts), cell i
+    const int64_t tag = valid ? __float_as_int(r[0]) : 0;
+    const int64_t comp = tag >= dm.N ? tag / dm.N : 0;
+    const int64_t i = tag - comp * dm.N;
+    const double* WLSENO_BODY_RESTRICT ubc = ubar + comp * dm.N;
     const int beg = __float_as_int(r[1]);
     const int n = valid ? __float_as_int(r[2]) : 0;
     const float wc = r[3];
@@ -417,7 +496,7 @@ refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict
     }
     double uj[RPL];
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) uj[q] = ubar[jrow[q]];
+    for (int q = 0; q < RPL; ++q) uj[q] = ubc[jrow[q]];
     double x[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) x[c] = static_cast<double>(r[4 + c]);
@@ -474,7 +553,7 @@ refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict
 #pragma unroll
       for (int c = 0; c < M; ++c)
         if (c == lane)
-          coeffs[i * M + c] = static_cast<double>(xh[c]) + static_cast<double>(dl[c]) + (c == 0 ? ui : 0.0);
+          coeffs[(comp * dm.N + i) * M + c] = static_cast<double>(xh[c]) + static_cast<double>(dl[c]) + (c == 0 ? ui : 0.0);
     }
     if (lane < NP) {
       float mono[M];
@@ -486,40 +565,49 @@ refine_kernel(DeviceMesh dm, const double* __restrict__ ubar, double* __restrict
         sl = fmaf(dl[c], mono[c], sl);
       }
       if (fdev)
-        fdev[i * NP + lane] = sh + sl;
+        fdev[(comp * dm.N + i) * NP + lane] = sh + sl;
       else
-        fvals[i * NP + lane] = ui + static_cast<double>(sh) + static_cast<double>(sl);
+        fvals[(comp * dm.N + i) * NP + lane] = ui + static_cast<double>(sh) + static_cast<double>(sl);
     }
   }
 }
 
-// Cells of the refinement sweep above this conditioning estimate take the
-// pivoted path instead (one FP32 sweep contracts the error by about
-// kappa * 2^-24).
-constexpr float kRefinePivotBound = 1e5f;
+template <int DIM, int M, int L, int RPL>
+__global__ void __launch_bounds__(64)
+refine_kernel(DeviceMesh dm, const double* WLSENO_BODY_RESTRICT ubar, double* WLSENO_BODY_RESTRICT coeffs,
+              double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev, TpcWork work) {
+  refine_records<DIM, M, L, RPL>(dm, ubar, coeffs, fvals, fdev, work,
+                                 blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x,
+                                 gridDim.x * static_cast<int64_t>(blockDim.x));
+}
 
-// The main kernel; the list lengths (work.counts[0..1]) must be zero.
-template <typename T, int DIM, int M>
+
+// The main kernel; the list lengths (work.counts[0..1]) must be zero.  C > 1:
+// all components at once (FP32-bulk 2-D Euler), ubar the [C][N] state.
+template <typename T, int DIM, int M, int C = 1>
 cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
                              const ReconOut& out, const TpcWork& work, cudaStream_t s) {
   constexpr int threads = kTpcThreads;
-  const unsigned blocks = static_cast<unsigned>((dm.N + threads - 1) / threads);
-  // FP32-bulk: refine above kappa_flag (pivot above kRefinePivotBound);
-  // FP64: take the pivoted path above 1e6
+  const unsigned blocks = static_cast<unsigned>((dm.N * C + threads - 1) / threads);
+  // thresholds: refine / pivot bounds (tpc_thresholds, capi.cpp)
   const bool f32 = sizeof(T) == 4;
-  const T flag = f32 ? static_cast<T>(sp.kappa_flag) : T(1e6);
-  const T pivot = f32 ? static_cast<T>(kRefinePivotBound) : flag;
+  double flag64 = 0.0, pivot64 = 0.0;
+  tpc_thresholds(sp, f32, &flag64, &pivot64);
+  const T pivot = static_cast<T>(pivot64);
+  const T flag = static_cast<T>(flag64);
   if (f32 && !work.upair) return cudaErrorInvalidValue;
+  if (work.capacity < dm.N * C) return cudaErrorInvalidValue;
+  if (C > 1 && !work.pos_ok) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     if (work.otf) {
       if (!dm.geo32 || !dm.own32) return cudaErrorInvalidValue;
-      recon_tpc_kernel<T, DIM, M, true><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
-                                                                  out.fdev, out.counters, work, flag, pivot);
+      recon_tpc_kernel<T, DIM, M, true, C><<<blocks, threads, 0, s>>>(
+          dm, sp, ubar, out.coeffs, out.fvals, out.fdev, out.counters, work, flag, pivot);
       return cudaGetLastError();
     }
   }
-  recon_tpc_kernel<T, DIM, M><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
-                                                        out.fdev, out.counters, work, flag, pivot);
+  recon_tpc_kernel<T, DIM, M, false, C><<<blocks, threads, 0, s>>>(dm, sp, ubar, out.coeffs, out.fvals,
+                                                                  out.fdev, out.counters, work, flag, pivot);
   return cudaGetLastError();
 }
 

@@ -210,9 +210,9 @@ constexpr size_t recon_smem_per_cell() {
 // list of the thread-per-cell kernel; in FP32-bulk it is always refined.
 template <typename T, int DIM, int M, int G, int R>
 __device__ __forceinline__ void group_reconstruct_cell(
-    const DeviceMesh& dm, const SchemeParams& sp, const double* __restrict__ ubar,
-    double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
-    unsigned long long* __restrict__ counters, unsigned char* smem_raw, int g, int gib,
+    const DeviceMesh& dm, const SchemeParams& sp, const double* WLSENO_BODY_RESTRICT ubar,
+    double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+    unsigned long long* WLSENO_BODY_RESTRICT counters, unsigned char* smem_raw, int g, int gib,
     int64_t cell, bool valid, bool listed) {
   constexpr int NF = DIM + 1;
   constexpr int NQ = nq_of(DIM);
@@ -272,13 +272,16 @@ __device__ __forceinline__ void group_reconstruct_cell(
 #pragma unroll
     for (int r = 0; r < R; ++r) st.B[r][c] *= st.inv_s[c];
   }
-  // sort the rows by decreasing norm (ties: stencil order)
+  // sort the rows by decreasing norm (ties: stencil order).  A non-finite
+  // norm sorts like a padding row (-1): the order must stay a strict total
+  // order (value, then index) so that every slot of the sorted rows and of
+  // their row indices is written
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     float s = 0.0f;
 #pragma unroll
     for (int c = 0; c < M; ++c) s += static_cast<float>(st.B[r][c]) * static_cast<float>(st.B[r][c]);
-    rn[r] = g + G * r < n ? s : -1.0f;
+    rn[r] = g + G * r < n && s <= 3.0e38f ? s : -1.0f;
   }
   int rank_of[R];
 #pragma unroll
@@ -370,7 +373,7 @@ __device__ __forceinline__ void group_reconstruct_cell(
     for (int r = 0; r < R; ++r) {
       z[r] = T(0);
       const int row = myrow[r];
-      if (flagged && row < n) {
+      if (flagged && static_cast<unsigned>(row) < static_cast<unsigned>(n)) {
         const int j = dm.st_idx[beg + row];
         const double dev = ubar[j] - ui;
         const double w = row == 0 ? sp.alpha_c * eh2d / bmind : eh2d / (dev * dev + eh2d);
@@ -432,7 +435,7 @@ __device__ __forceinline__ void group_reconstruct_cell(
       finite = finite && isfinite(val);
     }
   }
-  if (!finite) atomicAdd(&counters[2], 1ull);
+  if (!finite) report_nonfinite(dm, counters);
   if (g == 0) {
     if (st.rank < M) atomicAdd(&counters[1], 1ull);
     if (flagged && !listed) atomicAdd(&counters[0], 1ull);
@@ -441,9 +444,9 @@ __device__ __forceinline__ void group_reconstruct_cell(
 
 template <typename T, int DIM, int M, int G, int R>
 __global__ void __launch_bounds__(128)
-reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                   double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
-                   unsigned long long* __restrict__ counters) {
+reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
+                   double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+                   unsigned long long* WLSENO_BODY_RESTRICT counters) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t cell = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
   group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, smem_raw,
@@ -453,24 +456,44 @@ reconstruct_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ub
 
 // The work-listed cells of the thread-per-cell kernel (pivoted path, and in
 // FP32-bulk the refinement sweep), grid-stride over the list.
+// The listed cells for block `block` of `nblocks` (the kernel's body and the
+// pivoted phase of the persistent step); smem_raw holds
+// recon_smem_per_cell<T, M, G, R>() * (blockDim.x / G) bytes.
 template <typename T, int DIM, int M, int G, int R>
-__global__ void __launch_bounds__(128)
-reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* __restrict__ ubar,
-                        double* __restrict__ coeffs, double* __restrict__ fvals, float* __restrict__ fdev,
-                        unsigned long long* __restrict__ counters, const int* __restrict__ worklist,
-                        const int* __restrict__ wl_count) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int count = *wl_count;
+__device__ __forceinline__ void reconstruct_listed(const DeviceMesh& dm, const SchemeParams& sp,
+                                                   const double* WLSENO_BODY_RESTRICT ubar, double* WLSENO_BODY_RESTRICT coeffs,
+                                                   double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+                                                   unsigned long long* WLSENO_BODY_RESTRICT counters,
+                                                   const int* WLSENO_BODY_RESTRICT worklist, const int* WLSENO_BODY_RESTRICT wl_count,
+                                                   unsigned char* smem_raw, int64_t block, int64_t nblocks) {
+  const int count = *reinterpret_cast<const volatile int*>(wl_count);
   const int gpb = blockDim.x / G;
   const int gib = threadIdx.x / G;
-  for (int base = blockIdx.x * gpb; base < count; base += gridDim.x * gpb) {
+  for (int64_t base = block * gpb; base < count; base += nblocks * gpb) {
     __syncwarp();
     const int idx = base + gib;
     const bool valid = idx < count;
-    const int64_t cell = valid ? worklist[idx] : 0;
-    group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, smem_raw,
-                                            threadIdx.x % G, gib, cell, valid, true);
+    // list entries c N + i: component c (multi-component contexts), cell i
+    const int64_t tag = valid ? worklist[idx] : 0;
+    const int64_t comp = tag >= dm.N ? tag / dm.N : 0;
+    const int64_t cell = tag - comp * dm.N;
+    constexpr int NP = (DIM + 1) * nq_of(DIM);
+    const int64_t off = comp * dm.N;
+    group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar + off, coeffs ? coeffs + off * M : nullptr,
+                                            fvals ? fvals + off * NP : nullptr, fdev ? fdev + off * NP : nullptr,
+                                            counters, smem_raw, threadIdx.x % G, gib, cell, valid, true);
   }
+}
+
+template <typename T, int DIM, int M, int G, int R>
+__global__ void __launch_bounds__(128)
+reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
+                        double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
+                        unsigned long long* WLSENO_BODY_RESTRICT counters, const int* WLSENO_BODY_RESTRICT worklist,
+                        const int* WLSENO_BODY_RESTRICT wl_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  reconstruct_listed<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, worklist, wl_count, smem_raw,
+                                      blockIdx.x, gridDim.x);
 }
 
 template <typename T, int DIM, int M, int G, int R>
@@ -479,14 +502,12 @@ cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp
                                     const int* wl_count, cudaStream_t s) {
   constexpr int threads = 128;
   const size_t smem = recon_smem_per_cell<T, M, G, R>() * (threads / G);
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(reconstruct_list_kernel<T, DIM, M, G, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set before every launch: the attribute belongs to the current device's
+  // context, so a flag kept per process would miss a second device
+  cudaError_t e = cudaFuncSetAttribute(reconstruct_list_kernel<T, DIM, M, G, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
   // a few blocks per SM: the list is short (and usually empty)
   const int64_t groups = (dm.N * G + threads - 1) / threads;
   const unsigned blocks = static_cast<unsigned>(groups < 152 * 2 ? groups : 152 * 2);
@@ -500,14 +521,11 @@ cudaError_t launch_reconstruct_shape(const DeviceMesh& dm, const SchemeParams& s
                                      const double* ubar, const ReconOut& out, cudaStream_t s) {
   constexpr int threads = 128;
   const size_t smem = recon_smem_per_cell<T, M, G, R>() * (threads / G);
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(reconstruct_kernel<T, DIM, M, G, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set before every launch (per device, see launch_reconstruct_list)
+  cudaError_t e = cudaFuncSetAttribute(reconstruct_kernel<T, DIM, M, G, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
   const int64_t total = dm.N * G;
   const unsigned blocks = static_cast<unsigned>((total + threads - 1) / threads);
   reconstruct_kernel<T, DIM, M, G, R>

@@ -23,4 +23,9 @@ cudaError_t launch_recon_fixup_inst<float, 2, 6>(const DeviceMesh& dm, const Sch
                                    cudaStream_t s, int* launches) {
   return launch_recon_fixup<float, 2, 6>(dm, sp, ubar, out, work, s, launches);
 }
+
+cudaError_t launch_recon_euler2d(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                                 const ReconOut& out, const TpcWork& work, cudaStream_t s) {
+  return launch_recon_tpc<float, 2, 6, 4>(dm, sp, ubar, out, work, s);
+}
 }  // namespace wlseno

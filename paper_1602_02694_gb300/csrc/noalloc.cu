@@ -95,7 +95,7 @@ extern "C" wlseno_status wlseno_flux_residual_static(wlseno_ctx* ctx, const doub
     st = WLSENO_ERR_INVALID_ARG;
   } else {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = cudaMemsetAsync(v.counters, 0, 4 * sizeof(unsigned long long), s);
+    e = cudaMemsetAsync(v.counters, 0, kCounters * sizeof(unsigned long long), s);
     for (int c = 0; c < v.n_comp && e == cudaSuccess; ++c) {
       const double* u = ubar + c * v.dm.N;
       // the same facet-value format as wlseno_flux_residual (FP32 deviations

@@ -10,6 +10,14 @@
 
 #include "../../include/wlseno.h"
 
+// The pointer qualifier of the per-cell kernel bodies (k_recon_tpc*.cuh,
+// k_reconstruct.cuh, k_flux_cell.cuh): __restrict__, except in the
+// persistent step kernel, whose phases read arrays that earlier phases of
+// the same launch wrote (there the loads must stay coherent).
+#ifndef WLSENO_BODY_RESTRICT
+#define WLSENO_BODY_RESTRICT __restrict__
+#endif
+
 namespace wlseno {
 
 constexpr int kMaxDim = 3;
@@ -48,6 +56,10 @@ struct HostSetup {
   std::vector<int64_t> bal_ptr;   // [N+1]
   std::vector<int64_t> bal_idx;
 };
+
+// new_to_old order of one mesh's cells along the Hilbert curve of their
+// centroids (reorder.cpp); false on a bad vertex index.
+bool hilbert_order(const wlseno_mesh& m, std::vector<int64_t>* new_to_old);
 
 // balance_steps > 0 also collects, for every cell, the cells within that
 // many vertex-sharing steps (the balanced-stencil candidates).
@@ -104,9 +116,29 @@ struct DeviceMesh {
   float* own32;             // [N][own_width]
   int own_width;            // own32_width(dim, m)
   const FacetF32* ff32;     // [N][dim+1] FP32-bulk scalar flux coefficients (else null)
-  const float2* inv_vol2;   // [N] FP32-bulk scalar: 1/|tau| as a double-float pair (else null)
+  const float2* inv_vol2;   // [N] FP32-bulk scalar and 2-D Euler: 1/|tau| as a double-float pair (else null)
+  const float4* nf32;       // [N][dim+1] FP32-bulk 2-D Euler: owner normal (x, y, 0) and area (else null)
   int rec_width;            // round_up(m + 1, 4)
+  // the context's non-finite status word: mapped pinned host memory that a
+  // kernel sets to 1 when it writes a non-finite value (may be null)
+  unsigned int* nf_latch;
 };
+
+// Device counters of a context: flagged, rank deficient, nonfinite,
+// positivity fallbacks, balanced re-selections.
+constexpr int kCounters = 5;
+
+#ifdef __CUDACC__
+// A non-finite output: counted for the call's diagnostics and latched in the
+// host-visible status word, which the next entry point reports.
+__device__ __forceinline__ void report_nonfinite(const DeviceMesh& dm, unsigned long long* counters) {
+  atomicAdd(&counters[2], 1ull);
+  if (dm.nf_latch) {
+    *reinterpret_cast<volatile unsigned int*>(dm.nf_latch) = 1u;
+    __threadfence_system();
+  }
+}
+#endif
 
 // Width in floats of one FP32 row record (moments + index, 16-byte padded).
 __host__ __device__ constexpr int rec32_width(int m) { return (m + 1 + 3) / 4 * 4; }
@@ -134,6 +166,21 @@ cudaError_t launch_euler_char(const DeviceMesh& dm, const SchemeParams& sp, int 
                               cudaStream_t s);
 cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
                                unsigned long long* lmax_bits, int n_meshes, cudaStream_t s);
+// FP32-bulk 2-D Euler (k_euler32.cu): out = a u0 + b (u + dt L(u)) (or L(u))
+// from the FP32 trace deviations fdev [4][N][6] of the all-components
+// reconstruction, its positivity flags and the interleaved pairs pin / p0
+// ([N][4]) of u and u0; pout (may be null) receives the pairs of out.
+cudaError_t launch_euler2_flux32(const DeviceMesh& dm, double gamma, const float* fdev,
+                                 const unsigned char* pos_ok, const float2* pin, const float2* p0,
+                                 double a, double b, const float2* dt2, bool residual_only, double* out,
+                                 unsigned long long* counters, float2* pout, cudaStream_t s);
+// The interleaved FP32 pairs of the 2-D Euler state and, in the same pass,
+// the largest |u| + c per mesh (FP32, as double bits) for the CFL step.
+cudaError_t launch_euler2_speed_pairs32(const DeviceMesh& dm, double gamma, const double* u,
+                                        unsigned long long* lmax_bits, int n_meshes, float2* pairs,
+                                        cudaStream_t s);
+// pairs[i][c] = FP32 pair of u[c][i] (the four components of 2-D Euler).
+cudaError_t launch_euler2_split_pairs(const double* u, float2* pairs, int64_t N, cudaStream_t s);
 
 struct ReconOut {
   double* coeffs;           // [N][m] or null
@@ -184,6 +231,13 @@ struct TpcWork {
   // FP32-bulk main kernel: form each moment row from geo32/own32 instead of
   // streaming the stored row records
   bool otf = false;
+  // entries the group list and the refine records hold (N, or C N when the
+  // components of a multi-component context are reconstructed together)
+  int64_t capacity = 0;
+  // multi-component (2-D Euler, FP32-bulk) kernel: the per-cell positivity
+  // flags it writes (1: the traces are used, 0: the averages) and gamma
+  unsigned char* pos_ok = nullptr;
+  float gamma = 0.0f;
 };
 
 // pair[k] = (fl32(u[k]), fl32(u[k] - fl32(u[k]))) for k < n.
@@ -228,6 +282,14 @@ WLSENO_DECLARE_TPC(float, 2, 10)
 WLSENO_DECLARE_TPC(float, 3, 10)
 #undef WLSENO_DECLARE_TPC
 
+// FP32-bulk 2-D Euler, p = 3: the main kernel for all four components at once
+// (one thread per (cell, component), the state pairs work.upair interleaved
+// [N][4], ubar the [4][N] state) with the positivity flags work.pos_ok; the
+// flagged (component, cell) pairs are finished by
+// launch_recon_fixup_inst<float, 2, 6> on the same outputs.
+cudaError_t launch_recon_euler2d(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
+                                 const ReconOut& out, const TpcWork& work, cudaStream_t s);
+
 // Reconstruction for one component; one translation unit per (T, DIM, M).
 template <typename T, int DIM, int M>
 cudaError_t launch_reconstruct_inst(const DeviceMesh& dm, const SchemeParams& sp, int G, int R,
@@ -270,6 +332,42 @@ cudaError_t launch_cfl_dt_impl(const DeviceMesh& dm, const SchemeParams& sp, int
                                const double* u, const double* rmin, double cfl, double dt_fixed,
                                unsigned long long* lmax_bits, double* dt_mesh, cudaStream_t s,
                                int* launches, float2* dt2 = nullptr, float2* pairs_out = nullptr);
+
+// One TVD-RK3 step of the scalar equations as one persistent cooperative
+// kernel (k_persistent.cu): 2-D meshes, p = 3 or 4 (m = 6, 10), the
+// thread-per-cell reconstruction.
+struct PersistLaunch {
+  DeviceMesh dm;
+  SchemeParams sp;
+  bool fp32 = false, otf = false;
+  double* u = nullptr;             // [N] state, in/out
+  double* k1 = nullptr;            // [N] stage states
+  double* k2 = nullptr;
+  float2* pairs = nullptr;         // [3][N] FP32 pairs of u, k1, k2 (FP32-bulk)
+  double* fvals = nullptr;         // [N][NP] (FP64)
+  float* fdev = nullptr;           // [N][NP] (FP32-bulk)
+  unsigned long long* counters = nullptr;
+  int* group_list = nullptr;
+  int* counts = nullptr;           // [6]
+  float* refine_buf = nullptr;
+  int64_t capacity = 0;
+  int dt_mode = 0;                 // 0: CFL, 1: dt_fixed, 2: the per-mesh steps in dt_mesh
+  double cfl = 0.0, dt_fixed = 0.0;
+  float speed = 0.0f;              // advection |a|
+  int n_meshes = 1;
+  const double* rmin = nullptr;
+  unsigned long long* lmax = nullptr;
+  double* dt_mesh = nullptr;
+  float2* dt2 = nullptr;
+  unsigned int* sync_words = nullptr;  // [3]: barrier arrivals, generation, status
+  unsigned int* timeout_word = nullptr;  // host-visible (mapped) timeout word
+  long long spin_cap = 0;
+  double flag = 0.0, pivot = 0.0;
+};
+bool persistent_supported(int dim, int m);
+cudaError_t launch_persistent_step(const PersistLaunch& L, cudaStream_t s);
+// The flag and pivot thresholds of the thread-per-cell reconstruction.
+void tpc_thresholds(const SchemeParams& sp, bool f32, double* flag, double* pivot);
 
 // Work arrays of the adjoint (k_adjoint.cu).
 struct AdjointWork {

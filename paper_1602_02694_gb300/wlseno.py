@@ -35,7 +35,8 @@ class wlseno_mesh(ctypes.Structure):
 class wlseno_stencil_opts(ctypes.Structure):
     _fields_ = [("order_p", ctypes.c_int), ("ring", ctypes.c_double), ("radius_cut", ctypes.c_double),
                 ("min_rows", ctypes.c_int), ("lanes_per_cell", ctypes.c_int),
-                ("rows_per_lane", ctypes.c_int), ("moments_mode", ctypes.c_int)]
+                ("rows_per_lane", ctypes.c_int), ("moments_mode", ctypes.c_int),
+                ("reorder", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class wlseno_scheme(ctypes.Structure):
@@ -52,10 +53,10 @@ class wlseno_info(ctypes.Structure):
                 ("stencil_nnz", ctypes.c_int64), ("max_stencil", ctypes.c_int),
                 ("min_stencil", ctypes.c_int), ("quad_per_facet", ctypes.c_int),
                 ("lanes_per_cell", ctypes.c_int), ("rows_per_lane", ctypes.c_int),
-                ("moments_mode", ctypes.c_int)]
+                ("moments_mode", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
-KERNEL_KINDS = ("moments", "reconstruct", "flux", "dt", "adjoint", "fixup")
+KERNEL_KINDS = ("moments", "reconstruct", "flux", "dt", "adjoint", "fixup", "step")
 
 
 class wlseno_diagnostics(ctypes.Structure):
@@ -75,7 +76,7 @@ SIGNATURES = {
     "wlseno_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(wlseno_scheme)]),
     "wlseno_destroy": (None, [_P]),
     "wlseno_build_stencils": (_I, [_P, ctypes.POINTER(wlseno_mesh), _I,
-                                   ctypes.POINTER(wlseno_stencil_opts)]),
+                                   ctypes.POINTER(wlseno_stencil_opts), _P]),
     "wlseno_precompute_moments": (_I, [_P, _P]),
     "wlseno_reconstruct": (_I, [_P, _P, _P, _P, _P]),
     "wlseno_flux_residual": (_I, [_P, _P, _P, _P]),
@@ -86,9 +87,11 @@ SIGNATURES = {
     "wlseno_get_geometry": (_I, [_P, _P, _P, _P, _P]),
     "wlseno_get_diagnostics": (_I, [_P, ctypes.POINTER(wlseno_diagnostics)]),
     "wlseno_set_timing": (_I, [_P, _I]),
+    "wlseno_set_wait_limit": (_I, [_P, ctypes.c_int64]),
     "wlseno_autotune": (_I, [_P, _P, _I, _P, _P]),
     "wlseno_flux_residual_static": (_I, [_P, _P, _P, _P]),
     "wlseno_set_mesh_dt": (_I, [_P, _P]),
+    "wlseno_measure_fma_peak": (_I, [_I, _I, ctypes.POINTER(_D)]),
     "wlseno_status_string": (ctypes.c_char_p, [_I]),
     "wlseno_last_error_message": (ctypes.c_char_p, [_P]),
 }
@@ -110,6 +113,17 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def measure_fma_peak(device: int, precision: str) -> float:
+    """wlseno_measure_fma_peak: measured FP32 ("fp32") or FP64 ("fp64") FMA
+    throughput of the device in TFLOP/s."""
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    st = lib.wlseno_measure_fma_peak(int(device), FP64 if precision == "fp64" else FP32_BULK, ctypes.byref(out))
+    if st != 0:
+        raise WlsenoError(st, "wlseno_measure_fma_peak")
+    return out.value
 
 
 def status_string(status: int) -> str:
@@ -224,12 +238,15 @@ class Context:
 
     # -- entry points
     def build_stencils(self, meshes, order_p, ring, radius_cut=0.0, min_rows=0,
-                       lanes_per_cell=0, rows_per_lane=0, moments_mode=0):
+                       lanes_per_cell=0, rows_per_lane=0, moments_mode=0, reorder=0, persistent=0):
         """wlseno_build_stencils over one mesh or a list of meshes (objects with
         .vertices [nv][d] float64, .cells [nc][d+1] int64 and .period [d]).
         lanes_per_cell, rows_per_lane: kernel shape ((0, 0): the default);
         moments_mode: FP32-bulk thread-per-cell only, 0 stored moment rows,
-        1 rows formed on the fly.  Returns the context's info dict."""
+        1 rows formed on the fly; reorder: 1 renumbers each mesh's cells along
+        the Hilbert curve of their centroids (self.perm then holds new -> old,
+        so ubar_lib = ubar_caller[perm]); persistent: 1 runs each RK step as
+        one persistent cooperative kernel.  Returns the context's info dict."""
         if not isinstance(meshes, (list, tuple)):
             meshes = [meshes]
         arr = (wlseno_mesh * len(meshes))()
@@ -246,10 +263,12 @@ class Context:
             arr[k].cells = c.ctypes.data
             arr[k].period = p.ctypes.data
         opts = wlseno_stencil_opts(order_p, float(ring), float(radius_cut), min_rows,
-                                   lanes_per_cell, rows_per_lane, moments_mode)
+                                   lanes_per_cell, rows_per_lane, moments_mode, reorder, persistent)
         self._info = None
-        self._check(self.lib.wlseno_build_stencils(self.h, arr, len(meshes), ctypes.byref(opts)),
-                    "wlseno_build_stencils")
+        perm = np.zeros(sum(int(np.asarray(m.cells).shape[0]) for m in meshes), dtype=np.int64)
+        self._check(self.lib.wlseno_build_stencils(self.h, arr, len(meshes), ctypes.byref(opts),
+                                                   perm.ctypes.data), "wlseno_build_stencils")
+        self.perm = perm
         self._info = self.info()
         return self._info
 
@@ -369,6 +388,10 @@ class Context:
         out["positivity_fallbacks"] = d.positivity_fallbacks
         out["balanced_cells"] = d.balanced_cells
         return out
+
+    def set_wait_limit(self, max_polls=0):
+        """Poll limit of the persistent step's bounded barrier waits (0: default)."""
+        self._check(self.lib.wlseno_set_wait_limit(self.h, int(max_polls)), "wlseno_set_wait_limit")
 
     def set_timing(self, enable=True):
         self._check(self.lib.wlseno_set_timing(self.h, 1 if enable else 0), "wlseno_set_timing")

@@ -1,8 +1,8 @@
 // Test probe for the CPU suite: the library's square-root-free Givens fold
 // (csrc/k_recon_tpc.cuh: sqrt_free_init / fold / spread / solve, FP64)
 // compiled as host C++, on weighted least-squares problems read from stdin:
-// "n" then n rows of "w a_0 .. a_9 b"; prints "x x_0 .. x_9" and
-// "spread qmax qmin".  The probe supplies the host stand-in for the
+// "n" then n rows of "w a_0 .. a_9 b"; prints "x x_0 .. x_9",
+// "spread qmax qmin" and "est z" (the inverse estimate of the factor).  The probe supplies the host stand-in for the
 // correctly rounded FP64 reciprocal the fold uses on the device.
 #include <cuda_runtime.h>
 
@@ -31,6 +31,7 @@ int main() {
     std::printf("x");
     for (int c = 0; c < M; ++c) std::printf(" %.17g", x[c]);
     std::printf("\nspread %.17g %.17g\n", qmax, qmin);
+    std::printf("est %.9g\n", static_cast<double>(wlseno::sqrt_free_inverse_estimate(f)));
   }
   return 0;
 }

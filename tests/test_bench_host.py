@@ -86,3 +86,26 @@ def test_cpu_baseline_times_whole_stages(monkeypatch):
     u0 = synth.burgers_2d_initial(mesh)
     done, elapsed, k = bench._oracle_patch_worker((mesh, u0, 9, 9, 0.05, 0, None))
     assert k == 2 * 4 * 4 and done % k == 0 and done >= k and elapsed >= 0.05
+
+
+def test_euler_reference_arm_times_whole_oracle_steps():
+    """The Euler workload's oracle baseline: K timed whole RK3 steps of a
+    transmissive sub-mesh of the grid (3 cell-stages per cell and step),
+    and the sub-mesh's oracle step equals the oracle's step of that mesh."""
+    done, elapsed, cells = bench._oracle_euler_worker((48, 3, 24, 24, 0.3, 1, 2))
+    assert cells >= 8 and done == 3 * cells * 2 and elapsed > 0.0
+    done, elapsed, cells = bench._oracle_euler_worker((48, 3, 24, 24, 0.05, 0, None))
+    assert done % (3 * cells) == 0 and done >= 3 * cells and elapsed >= 0.05
+
+
+def test_euler_and_flux_algorithmic_bytes():
+    # 2-D Euler, p = 3 on the 1-ring: 13 offset records, one own-moment record
+    n, m, npts, dim = 13, 6, 6, 2
+    fly = bench.euler_recon_bytes_per_cell(n, m, npts, dim, True)
+    assert fly == 13 * 16 + 16 + 4 + 8 * 4 + 8 + 12 + 6 * 2 * 4 + 1 + 4 * 4 * 6
+    stored = bench.euler_recon_bytes_per_cell(n, m, npts, dim, False)
+    assert stored == 13 * 32 + 4 + 32 + 8 + 12 + 48 + 1 + 96
+    # scalar double-float flux: deviations, pairs of u and u0, neighbours,
+    # facet records, 1/|tau|, FP64 state and pairs written
+    assert bench.flux_bytes_per_cell(2, 6, 1, False) == 6 * 4 + 8 + 8 + 12 + 48 + 8 + 16
+    assert bench.flux_bytes_per_cell(2, 6, 4, True) == 4 * (24 + 16) + 12 + 48 + 8 + 4 * 16 + 1
