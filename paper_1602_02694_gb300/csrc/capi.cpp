@@ -1004,7 +1004,7 @@ wlseno_status wlseno_rk_step(wlseno_ctx* ctx, double* ubar, double dt, double cf
       L.dt_fixed = dt > 0.0 ? dt : 0.0;
       double sp2 = 0.0;
       for (int a = 0; a < ctx->dm.dim; ++a) sp2 += ctx->sp.vel[a] * ctx->sp.vel[a];
-      L.speed = ctx->scheme.pde == WLSENO_ADVECTION ? static_cast<float>(std::sqrt(sp2)) : 0.0f;
+      L.adv_speed = std::sqrt(sp2);  // as launch_cfl_dt_impl and the flux kernels take it
       L.n_meshes = ctx->host.n_meshes;
       L.rmin = ctx->d_rmin;
       L.lmax = dt == 0.0 && ctx->scheme.pde == WLSENO_BURGERS ? ctx->d_lmax : nullptr;

@@ -45,7 +45,8 @@ struct PersistArgs {
   int64_t capacity;
   int dt_mode;  // 0: CFL step from the state; 1: dt_fixed; 2: the per-mesh steps already in dt_mesh
   double cfl, dt_fixed;
-  float speed;  // advection |a|
+  double adv_speed;  // advection |a| (the CFL step's wave speed)
+  float speed;       // the same in FP32 (the FP32-bulk flux)
   int n_meshes;
   const double* rmin;
   unsigned long long* lmax;  // [n_meshes] (zero at launch)
@@ -123,8 +124,9 @@ __global__ void __launch_bounds__(128, 2) persistent_step_kernel(PersistArgs a) 
     // the time step of every mesh (read by the first flux phase, two
     // barriers later)
     for (int k = threadIdx.x; k < a.n_meshes; k += blockDim.x) {
-      const unsigned long long bits = reinterpret_cast<volatile unsigned long long*>(a.lmax)[k];
-      const double dt = cfl_dt_of(a.sp.pde, DIM, a.speed, bits, a.rmin[k], a.cfl,
+      // (the maxima exist for CFL steps of Burgers only: advection has |a|)
+      const unsigned long long bits = a.lmax ? reinterpret_cast<volatile unsigned long long*>(a.lmax)[k] : 0ull;
+      const double dt = cfl_dt_of(a.sp.pde, DIM, a.adv_speed, bits, a.rmin[k], a.cfl,
                                   a.dt_mode == 1 ? a.dt_fixed : 0.0);
       a.dt_mesh[k] = dt;
       if (a.dt2) {
@@ -214,7 +216,8 @@ cudaError_t launch_persistent_step(const PersistLaunch& L, cudaStream_t s) {
   a.dt_mode = L.dt_mode;
   a.cfl = L.cfl;
   a.dt_fixed = L.dt_fixed;
-  a.speed = L.speed;
+  a.speed = static_cast<float>(L.adv_speed);
+  a.adv_speed = L.adv_speed;
   a.n_meshes = L.n_meshes;
   a.rmin = L.rmin;
   a.lmax = L.lmax;

@@ -353,7 +353,7 @@ struct PersistLaunch {
   int64_t capacity = 0;
   int dt_mode = 0;                 // 0: CFL, 1: dt_fixed, 2: the per-mesh steps in dt_mesh
   double cfl = 0.0, dt_fixed = 0.0;
-  float speed = 0.0f;              // advection |a|
+  double adv_speed = 0.0;          // advection |a|
   int n_meshes = 1;
   const double* rmin = nullptr;
   unsigned long long* lmax = nullptr;
