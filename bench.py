@@ -80,6 +80,14 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="",
                     help="comma-separated workloads besides the headline (default: all)")
+    ap.add_argument("--profile-workload", default="",
+                    help="profiling run instead of the benchmark: this workload (euler1024, burgers256, "
+                         "advection3d64, ...) on an n x n (n^3) mesh of --profile-n, one warm-up step and "
+                         "--steps steps as separate launches (the library's timing mode), for ncu")
+    ap.add_argument("--profile-n", type=int, default=0, help="mesh size of --profile-workload")
+    ap.add_argument("--profile-moments", type=int, default=1, choices=[0, 1],
+                    help="FP32 moment rows stored (0) or formed on the fly (1) in --profile-workload")
+    ap.add_argument("--profile-precision", default="fp32_bulk", choices=["fp32_bulk", "fp64"])
     ap.add_argument("--shape", default="auto",
                     help="reconstruction kernel shape 'lanes,rows' (1,0 = thread per cell); "
                          "default: the autotuner picks the shape and the moments mode")
@@ -884,8 +892,53 @@ def measure_workload(torch, wl, steps, warmup, dist, peaks, dev, shape, sampler=
     return res
 
 
+def profile_run(args):
+    """The step of one workload as separate kernel launches (no graph): a
+    warm-up step, then --steps steps; prints the per-kind mean launch times."""
+    import torch
+    from paper_1602_02694_gb300.wlseno import Context
+    name, n = args.profile_workload, args.profile_n
+    if name.startswith("euler"):
+        mesh = synth.tri_mesh(n or 1024, jitter=JITTER, seed=SEED, periodic=False)
+        u0, _ = synth.euler_quadrant_initial(mesh, seed=3)
+        scheme, build = {"pde": "euler"}, {"order_p": 3, "ring": 1.0}
+    elif name.startswith("burgers"):
+        mesh = synth.tri_mesh(n or N_SIDE, jitter=JITTER, seed=SEED)
+        u0 = synth.burgers_2d_initial(mesh)
+        scheme, build = {"pde": "burgers"}, {"order_p": P_ORDER, "ring": RING}
+    elif name.startswith("advection3d"):
+        mesh = synth.tet_mesh(n or 64, jitter=0.15, seed=SEED)
+        u0 = tet_initial(mesh)
+        scheme = {"pde": "advection", "velocity": (1.0, 0.5, 0.25)}
+        build = {"order_p": 3, "ring": 2.0 / 3.0, "radius_cut": 0.95}
+    else:
+        raise SystemExit(f"unknown profiling workload {name}")
+    torch.cuda.set_device(0)
+    prec = args.profile_precision
+    ctx = Context(0, precision=prec, **scheme)
+    ctx.build_stencils(mesh, lanes_per_cell=1, rows_per_lane=0,
+                       moments_mode=args.profile_moments if prec == "fp32_bulk" else 0, **build)
+    ctx.precompute_moments()
+    u = torch.tensor(u0, device="cuda").contiguous()
+    ctx.set_timing(True)
+    ctx.rk_step(u, cfl=CFL, n_steps=1)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.rk_step(u, cfl=CFL, n_steps=max(1, args.steps))
+    torch.cuda.synchronize()
+    d = ctx.diagnostics()
+    print(json.dumps({"profile": name, "cells": int(u.shape[-1]), "precision": prec,
+                      "mean_launch_us": {k: 1e3 * d["kernel_ms"][k] / d["launches_by_kind"][k]
+                                         for k in d["kernel_ms"] if d["launches_by_kind"][k]},
+                      "launches": {k: v for k, v in d["launches_by_kind"].items() if v}}))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.profile_workload:
+        return profile_run(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -941,7 +994,7 @@ def main():
         # amplify rounding by themselves: their precisions are compared over
         # the horizon in which that growth stays below about 1e3 (the design
         # notes give the measured rates)
-        horizons = {"burgers256": (3, 20), "advection3d64": (3, 30, 60)}.get(name)
+        horizons = {"burgers256": (3, 20), "advection3d64": (3, 30, 50)}.get(name)
         res = measure_workload(torch, w, w.default_steps, args.warmup, dist, peaks, dev, args.shape,
                                horizons=horizons)
         res.pop("_r32")

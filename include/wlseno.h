@@ -377,8 +377,8 @@ wlseno_status wlseno_set_mesh_dt(wlseno_ctx* ctx, const double* dt_host);
  * recomputed.  dt: > 0 fixed for every mesh, < 0 the per-mesh steps of
  * wlseno_set_mesh_dt (0 is rejected: a CFL step is not differentiated).
  * All arrays [n_cells] (n_comp = 1), host or device; the first call
- * allocates the adjoint's work arrays.  Scalar equations on 2-D and 3-D
- * meshes with fixed stencils (balanced = 0), else INVALID_ARG.  A call with
+ * allocates the adjoint's work arrays.  FP64 contexts, scalar equations on
+ * 2-D and 3-D meshes with fixed stencils (balanced = 0), else INVALID_ARG.  A call with
  * dt > 0 discards the steps of wlseno_set_mesh_dt, as in wlseno_rk_step.
  * Errors: STATE, INVALID_ARG, CUDA, NUMERIC. */
 wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double dt,

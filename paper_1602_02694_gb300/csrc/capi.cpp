@@ -1240,6 +1240,10 @@ wlseno_status wlseno_step_adjoint(wlseno_ctx* ctx, const double* ubar_n, double 
   if (dt == 0.0) return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint needs a fixed dt (> 0, or < 0 for per-mesh steps)");
   if (ctx->scheme.pde == WLSENO_EULER)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for the scalar equations");
+  if (ctx->scheme.precision != WLSENO_FP64)
+    return fail(ctx, WLSENO_ERR_INVALID_ARG,
+                "the adjoint is built for FP64 contexts (its VJP would not be the derivative of the "
+                "FP32-bulk step it recomputes)");
   if (ctx->dm.dim == 1)
     return fail(ctx, WLSENO_ERR_INVALID_ARG, "the adjoint is built for 2-D and 3-D meshes");
   if (ctx->scheme.balanced)

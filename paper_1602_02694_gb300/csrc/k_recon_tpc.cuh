@@ -120,7 +120,8 @@ __device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, T* q
     T n = f.d[k];
 #pragma unroll
     for (int i = 0; i < k; ++i) n = fma(f.d[i] * f.U[i][k], f.U[i][k], n);
-    const T q = f.d[k] / n;
+    // (FP32: the hardware reciprocal, ample for a threshold test)
+    const T q = sizeof(T) == 4 ? f.d[k] * recip_t<T>(n) : f.d[k] / n;
     qmax = q > qmax ? q : qmax;
     qmin = q < qmin ? q : qmin;
   }

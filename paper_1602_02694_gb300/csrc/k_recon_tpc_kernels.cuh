@@ -90,10 +90,12 @@ constexpr int kLeadR = 6, kLeadU = 3;
 constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (kLeadR - kLeadU - 1);
 static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");
 
-template <int DIM, int M, int C = 1>
+// weights(&eh2, &w_centre) computes the cell's weights; it runs after the
+// first record copies are issued, so its gathers overlap them.
+template <int DIM, int M, int C = 1, typename WFn>
 __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
-                                                int64_t i, float2 pi, int n, float eh2, float w_centre,
-                                                SqrtFreeQR<float, M>& f) {
+                                                int64_t i, float2 pi, int n, WFn&& weights, float* eh2_out,
+                                                float* wc_out, SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
   constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
   __shared__ float4 srec[kRec][W4][kTpcThreads];
@@ -113,6 +115,10 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
   sqrt_free_init(f);
   for (int t = 0; t < kLeadR && t < n; ++t) fetch_rec(t, t);
   cp_async_commit();
+  float eh2, w_centre;
+  weights(&eh2, &w_centre);
+  *eh2_out = eh2;
+  *wc_out = w_centre;
   cp_async_wait<0>();
   for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
@@ -152,10 +158,10 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
 // 16-byte geometry record (offset and index) kLeadR rows ahead, and the pair
 // of ubar_j with cell j's own moments kLeadU rows ahead, through the same
 // commit-group schedule.
-template <int DIM, int M, int C = 1>
+template <int DIM, int M, int C = 1, typename WFn>
 __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
-                                                    int64_t i, float2 pi, int n, float eh2, float w_centre,
-                                                    SqrtFreeQR<float, M>& f) {
+                                                    int64_t i, float2 pi, int n, WFn&& weights, float* eh2_out,
+                                                    float* wc_out, SqrtFreeQR<float, M>& f) {
   constexpr int OW4 = own32_width(DIM, M) / 4;
   // the 16-byte geometry records allow a deeper lead than the stored rows
   constexpr int kLeadRo = 7, kRec = kLeadRo + 1, kU = kLeadU + 1, kUnrollO = 8;
@@ -183,6 +189,10 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   sqrt_free_init(f);
   for (int t = 0; t < kLeadRo && t < n; ++t) fetch_rec(t, t);
   cp_async_commit();
+  float eh2, w_centre;
+  weights(&eh2, &w_centre);
+  *eh2_out = eh2;
+  *wc_out = w_centre;
   cp_async_wait<0>();
   for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
@@ -288,20 +298,22 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
   if (coeffs) coeffs += coff * M;
   if (fvals) fvals += coff * NP;
   if (fdev) fdev += coff * NP;
-  const double ui = ubar[i];
   T eh2, wc;
   SqrtFreeQR<T, M> f;
   float2 pi = make_float2(0.0f, 0.0f);
   double w_spread = 1.0;  // FP64: spread of the row weights
+  double ui;
   if constexpr (sizeof(T) == 4) {
     const float2* up = work.upair + comp;
     pi = up[i * C];
-    tpc_weights_pair<DIM, C>(dm, sp, up, i, pi, &eh2, &wc);
+    auto wfn = [&](float* e, float* w) { tpc_weights_pair<DIM, C>(dm, sp, up, i, pi, e, w); };
     if constexpr (OTF)
-      tpc_fold_staged_otf<DIM, M, C>(dm, up, i, pi, n, eh2, wc, f);
+      tpc_fold_staged_otf<DIM, M, C>(dm, up, i, pi, n, wfn, &eh2, &wc, f);
     else
-      tpc_fold_staged<DIM, M, C>(dm, up, i, pi, n, eh2, wc, f);
+      tpc_fold_staged<DIM, M, C>(dm, up, i, pi, n, wfn, &eh2, &wc, f);
+    ui = ubar[i];  // needed by the outputs only (after the fold)
   } else {
+    ui = ubar[i];
     tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
     tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f, &w_spread);
   }
@@ -327,7 +339,7 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
       float ke = 0.0f;
 #pragma unroll
       for (int a = 0; a < C - 2; ++a) ke = fmaf(U[1 + a], U[1 + a], ke);
-      const float pr = gm1 * (U[C - 1] - 0.5f * ke / U[0]);
+      const float pr = gm1 * (U[C - 1] - 0.5f * ke * recip_t(U[0]));  // a threshold test
       ok = ok && U[0] > 1e-12f && pr > 1e-12f;
     }
     if (comp == 0) {

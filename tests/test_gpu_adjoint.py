@@ -127,3 +127,18 @@ def test_checkpoint_spacing_does_not_change_the_gradient(dev):
     for gk in grads[1:]:
         assert torch.equal(gk, grads[0])
     ctx.close()
+
+
+def test_adjoint_refuses_fp32_bulk_contexts(dev):
+    """The adjoint is the derivative of the FP64 step: an FP32-bulk context
+    gets INVALID_ARG with a message instead of a VJP of another step."""
+    from paper_1602_02694_gb300.wlseno import WlsenoError
+    mesh = synth.tri_mesh(6, seed=21)
+    u = torch.tensor(synth.burgers_2d_initial(mesh), device=dev)
+    ctx = Context(pde="burgers", precision="fp32_bulk")
+    ctx.build_stencils(mesh, order_p=3, ring=1.0)
+    ctx.precompute_moments()
+    with pytest.raises(WlsenoError) as ei:
+        ctx.step_adjoint(u, 1e-3, torch.ones_like(u), torch.empty_like(u))
+    assert ei.value.status == -1 and "FP64" in str(ei.value)
+    ctx.close()
