@@ -726,6 +726,17 @@ wlseno_status wlseno_build_stencils(wlseno_ctx* ctx, const wlseno_mesh* meshes, 
   dm.inv_vol2 = nullptr;
   dm.nf_latch = ctx->d_latch;
   dm.nf32 = nullptr;
+  dm.hscale32 = nullptr;
+  if (ctx->scheme.precision == WLSENO_FP32_BULK) {
+    std::vector<float2> hs(static_cast<size_t>(N));
+    for (int64_t i = 0; i < N; ++i) {
+      const double hh = H.h[i];
+      hs[i] = make_float2(static_cast<float>(ctx->sp.eps * hh * hh), static_cast<float>(1.0 / hh));
+    }
+    float2* d_hs = nullptr;
+    if ((st = upload(ctx, &d_hs, hs))) return st;
+    dm.hscale32 = d_hs;
+  }
   ctx->euler32 = ctx->scheme.precision == WLSENO_FP32_BULK && ctx->scheme.pde == WLSENO_EULER &&
                  !ctx->scheme.characteristic && H.dim == 2 && H.m == 6;
   if (ctx->euler32) {

@@ -44,7 +44,7 @@ __device__ __forceinline__ void euler2_state(const float (&U)[kC], float nx, flo
   *speed = fabsf(un) + sqrtf(c2 > 0.0f ? c2 : 0.0f);
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
                      const unsigned char* __restrict__ pos_ok, const float2* __restrict__ pin,
                      const float2* __restrict__ p0, dfloat a, dfloat b, const float2* __restrict__ dt2,

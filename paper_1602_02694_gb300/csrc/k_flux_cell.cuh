@@ -374,15 +374,27 @@ __device__ __forceinline__ void chunked_mesh_max(int64_t N, const int32_t* WLSEN
   const int64_t end = begin + chunk < N ? begin + chunk : N;
   int cur = -1;
   unsigned long long mx = 0ull;
-  for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-    const int m = mesh_of[i];
-    if (m != cur) {
-      if (cur >= 0) atomicMax(&lmax[cur], mx);
-      cur = m;
-      mx = 0ull;
+  // four cells per pass, their loads issued together
+  constexpr int kU = 4;
+  for (int64_t i0 = begin + threadIdx.x; i0 < end; i0 += kU * static_cast<int64_t>(blockDim.x)) {
+    unsigned long long b[kU];
+    int m[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + u * static_cast<int64_t>(blockDim.x);
+      m[u] = i < end ? mesh_of[i] : -1;
+      b[u] = i < end ? value_of(i) : 0ull;
     }
-    const unsigned long long b = value_of(i);
-    mx = b > mx ? b : mx;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (m[u] < 0) continue;
+      if (m[u] != cur) {
+        if (cur >= 0) atomicMax(&lmax[cur], mx);
+        cur = m[u];
+        mx = 0ull;
+      }
+      mx = b[u] > mx ? b[u] : mx;
+    }
   }
   if (threadIdx.x == 0) m0 = cur;
   __syncthreads();

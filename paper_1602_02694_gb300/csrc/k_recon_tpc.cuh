@@ -242,8 +242,8 @@ __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const Sch
                                                  const float2* WLSENO_BODY_RESTRICT upair, int64_t i, float2 pi,
                                                  float* eh2, float* w_centre) {
   constexpr int NF = DIM + 1;
-  const double hi = dm.h[i];
-  const float e = static_cast<float>(sp.eps * hi * hi);
+  // eps h_i^2 rounded to FP32 on the host (no FP64 arithmetic here)
+  const float e = dm.hscale32 ? dm.hscale32[i].x : static_cast<float>(sp.eps * dm.h[i] * dm.h[i]);
   float bmin = INFINITY;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {

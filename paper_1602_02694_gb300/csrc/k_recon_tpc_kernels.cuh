@@ -176,7 +176,7 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   const float4* own = reinterpret_cast<const float4*>(dm.own32);
   float hp[5];
   hp[0] = 1.0f;
-  hp[1] = static_cast<float>(1.0 / dm.h[i]);
+  hp[1] = dm.hscale32 ? dm.hscale32[i].y : static_cast<float>(1.0 / dm.h[i]);  // 1/h_i (FP32, from the host)
 #pragma unroll
   for (int k = 2; k < 5; ++k) hp[k] = hp[k - 1] * hp[1];
   auto fetch_rec = [&](int t, int slot) { cp_async16(&sgeo[slot][tid], geo + static_cast<int64_t>(t) * N + i); };

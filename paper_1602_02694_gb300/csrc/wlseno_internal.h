@@ -118,6 +118,9 @@ struct DeviceMesh {
   const FacetF32* ff32;     // [N][dim+1] FP32-bulk scalar flux coefficients (else null)
   const float2* inv_vol2;   // [N] FP32-bulk scalar and 2-D Euler: 1/|tau| as a double-float pair (else null)
   const float4* nf32;       // [N][dim+1] FP32-bulk 2-D Euler: owner normal (x, y, 0) and area (else null)
+  // [N] FP32-bulk: (eps h_i^2, 1/h_i), each computed in FP64 and rounded to
+  // FP32 on the host, so the FP32 kernels need no FP64 arithmetic (else null)
+  const float2* hscale32;
   int rec_width;            // round_up(m + 1, 4)
   // the context's non-finite status word: mapped pinned host memory that a
   // kernel sets to 1 when it writes a non-finite value (may be null)
