@@ -245,8 +245,39 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
 template <typename T, int DIM, int M>
 __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
                                           double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals,
-                                          float* WLSENO_BODY_RESTRICT fdev, T* dev_out = nullptr) {
+                                          float* WLSENO_BODY_RESTRICT fdev, T* dev_out = nullptr);
+
+// The FP32-deviation output alone (no coefficients): with the FP64 output
+// path compiled out, no FP64 instruction is predicated into the FP32 kernel.
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_write_dev(const DeviceMesh& dm, int64_t i, const T (&x)[M],
+                                              float* WLSENO_BODY_RESTRICT fdev, T* dev_out) {
   constexpr int NP = (DIM + 1) * nq_of(DIM);
+  const T* P = tpc_points<T>(dm) + i * NP * DIM;
+#pragma unroll
+  for (int pt = 0; pt < NP; ++pt) {
+    T yy[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) yy[a] = P[pt * DIM + a];
+    T mono[M];
+    eval_monomials<T, DIM, M>(yy, mono);
+    T sh = T(0);
+#pragma unroll
+    for (int c = 0; c < M; ++c) sh = fma(x[c], mono[c], sh);
+    if (dev_out) dev_out[pt] = sh;
+    fdev[i * NP + pt] = static_cast<float>(sh);
+  }
+}
+
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, double ui, const T (&x)[M],
+                                          double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals,
+                                          float* WLSENO_BODY_RESTRICT fdev, T* dev_out) {
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
+  if (fdev && !coeffs) {
+    tpc_write_dev<T, DIM, M>(dm, i, x, fdev, dev_out);
+    return;
+  }
   if (coeffs) {
 #pragma unroll
     for (int c = 0; c < M; ++c) coeffs[i * M + c] = static_cast<double>(x[c]) + (c == 0 ? ui : 0.0);
@@ -391,7 +422,7 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
 }
 
 template <typename T, int DIM, int M, bool OTF = false, int C = 1>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (C > 1 ? 5 : 4) : 1)
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
                  double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
                  unsigned long long* WLSENO_BODY_RESTRICT counters, TpcWork work, T flag_threshold,

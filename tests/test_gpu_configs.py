@@ -444,3 +444,109 @@ def test_burgers_fp32_bulk_tolerance_over_the_stable_horizon(dev):
     e64 = rel(states["fp64"][1], exact)
     e32 = rel(states["fp32_bulk"][1], exact)
     assert abs(e32 - e64) <= 0.01 * e64, (e32, e64)
+
+
+def test_euler_config3_full_run_fp32_bulk_within_tolerance(dev):
+    """The 2-D Euler workload's whole run: 200 CFL-0.3 steps on the 1024 x
+    1024 mesh in both precisions; FP32-bulk within relative L1 1e-5 of FP64
+    (observed 9e-8), every state finite and positive."""
+    mesh, U = euler_problem(1024)
+    out = {}
+    for precision in ("fp64", "fp32_bulk"):
+        ctx = Context(pde="euler", precision=precision)
+        ctx.build_stencils(mesh, order_p=3, ring=1.0)
+        ctx.precompute_moments()
+        u = torch.tensor(U, device=dev).contiguous()
+        ctx.rk_step(u, cfl=0.3, n_steps=200)
+        assert ctx.diagnostics()["nonfinite"] == 0
+        a = u.cpu().numpy()
+        rho = a[0]
+        p = 0.4 * (a[3] - 0.5 * (a[1] ** 2 + a[2] ** 2) / rho)
+        assert np.all(rho > 0) and np.all(p > 0)
+        out[precision] = a
+        ctx.close()
+    a, b = out["fp32_bulk"], out["fp64"]
+    assert np.sum(np.abs(a - b)) / np.sum(np.abs(b)) <= 1e-5
+
+
+def test_config4_residual_and_steps_match_oracle(dev):
+    """3-D advection on a 5^3 Kuhn mesh (750 tetrahedra, the workload's
+    stencils): the FP64 residual of every cell and two CFL-0.3 steps against
+    the oracle (1e-10), FP32-bulk within relative L1 1e-5."""
+    mesh = synth.tet_mesh(5, jitter=0.15, seed=1)
+    ubar = tet_initial(mesh)
+    vel = (1.0, 0.5, 0.25)
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=2.0 / 3.0, velocity=vel,
+                     radius_cut=RADIUS_CUT_3D)
+    ref = O.residual(prob, ubar)
+    ref2, dts = O.rk3_run(prob, ubar, 2, cfl=0.3)
+    for precision in ("fp64", "fp32_bulk"):
+        ctx = Context(pde="advection", velocity=vel, precision=precision)
+        ctx.build_stencils(mesh, order_p=3, ring=2.0 / 3.0, radius_cut=RADIUS_CUT_3D)
+        ctx.precompute_moments()
+        u = torch.tensor(ubar, device=dev)
+        L = torch.empty_like(u)
+        ctx.flux_residual(u, L)
+        got = L.cpu().numpy()
+        dt = None
+        for _ in range(2):
+            dt = ctx.rk_step(u, cfl=0.3, n_steps=1, want_dt=True)
+        got2 = u.cpu().numpy()
+        if precision == "fp64":
+            assert float(np.max(np.abs(got - ref))) <= TOL64 * max(1.0, float(np.max(np.abs(ref))))
+            assert abs(dt - dts[-1]) <= 1e-14 * dt
+            assert float(np.max(np.abs(got2 - ref2))) <= TOL64
+        else:
+            assert np.sum(np.abs(got - ref)) / np.sum(np.abs(ref)) <= 1e-5
+            assert np.sum(np.abs(got2 - ref2)) / np.sum(np.abs(ref2)) <= 1e-5
+        ctx.close()
+
+
+def test_config4_fp32_bulk_over_the_stable_horizon(dev):
+    """The full 64^3 3-D advection workload, 50 CFL-0.3 steps in both
+    precisions: FP32-bulk within relative L1 1e-5 of FP64 (the 3-D p = 3
+    scheme amplifies rounding by itself, about e-fold per 7 steps later on),
+    and exact conservation."""
+    mesh = synth.tet_mesh(64, jitter=0.15, seed=1)
+    ubar = tet_initial(mesh, k=2)
+    vel = (1.0, 0.5, 0.25)
+    out = {}
+    for precision in ("fp64", "fp32_bulk"):
+        ctx = Context(pde="advection", velocity=vel, precision=precision)
+        ctx.build_stencils(mesh, order_p=3, ring=2.0 / 3.0, radius_cut=RADIUS_CUT_3D)
+        ctx.precompute_moments()
+        vol = ctx.geometry()["volume"]
+        u = torch.tensor(ubar, device=dev)
+        ctx.rk_step(u, cfl=0.3, n_steps=50)
+        out[precision] = u.cpu().numpy()
+        drift = abs(np.sum(vol * out[precision]) - np.sum(vol * ubar)) / np.sum(vol * np.abs(ubar))
+        assert drift <= 1e-12, (precision, drift)
+        ctx.close()
+    a, b = out["fp32_bulk"], out["fp64"]
+    assert np.sum(np.abs(a - b)) / np.sum(np.abs(b)) <= 1e-5
+
+
+@pytest.mark.parametrize("jitter,low", [(0.2, 1.7), (0.0, 2.6)])
+def test_advection_2d_observed_order(dev, jitter, low):
+    """Sec. 5.2.1: quadratic WLS-ENO (p = 3) on the 2-D wave equation
+    u_t + u_x + u_y = 0 with smooth data converges at second order on
+    jittered unstructured meshes and one order higher on uniform ones.
+    FP64 runs to t = 0.1 at dt = 0.1 h on 32^2, 64^2, 128^2; error of the
+    cell averages against the exact translated solution."""
+    errs = []
+    for n in (32, 64, 128):
+        mesh = synth.tri_mesh(n, jitter=jitter, seed=1)
+        f0 = lambda P, t=0.0: np.sin(2 * np.pi * (P[:, 0] - t)) * np.cos(2 * np.pi * (P[:, 1] - t))
+        u0 = synth.cell_averages(mesh, f0, k=6)
+        steps = n
+        dt = 0.1 / steps
+        exact = synth.cell_averages(mesh, lambda P: f0(P, dt * steps), k=6)
+        ctx = Context(pde="advection", velocity=(1.0, 1.0, 0.0))
+        ctx.build_stencils(mesh, order_p=3, ring=1.0)
+        ctx.precompute_moments()
+        u = torch.tensor(u0, device=dev)
+        ctx.rk_step(u, dt=dt, n_steps=steps)
+        errs.append(float(np.mean(np.abs(u.cpu().numpy() - exact))))
+        ctx.close()
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert orders[-1] >= low, (errs, orders)

@@ -36,7 +36,8 @@ def case_data(kind):
         mesh = synth.periodic_line_mesh(40, jitter=0.2, seed=2)
         x = mesh.cell_coords.mean(axis=1)[:, 0]
         data = [np.sin(2 * np.pi * x), 0.3 + (x > 0.5)]
-        return mesh, data, {"p": 5, "ring": 3.0}, {"order_p": 5, "ring": 3.0}
+        # the seven-cell stencil of Sec. 4.2 (no growth to ceil(1.5 m) rows)
+        return mesh, data, {"p": 5, "ring": 3.0}, {"order_p": 5, "ring": 3.0, "min_rows": 7}
     if kind == "3d":
         mesh = synth.tet_mesh(4, jitter=0.15, seed=1)
         c = mesh.cell_coords.mean(axis=1)
