@@ -684,7 +684,7 @@ def roofline(wl, info, diag, precision, peaks):
     hbm = nbytes / dur / 1e9
     name = f"{kind} kernel ({precision}{', all components' if fused and kind == 'reconstruct' else ''}" \
            f"{', moments on the fly' if otf and kind == 'reconstruct' else ''}), per launch"
-    traffic = TRAFFIC_PER_LAUNCH.get((wl.name, precision, kind, otf))
+    traffic = traffic_per_launch(wl.name, precision, kind, otf, N)
     out_alu = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
                "frac": alu / alu_peak if alu_peak else None, "traffic": traffic, "kernel": name,
                "flops_per_launch": flops, "launch_us": dur * 1e6,
@@ -698,10 +698,48 @@ def roofline(wl, info, diag, precision, peaks):
     return out_hbm, out_alu
 
 
-# DRAM bytes (read + write) per launch of a workload's dominant kernel from
-# one ncu capture of the current kernel, keyed by (workload, precision,
-# kind, moments on the fly); None where no capture of it exists.
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per cell of one launch of a workload's dominant
+# kernel, from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum,
+# cold L2) of the kernels built from the sources whose digest is
+# TRAFFIC_SOURCES_DIGEST, keyed by (workload, precision, kind, moments on the
+# fly), with the mesh the capture ran on.  A launch's traffic grows in
+# proportion to its cells (every cell streams its own records), so the figure
+# is scaled to the workload's cell count.  Once the kernel sources change the
+# counters no longer describe the kernel and the traffic is reported as null.
+TRAFFIC_SOURCES_DIGEST = "7c95869cfbea"
+TRAFFIC_BYTES_PER_CELL = {
+    ("euler1024", "fp32_bulk", "reconstruct", False): (623.04, "512x512 triangles, 2 launches"),
+    ("euler1024", "fp64", "reconstruct", False): (842.01, "512x512 triangles, 4 launches"),
+    ("burgers256", "fp32_bulk", "reconstruct", True): (731.40, "256x256 triangles, 1 launch"),
+    ("burgers256", "fp32_bulk", "reconstruct", False): (1895.69, "256x256 triangles, 1 launch"),
+    ("burgers256", "fp64", "reconstruct", False): (3290.41, "256x256 triangles, 1 launch"),
+    ("advection3d64", "fp32_bulk", "reconstruct", True): (976.33, "32^3 Kuhn tetrahedra, 1 launch"),
+    ("advection3d64", "fp32_bulk", "reconstruct", False): (2326.09, "32^3 Kuhn tetrahedra, 1 launch"),
+    ("advection3d64", "fp64", "reconstruct", False): (4295.59, "32^3 Kuhn tetrahedra, 1 launch"),
+}
+
+
+def kernel_sources_digest():
+    """First 12 hex digits of the SHA-256 over the library's CUDA/C++
+    sources (sorted by name), which identifies the kernels a traffic
+    capture describes."""
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1602_02694_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_per_launch(workload, precision, kind, otf, n_cells):
+    """Measured DRAM bytes of one launch scaled to n_cells, or None."""
+    entry = TRAFFIC_BYTES_PER_CELL.get((workload, precision, kind, otf))
+    if entry is None or kernel_sources_digest() != TRAFFIC_SOURCES_DIGEST:
+        return None
+    return entry[0] * n_cells
 
 
 def burgers_exact_averages(mesh, t):

@@ -74,21 +74,32 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(kPending) : "memory");
 }
 
-// FP32 fold with the rows staged through shared memory.  Each thread copies
-// its own rows asynchronously: the row record (moments + stencil index) kLeadR
-// rows ahead, and the FP32 pair of ubar_j kLeadU rows ahead (its index read from the staged
-// record), so neither the HBM latency of the records nor the record -> index
-// -> ubar chain stalls the rotations, and no prefetched row occupies
-// registers.  Commit groups: one per iteration t, holding ubar of row t+kLeadU
-// and the record of row t+kLeadR.  Iteration t needs the groups of iterations
-// t-kLeadU (ubar of row t) and t+kLeadU-kLeadR (record of row t+kLeadU), so
-// all but the newest kPending groups must be complete.  Record slots cycle
-// mod kLeadR+1 and ubar slots mod kLeadU+1, so a copy never lands in a slot
-// whose previous row is still to be read.  Threads touch only their own
-// slots: no block barrier.
-constexpr int kLeadR = 6, kLeadU = 3;
+// FP32 fold with the rows staged through shared memory.  Each cell's rows
+// are copied asynchronously: the row record (moments + stencil index) kLeadR
+// rows ahead, and the FP32 pair of ubar_j kLeadU rows ahead (its index read
+// from the staged record), so neither the HBM latency of the records nor the
+// record -> index -> ubar chain stalls the rotations, and no prefetched row
+// occupies registers.  Commit groups: one per iteration t, holding ubar of row
+// t+kLeadU and the record of row t+kLeadR.  Iteration t needs the groups of
+// iterations t-kLeadU (ubar of row t) and t+kLeadU-kLeadR (record of row
+// t+kLeadU), so all but the newest kPending groups must be complete.  Record
+// slots cycle mod kLeadR+1 and ubar slots mod kLeadU+1, so a copy never lands
+// in a slot whose previous row is still to be read; the row loop is unrolled
+// by a common multiple of both, so every slot is a compile-time constant.
+// With C > 1 the C threads of a cell share one record slot (each copies part
+// of the record) and order their copies with a barrier over the cell's lanes;
+// the ubar pairs stay per thread.  No block barrier.
+constexpr int kLeadR = 7, kLeadU = 3, kUnrollS = 8;
 constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (kLeadR - kLeadU - 1);
 static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");
+static_assert(kUnrollS % (kLeadR + 1) == 0 && kUnrollS % (kLeadU + 1) == 0, "unroll by whole slot cycles");
+
+// Lanes of the C threads of this thread's cell (C divides 32).
+template <int C>
+__device__ __forceinline__ unsigned cell_lanes() {
+  const unsigned lane = threadIdx.x & 31u;
+  return C == 1 ? (1u << lane) : (((1u << C) - 1u) << (lane & ~static_cast<unsigned>(C - 1)));
+}
 
 // weights(&eh2, &w_centre) computes the cell's weights; it runs after the
 // first record copies are issued, so its gathers overlap them.
@@ -97,19 +108,22 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
                                                 int64_t i, float2 pi, int n, WFn&& weights, float* eh2_out,
                                                 float* wc_out, SqrtFreeQR<float, M>& f) {
   constexpr int W4 = rec32_width(M) / 4;
-  constexpr int kRec = kLeadR + 1, kU = kLeadU + 1;
-  __shared__ float4 srec[kRec][W4][kTpcThreads];
+  constexpr int kRec = kLeadR + 1, kU = kLeadU + 1, kCells = kTpcThreads / C;
+  __shared__ float4 srec[kRec][W4][kCells];
   __shared__ float2 su[kU][kTpcThreads];
   const int tid = threadIdx.x;
+  const int cell = tid / C, part = tid % C;
+  const unsigned lanes = cell_lanes<C>();
   const int64_t N = dm.N;
   const float4* rec = reinterpret_cast<const float4*>(dm.rec32);
   auto fetch_rec = [&](int t, int slot) {
     const float4* src = rec + (static_cast<int64_t>(t) * N + i) * W4;
 #pragma unroll
-    for (int k = 0; k < W4; ++k) cp_async16(&srec[slot][k][tid], src + k);
+    for (int k = 0; k < W4; ++k)
+      if (k % C == part) cp_async16(&srec[slot][k][cell], src + k);
   };
   auto fetch_u = [&](int rec_slot, int u_slot) {
-    const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][tid])[M % 4]);
+    const int j = __float_as_int(reinterpret_cast<const float*>(&srec[rec_slot][M / 4][cell])[M % 4]);
     cp_async8(&su[u_slot][tid], upair + static_cast<int64_t>(j) * C);
   };
   sqrt_free_init(f);
@@ -120,36 +134,40 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
   *eh2_out = eh2;
   *wc_out = w_centre;
   cp_async_wait<0>();
+  if (C > 1) __syncwarp(lanes);
   for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
   // empty groups: the first waits below then cover the ubar copies
 #pragma unroll
   for (int k = 0; k < kPending; ++k) cp_async_commit();
-  int sr = 0, sv = 0;  // slots of row t
-  for (int t = 0; t < n; ++t) {
-    cp_async_wait<kPending>();
-    float z[M + 1];
+  for (int t0 = 0; t0 < n; t0 += kUnrollS) {
 #pragma unroll
-    for (int k = 0; k < W4; ++k) {
-      const float4 v = srec[sr][k][tid];
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+    for (int s = 0; s < kUnrollS; ++s) {
+      const int t = t0 + s;
+      if (t >= n) break;
+      const int sr = s % kRec, sv = s % kU;  // slots of row t
+      cp_async_wait<kPending>();
+      // the cell's other lanes' record copies; every lane has also read row
+      // t-1 (the slot the record copy below overwrites)
+      if (C > 1) __syncwarp(lanes);
+      float z[M + 1];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (4 * k + q < M) z[4 * k + q] = vv[q];
+      for (int k = 0; k < W4; ++k) {
+        const float4 v = srec[sr][k][cell];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (4 * k + q < M) z[4 * k + q] = vv[q];
+      }
+      const float2 pj = su[sv][tid];
+      if (t + kLeadU < n) fetch_u((s + kLeadU) % kRec, (s + kLeadU) % kU);
+      if (t + kLeadR < n) fetch_rec(t + kLeadR, (s + kLeadR) % kRec);
+      cp_async_commit();
+      const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
+      const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
+      z[M] = dev;
+      sqrt_free_fold(f, z, w * w);
     }
-    const float2 pj = su[sv][tid];
-    const int srU = sr + kLeadU < kRec ? sr + kLeadU : sr + kLeadU - kRec;
-    const int srR = sr + kLeadR < kRec ? sr + kLeadR : sr + kLeadR - kRec;
-    const int svU = sv + kLeadU < kU ? sv + kLeadU : sv + kLeadU - kU;
-    if (t + kLeadU < n) fetch_u(srU, svU);
-    if (t + kLeadR < n) fetch_rec(t + kLeadR, srR);
-    cp_async_commit();
-    const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
-    const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
-    z[M] = dev;
-    sqrt_free_fold(f, z, w * w);
-    sr = sr + 1 < kRec ? sr + 1 : 0;
-    sv = sv + 1 < kU ? sv + 1 : 0;
   }
   cp_async_wait<0>();
 }
@@ -157,7 +175,8 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
 // The FP32 fold of tpc_fold_staged with the rows formed on the fly: the
 // 16-byte geometry record (offset and index) kLeadR rows ahead, and the pair
 // of ubar_j with cell j's own moments kLeadU rows ahead, through the same
-// commit-group schedule.
+// commit-group schedule (with C > 1 the geometry record and cell j's moments
+// shared by the cell's lanes, the pairs per thread).
 template <int DIM, int M, int C = 1, typename WFn>
 __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
                                                     int64_t i, float2 pi, int n, WFn&& weights, float* eh2_out,
@@ -167,10 +186,13 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   constexpr int kLeadRo = 7, kRec = kLeadRo + 1, kU = kLeadU + 1, kUnrollO = 8;
   constexpr int kPendingO = (kLeadU - 1) < (kLeadRo - kLeadU - 1) ? (kLeadU - 1) : (kLeadRo - kLeadU - 1);
   static_assert(kUnrollO % kRec == 0 && kUnrollO % kU == 0, "unroll by whole slot cycles");
-  __shared__ float4 sgeo[kRec][kTpcThreads];
-  __shared__ float4 sown[kU][OW4][kTpcThreads];
+  constexpr int kCells = kTpcThreads / C;
+  __shared__ float4 sgeo[kRec][kCells];
+  __shared__ float4 sown[kU][OW4][kCells];
   __shared__ float2 su[kU][kTpcThreads];
   const int tid = threadIdx.x;
+  const int cell = tid / C, part = tid % C;
+  const unsigned lanes = cell_lanes<C>();
   const int64_t N = dm.N;
   const float4* geo = reinterpret_cast<const float4*>(dm.geo32);
   const float4* own = reinterpret_cast<const float4*>(dm.own32);
@@ -179,12 +201,15 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   hp[1] = dm.hscale32 ? dm.hscale32[i].y : static_cast<float>(1.0 / dm.h[i]);  // 1/h_i (FP32, from the host)
 #pragma unroll
   for (int k = 2; k < 5; ++k) hp[k] = hp[k - 1] * hp[1];
-  auto fetch_rec = [&](int t, int slot) { cp_async16(&sgeo[slot][tid], geo + static_cast<int64_t>(t) * N + i); };
+  auto fetch_rec = [&](int t, int slot) {
+    if (part == 0) cp_async16(&sgeo[slot][cell], geo + static_cast<int64_t>(t) * N + i);
+  };
   auto fetch_u = [&](int rec_slot, int u_slot) {
-    const int j = __float_as_int(reinterpret_cast<const float*>(&sgeo[rec_slot][tid])[DIM]);
+    const int j = __float_as_int(reinterpret_cast<const float*>(&sgeo[rec_slot][cell])[DIM]);
     cp_async8(&su[u_slot][tid], upair + static_cast<int64_t>(j) * C);
 #pragma unroll
-    for (int k = 0; k < OW4; ++k) cp_async16(&sown[u_slot][k][tid], own + static_cast<int64_t>(j) * OW4 + k);
+    for (int k = 0; k < OW4; ++k)
+      if (k % C == part) cp_async16(&sown[u_slot][k][cell], own + static_cast<int64_t>(j) * OW4 + k);
   };
   sqrt_free_init(f);
   for (int t = 0; t < kLeadRo && t < n; ++t) fetch_rec(t, t);
@@ -194,6 +219,7 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
   *eh2_out = eh2;
   *wc_out = w_centre;
   cp_async_wait<0>();
+  if (C > 1) __syncwarp(lanes);
   for (int t = 0; t < kLeadU && t < n; ++t) fetch_u(t, t);
   cp_async_commit();
 #pragma unroll
@@ -207,7 +233,8 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
       if (t >= n) break;
       const int sr = s % kRec, sv = s % kU;  // slots of row t
       cp_async_wait<kPendingO>();
-      const float4 gv = sgeo[sr][tid];
+      if (C > 1) __syncwarp(lanes);  // as in tpc_fold_staged
+      const float4 gv = sgeo[sr][cell];
       const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
       float d[DIM];
 #pragma unroll
@@ -215,7 +242,7 @@ __device__ __forceinline__ void tpc_fold_staged_otf(const DeviceMesh& dm, const 
       float ow[OW4 * 4];
 #pragma unroll
       for (int k = 0; k < OW4; ++k) {
-        const float4 v = sown[sv][k][tid];
+        const float4 v = sown[sv][k][cell];
         ow[4 * k] = v.x;
         ow[4 * k + 1] = v.y;
         ow[4 * k + 2] = v.z;
@@ -421,8 +448,18 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
   }
 }
 
+// Resident blocks per SM the main kernel is compiled for: the FP32 kernels
+// of up to six columns fit 64 registers with the records shared by a
+// cell's lanes (C > 1: 8 blocks, 32 warps) or 80 with per-thread records
+// (6 blocks, which the 36 KB of staging per block also allows); the
+// ten-column fold needs 128 (4); the FP64 fold its full register file.
+template <typename T, int M, int C>
+constexpr int tpc_min_blocks() {
+  return sizeof(T) != 4 ? 1 : C > 1 ? 8 : M <= 6 ? 6 : 4;
+}
+
 template <typename T, int DIM, int M, bool OTF = false, int C = 1>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (C > 1 ? 5 : 4) : 1)
+__global__ void __launch_bounds__(128, tpc_min_blocks<T, M, C>())
 recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
                  double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
                  unsigned long long* WLSENO_BODY_RESTRICT counters, TpcWork work, T flag_threshold,

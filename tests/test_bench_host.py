@@ -109,3 +109,19 @@ def test_euler_and_flux_algorithmic_bytes():
     # facet records, 1/|tau|, FP64 state and pairs written
     assert bench.flux_bytes_per_cell(2, 6, 1, False) == 6 * 4 + 8 + 8 + 12 + 48 + 8 + 16
     assert bench.flux_bytes_per_cell(2, 6, 4, True) == 4 * (24 + 16) + 12 + 48 + 8 + 4 * 16 + 1
+
+
+def test_measured_traffic_only_for_the_captured_kernel_sources(monkeypatch):
+    # the stored per-cell DRAM bytes scale with the workload's cells while
+    # the sources match the capture's digest, and vanish once they do not
+    key = ("euler1024", "fp32_bulk", "reconstruct", False)
+    per_cell = bench.TRAFFIC_BYTES_PER_CELL[key][0]
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_DIGEST", bench.kernel_sources_digest())
+    assert bench.traffic_per_launch(*key, 2097152) == per_cell * 2097152
+    assert bench.traffic_per_launch("batched48", "fp32_bulk", "reconstruct", True, 10) is None
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_DIGEST", "0" * 12)
+    assert bench.traffic_per_launch(*key, 2097152) is None
+    # every capture is within a few times the algorithmic bytes of its kernel
+    # (more would mean the capture did not run the kernel the key names)
+    alg = bench.euler_recon_bytes_per_cell(13, 6, 6, 2, False)
+    assert 0.8 * alg < per_cell < 1.5 * alg
