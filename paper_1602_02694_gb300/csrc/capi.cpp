@@ -45,7 +45,7 @@ struct wlseno_ctx {
   int* d_wl_count = nullptr;     // [2] lengths of d_wl and of the refine records
   float* d_rbuf = nullptr;       // [wl_cap][refine_record_floats(m)] FP32-bulk refine records
   int64_t wl_cap = 0;            // N, or C N with the all-components Euler kernel
-  float* d_fdev = nullptr;       // [C][N][NP] FP32-bulk facet deviations (scalar equations, 2-D Euler)
+  float* d_fdev = nullptr;       // FP32-bulk facet deviations [N][NP] (scalar equations); 2-D Euler traces [N][NP][4]
   float2* d_pair = nullptr;      // [3][C][N] FP32 pairs of states: scratch, k1, k2 (FP32-bulk;
                                  // interleaved [N][C] on the all-components Euler path)
   bool euler32 = false;          // FP32-bulk 2-D Euler p = 3: all components in one kernel
@@ -366,8 +366,8 @@ cudaError_t stage_all(wlseno_ctx* ctx, const double* u, const double* u0, double
       if (e != cudaSuccess) return e;
     }
     KernelScope scope(ctx, WLSENO_KERNEL_FLUX, s);
-    e = launch_euler2_flux32(dm, ctx->sp.gamma, ctx->d_fdev, ctx->d_pos_ok, pu, p0, a, b, ctx->d_dt2,
-                             residual_only, out, ctx->d_counters, pout, s);
+    e = launch_euler2_flux32(dm, ctx->sp.gamma, ctx->d_fdev, pu, p0, a, b, ctx->d_dt2, residual_only, out,
+                             ctx->d_counters, pout, s);
     scope.done(e == cudaSuccess ? 1 : 0);
     return e;
   }
@@ -581,6 +581,7 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   for (int a = 0; a < 3; ++a) ctx->sp.vel[a] = scheme->velocity[a];
   ctx->sp.eps = scheme->eps;
   ctx->sp.alpha_c = scheme->alpha_c;
+  ctx->sp.alpha_c32 = static_cast<float>(scheme->alpha_c);
   ctx->sp.rank_tol = scheme->rank_tol;
   ctx->sp.kappa_flag = scheme->kappa_flag > 0.0 ? scheme->kappa_flag : 1e3;
   ctx->sp.gamma = scheme->gamma;

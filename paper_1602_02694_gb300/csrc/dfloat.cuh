@@ -14,6 +14,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <cstring>
+
 namespace wlseno {
 
 struct dfloat {
@@ -62,6 +65,51 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
 __host__ __device__ __forceinline__ dfloat df_from_double(double v) {
   const float hi = static_cast<float>(v);
   return {hi, static_cast<float>(v - static_cast<double>(hi))};
+}
+
+// The same pair from the bits of v by integer arithmetic alone (no FP64
+// instruction: on this part the FP64 pipe is the narrow one), where hi and
+// lo are normal FP32 numbers (binary exponent of v in [-73, 117]); other
+// values take df_from_double.  With v = (-1)^s (2^52 + m) 2^(e - 52): hi
+// keeps the top 23 bits of m rounded to nearest, ties to even (a carry out
+// of the mantissa moves into the exponent field, as it should); the
+// remainder r = (m mod 2^29) - 2^29 [rounded up] is v - hi in units of
+// 2^(e - 52), an integer of at most 29 bits, so fl32(v - hi) is the
+// round-to-nearest conversion of r times an exact power of two.  The
+// result equals df_from_double(v) bit for bit.
+__host__ __device__ __forceinline__ dfloat df_from_double_bits(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof b);
+  const uint32_t hw = static_cast<uint32_t>(b >> 32);
+  const int E = static_cast<int>((hw >> 20) & 0x7ffu);
+  if (E < 950 || E > 1140) return df_from_double(v);
+  const uint32_t top = static_cast<uint32_t>(b >> 29) & 0x7fffffu;
+  const uint32_t rem = static_cast<uint32_t>(b) & 0x1fffffffu;
+  const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (top & 1u))) ? 1u : 0u;
+  const uint32_t sign = hw & 0x80000000u;
+  const uint32_t hb = (sign | (static_cast<uint32_t>(E - 896) << 23) | top) + up;
+  const int32_t r = static_cast<int32_t>(rem) - static_cast<int32_t>(up << 29);
+  const uint32_t sb = static_cast<uint32_t>(E - 948) << 23;  // 2^(e - 52)
+  float hi, scale;
+  std::memcpy(&hi, &hb, sizeof hi);
+  std::memcpy(&scale, &sb, sizeof scale);
+  return {hi, static_cast<float>(sign ? -r : r) * scale};
+}
+
+// The bits of the FP64 value of a non-negative FP32 number s (a maximum
+// taken on FP64 bit patterns), by integer arithmetic for zero, infinity and
+// normal s (exponent rebiased by 1023 - 127, mantissa moved up 29 bits);
+// subnormal s and NaN take the conversion.
+__host__ __device__ __forceinline__ uint64_t df_f64_bits_nonneg(float s) {
+  uint32_t fb;
+  std::memcpy(&fb, &s, sizeof fb);
+  if (fb == 0u) return 0ull;
+  if (fb == 0x7f800000u) return 0x7ff0000000000000ull;
+  if (fb >= 0x00800000u && fb < 0x7f800000u) return (static_cast<uint64_t>(fb) + (896ull << 23)) << 29;
+  const double d = static_cast<double>(s);
+  uint64_t db;
+  std::memcpy(&db, &d, sizeof db);
+  return db;
 }
 
 }  // namespace wlseno

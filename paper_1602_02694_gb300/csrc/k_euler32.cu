@@ -2,12 +2,13 @@
 // flux / RK-stage kernel that follows the all-components reconstruction
 // (launch_recon_euler2d), and the FP32 pairs of the state it reads.
 //
-// Inputs per cell: the FP32 deviations of the four components' traces from
-// their cell averages ([4][N][6] floats, written by the reconstruction and
-// its follow-ups), the averages as FP32 pairs interleaved [N][4] (hi + lo of
-// each FP64 average), and the reconstruction's positivity flag (reading R14:
-// a cell whose traces give density or pressure <= 1e-12 uses its averages at
-// all its facets).  A trace is hi + (lo + deviation) in FP32.  Per facet the
+// Inputs per cell: the FP32 traces of the four components at its six facet
+// points ([N][6] float4, written by the reconstruction and its follow-ups:
+// hi + (lo + deviation) of each component, or the averages hi + lo at every
+// point of a cell whose traces give density or pressure <= 1e-12, reading
+// R14), and the averages as FP32 pairs interleaved [N][4] (hi + lo of each
+// FP64 average, for the stage update).  A facet reads its own traces and the
+// neighbour's at the same points: two 16-byte loads per point.  Per facet the
 // Lax-Friedrichs flux of Sec. 1, Eq. (flux), with alpha = max over the
 // facet's points and both sides of |u.n| + c, is evaluated in FP32 in the
 // orientation of the facet's lower-indexed cell with that cell's normal and
@@ -29,10 +30,23 @@ namespace {
 
 constexpr int kC = 4;  // rho, rho u, rho v, E
 
+// The normal flux F(U).n and the wave speed |u.n| + c of a state in FP32,
+// with the hardware reciprocal and reciprocal square root (about one ulp;
+// the flux carries FP32 rounding relative to |F| in any case, and both cells
+// of a facet evaluate it from the same operands: the same bits).
+__device__ __forceinline__ float approx_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float approx_sqrt_nonneg(float x) {  // 0 for x <= 0
+  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 __device__ __forceinline__ void euler2_state(const float (&U)[kC], float nx, float ny, float gamma,
                                              float (&F)[kC], float* speed) {
   const float rho = U[0];
-  const float inv = 1.0f / rho;
+  const float inv = approx_rcp(rho);
   const float un = (U[1] * nx + U[2] * ny) * inv;
   const float ke = U[1] * U[1] + U[2] * U[2];
   const float p = (gamma - 1.0f) * (U[3] - 0.5f * ke * inv);
@@ -41,12 +55,11 @@ __device__ __forceinline__ void euler2_state(const float (&U)[kC], float nx, flo
   F[2] = U[2] * un + p * ny;
   F[3] = (U[3] + p) * un;
   const float c2 = gamma * p * inv;
-  *speed = fabsf(un) + sqrtf(c2 > 0.0f ? c2 : 0.0f);
+  *speed = fabsf(un) + approx_sqrt_nonneg(c2);
 }
 
-__global__ void __launch_bounds__(128, 4)
-euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
-                     const unsigned char* __restrict__ pos_ok, const float2* __restrict__ pin,
+__global__ void __launch_bounds__(128, 6)
+euler2_flux32_kernel(DeviceMesh dm, float gamma, const float4* __restrict__ tr, const float2* __restrict__ pin,
                      const float2* __restrict__ p0, dfloat a, dfloat b, const float2* __restrict__ dt2,
                      int residual_only, double* __restrict__ out, unsigned long long* __restrict__ counters,
                      float2* __restrict__ pout) {
@@ -58,6 +71,9 @@ euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
   int nb[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) nb[f] = dm.nbr[i * NF + f];
+  float4 To[NP];  // own traces, the four components of a point together
+#pragma unroll
+  for (int k = 0; k < NP; ++k) To[k] = tr[i * NP + k];
   const float4* pin4 = reinterpret_cast<const float4*>(pin);
   float2 P[kC];
   {
@@ -66,18 +82,6 @@ euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
     P[1] = make_float2(v0.z, v0.w);
     P[2] = make_float2(v1.x, v1.y);
     P[3] = make_float2(v1.z, v1.w);
-  }
-  const bool ok_i = pos_ok[i] != 0;
-  float di[kC][NP];
-#pragma unroll
-  for (int c = 0; c < kC; ++c) {
-    const float2* src = reinterpret_cast<const float2*>(fdev + (c * N + i) * NP);
-#pragma unroll
-    for (int k = 0; k < NP / 2; ++k) {
-      const float2 v = src[k];
-      di[c][2 * k] = v.x;
-      di[c][2 * k + 1] = v.y;
-    }
   }
   float4 g[NF];
 #pragma unroll
@@ -98,25 +102,15 @@ euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
       q0[3] = make_float2(v1.z, v1.w);
     }
   }
-  float2 Pj[NF][kC];
-  float dj[NF][kC][NQ];
-  bool okj[NF];
+  // the neighbours' traces at the shared facets (the same points, in the
+  // same order, as the facet's points in cell i)
+  float4 Tn[NF][NQ];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const int64_t j = nb[f] >= 0 ? (nb[f] >> 2) : i;
     const int f2 = nb[f] >= 0 ? (nb[f] & 3) : f;
-    const float4 v0 = pin4[2 * j], v1 = pin4[2 * j + 1];
-    Pj[f][0] = make_float2(v0.x, v0.y);
-    Pj[f][1] = make_float2(v0.z, v0.w);
-    Pj[f][2] = make_float2(v1.x, v1.y);
-    Pj[f][3] = make_float2(v1.z, v1.w);
-    okj[f] = pos_ok[j] != 0;
 #pragma unroll
-    for (int c = 0; c < kC; ++c) {
-      const float2 v = *reinterpret_cast<const float2*>(fdev + (c * N + j) * NP + f2 * NQ);
-      dj[f][c][0] = v.x;
-      dj[f][c][1] = v.y;
-    }
+    for (int q = 0; q < NQ; ++q) Tn[f][q] = tr[j * NP + f2 * NQ + q];
   }
   dfloat acc[kC];
 #pragma unroll
@@ -130,11 +124,11 @@ euler2_flux32_kernel(DeviceMesh dm, float gamma, const float* __restrict__ fdev,
     float alpha = 0.0f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      float Uo[kC], Un[kC];
+      const float4 o = To[f * NQ + q];
+      const float4 t = inner ? Tn[f][q] : o;  // transmissive: u+ = u-
+      const float Uo[kC] = {o.x, o.y, o.z, o.w}, Un[kC] = {t.x, t.y, t.z, t.w};
 #pragma unroll
       for (int c = 0; c < kC; ++c) {
-        Uo[c] = P[c].x + (P[c].y + (ok_i ? di[c][f * NQ + q] : 0.0f));
-        Un[c] = inner ? Pj[f][c].x + (Pj[f][c].y + (okj[f] ? dj[f][c][q] : 0.0f)) : Uo[c];
         UL[q][c] = owner ? Uo[c] : Un[c];
         UR[q][c] = owner ? Un[c] : Uo[c];
       }
@@ -186,7 +180,7 @@ __global__ void euler2_split_pairs_kernel(const double* __restrict__ u, float2* 
   float v[2 * kC];
 #pragma unroll
   for (int c = 0; c < kC; ++c) {
-    const dfloat d = df_from_double(u[c * N + i]);
+    const dfloat d = df_from_double_bits(u[c * N + i]);
     v[2 * c] = d.hi;
     v[2 * c + 1] = d.lo;
   }
@@ -198,7 +192,9 @@ __global__ void euler2_split_pairs_kernel(const double* __restrict__ u, float2* 
 // The FP32 pairs of the state (interleaved) and, in the same pass, the
 // largest |u| + c per mesh from them in FP32 (the CFL step of the FP32-bulk
 // path; FP32 relative accuracy is ample for a time step), as the bits of a
-// non-negative double; a non-finite state gives infinity (dt = 0).
+// non-negative double; a non-finite state gives infinity (dt = 0).  The
+// pairs and the bits come from integer operations (dfloat.cuh): with four
+// FP64 values per cell, the FP64 pipe would otherwise bound the pass.
 __global__ void __launch_bounds__(256)
 euler2_speed_pairs32_kernel(int64_t N, float gamma, const double* __restrict__ u,
                             const int32_t* __restrict__ mesh_of, unsigned long long* __restrict__ lmax_bits,
@@ -208,20 +204,20 @@ euler2_speed_pairs32_kernel(int64_t N, float gamma, const double* __restrict__ u
     float v[2 * kC], U[kC];
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      const dfloat d = df_from_double(u[c * N + i]);
+      const dfloat d = df_from_double_bits(u[c * N + i]);
       v[2 * c] = d.hi;
       v[2 * c + 1] = d.lo;
       U[c] = d.hi;
     }
     po[2 * i] = make_float4(v[0], v[1], v[2], v[3]);
     po[2 * i + 1] = make_float4(v[4], v[5], v[6], v[7]);
-    const float inv = 1.0f / U[0];
+    const float inv = approx_rcp(U[0]);
     const float ke = U[1] * U[1] + U[2] * U[2];
     const float p = (gamma - 1.0f) * (U[3] - 0.5f * ke * inv);
     const float c2 = gamma * p * inv;
-    float s = sqrtf(ke) * inv + sqrtf(c2 > 0.0f ? c2 : 0.0f);
+    float s = approx_sqrt_nonneg(ke) * inv + approx_sqrt_nonneg(c2);
     if (!(s >= 0.0f) || !(s <= 3.0e38f)) s = INFINITY;
-    return static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(s)));
+    return static_cast<unsigned long long>(df_f64_bits_nonneg(s));
   });
 }
 
@@ -238,14 +234,14 @@ cudaError_t launch_euler2_speed_pairs32(const DeviceMesh& dm, double gamma, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_euler2_flux32(const DeviceMesh& dm, double gamma, const float* fdev,
-                                 const unsigned char* pos_ok, const float2* pin, const float2* p0,
-                                 double a, double b, const float2* dt2, bool residual_only, double* out,
-                                 unsigned long long* counters, float2* pout, cudaStream_t s) {
-  if (dm.dim != 2 || !dm.nf32 || !dm.inv_vol2 || !pin || !pos_ok || !fdev) return cudaErrorInvalidValue;
+cudaError_t launch_euler2_flux32(const DeviceMesh& dm, double gamma, const float* traces, const float2* pin,
+                                 const float2* p0, double a, double b, const float2* dt2, bool residual_only,
+                                 double* out, unsigned long long* counters, float2* pout, cudaStream_t s) {
+  if (dm.dim != 2 || !dm.nf32 || !dm.inv_vol2 || !pin || !traces) return cudaErrorInvalidValue;
   if (!residual_only && (!dt2 || (a != 0.0 && !p0))) return cudaErrorInvalidValue;
   const unsigned blocks = static_cast<unsigned>((dm.N + 127) / 128);
-  euler2_flux32_kernel<<<blocks, 128, 0, s>>>(dm, static_cast<float>(gamma), fdev, pos_ok, pin, p0,
+  euler2_flux32_kernel<<<blocks, 128, 0, s>>>(dm, static_cast<float>(gamma),
+                                              reinterpret_cast<const float4*>(traces), pin, p0,
                                               df_from_double(a), df_from_double(b), dt2, residual_only ? 1 : 0,
                                               out, counters, residual_only ? nullptr : pout);
   return cudaGetLastError();

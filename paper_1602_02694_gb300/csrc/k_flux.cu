@@ -60,9 +60,8 @@ flux_stage_df_kernel(DeviceMesh dm, int pde, float speed, const float* __restric
 __global__ void split_pairs_kernel(const double* __restrict__ u, float2* __restrict__ pair, int64_t n) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= n) return;
-  const double v = u[k];
-  const float hi = __double2float_rn(v);
-  pair[k] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+  const dfloat d = df_from_double_bits(u[k]);
+  pair[k] = make_float2(d.hi, d.lo);
 }
 
 // Largest |ubar| per mesh (and the state's FP32 pairs in the same pass).
@@ -72,10 +71,11 @@ max_abs_kernel(int64_t N, const double* __restrict__ u, const int32_t* __restric
   chunked_mesh_max(N, mesh_of, lmax_bits, [&](int64_t i) {
     const double v = u[i];
     if (pairs) {
-      const float hi = __double2float_rn(v);
-      pairs[i] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+      const dfloat d = df_from_double_bits(v);
+      pairs[i] = make_float2(d.hi, d.lo);
     }
-    return static_cast<unsigned long long>(__double_as_longlong(fabs(v)));
+    // |v| by clearing the sign bit (no FP64 instruction)
+    return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
   });
 }
 

@@ -334,12 +334,12 @@ __device__ __forceinline__ void max_abs_cell(int64_t N, const double* WLSENO_BOD
                                              unsigned long long* WLSENO_BODY_RESTRICT lmax_bits, float2* WLSENO_BODY_RESTRICT pairs,
                                              int64_t i, bool in) {
   if (pairs && in) {  // the FP32 pairs of the state, in the same pass
-    const double v = u[i];
-    const float hi = __double2float_rn(v);
-    pairs[i] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+    const dfloat d = df_from_double_bits(u[i]);
+    pairs[i] = make_float2(d.hi, d.lo);
   }
   const int mesh = in ? mesh_of[i] : -1;
-  unsigned long long bits = in ? static_cast<unsigned long long>(__double_as_longlong(fabs(u[i]))) : 0ull;
+  unsigned long long bits =
+      in ? static_cast<unsigned long long>(__double_as_longlong(u[i])) & 0x7fffffffffffffffull : 0ull;  // |u_i|
   const int lane = threadIdx.x & 31;
   const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
   const bool same = __all_sync(0xffffffffu, mesh == m0 || mesh < 0);

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128, 2) persistent_step_kernel(PersistArgs a) 
     }
   } else if (F32) {
     for (int64_t i = gt0; i < N; i += nthr) {
-      const dfloat d = df_from_double(a.u[i]);
+      const dfloat d = df_from_double_bits(a.u[i]);
       a.pu[i] = make_float2(d.hi, d.lo);
     }
   }

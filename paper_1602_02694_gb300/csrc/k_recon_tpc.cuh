@@ -112,21 +112,38 @@ constexpr double kWeightSpread = 1e6;
 // Spread of the column-scaled diagonal: qmax = max_k q_k^2 and qmin =
 // min_k q_k^2.  A cell is ill-conditioned at threshold K when
 // !(qmax <= K^2 qmin), which also catches a zero or non-finite diagonal.
+// Squared column norms n_k = sum_{i<=k} d_i u_ik^2 of R.
 template <typename T, int M>
-__device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, T* qmax_out, T* qmin_out) {
-  T qmax = T(0), qmin = T(INFINITY);
+__host__ __device__ __forceinline__ void sqrt_free_colnorms(const SqrtFreeQR<T, M>& f, T (&nrm)[M]) {
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     T n = f.d[k];
 #pragma unroll
     for (int i = 0; i < k; ++i) n = fma(f.d[i] * f.U[i][k], f.U[i][k], n);
+    nrm[k] = n;
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, const T (&nrm)[M], T* qmax_out,
+                                                 T* qmin_out) {
+  T qmax = T(0), qmin = T(INFINITY);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
     // (FP32: the hardware reciprocal, ample for a threshold test)
-    const T q = sizeof(T) == 4 ? f.d[k] * recip_t<T>(n) : f.d[k] / n;
+    const T q = sizeof(T) == 4 ? f.d[k] * recip_t<T>(nrm[k]) : f.d[k] / nrm[k];
     qmax = q > qmax ? q : qmax;
     qmin = q < qmin ? q : qmin;
   }
   *qmax_out = qmax;
   *qmin_out = qmin;
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_spread(const SqrtFreeQR<T, M>& f, T* qmax_out, T* qmin_out) {
+  T nrm[M];
+  sqrt_free_colnorms(f, nrm);
+  sqrt_free_spread(f, nrm, qmax_out, qmin_out);
 }
 
 // Approximate 1/sqrt for the estimate below (the hardware approximation on
@@ -139,54 +156,82 @@ __host__ __device__ __forceinline__ float est_rsqrt(float x) {
 #endif
 }
 
+// Approximate reciprocal for the estimate below (the hardware
+// approximation on the device, flushing subnormals: a diagonal entry below
+// the FP32 normal range gives infinity).
+__host__ __device__ __forceinline__ float est_rcp(float x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return 1.0f / x;
+#endif
+}
+
 // A second conditioning estimate, for the cells the spread misses (it only
 // bounds the conditioning from below, and nearly dependent columns can leave
 // every column-scaled diagonal entry moderate): the LINPACK estimate of
 // ||R_B^-1|| for the column-scaled factor R_B = D^(1/2) U diag(1/sqrt(n_k))
 // of W A S (Cline, Moler, Stewart and Wilkinson 1979): solve R_B^T z = e
 // with e_k = +-1 chosen as the solve goes to make |z_k| grow, then
-// R_B w = z, and return ||w|| / ||z|| (max norms), a lower bound on
+// R_B w = z, and take ||w|| / ||z|| (max norms), a lower bound on
 // ||R_B^-1|| that in practice lies within a small factor of it.  With
 // y_k = sqrt(d_k) z_k the first solve is y_k = e_k sqrt(n_k) -
 // sum_{i<k} u_ik y_i; with w = sqrt(n) v the second is the unit-triangular
-// U v = D^(-1/2) z: neither divides by U.  An estimate only decides a
-// routing threshold, so it runs in FP32 for either factor precision (a
-// diagonal entry below the FP32 range gives infinity: near singular).
+// U v = D^(-1/2) z = D^(-1) y: neither divides by U.  The squares
+// z_k^2 = y_k^2 / d_k and w_k^2 = v_k^2 n_k need no square root of d or w,
+// so this returns max w_k^2 and max z_k^2 (the estimate is the square root
+// of their quotient).  An estimate only decides a routing threshold, so it
+// runs in FP32 for either factor precision (a diagonal entry below the FP32
+// range gives an infinite w: near singular).
 template <typename T, int M>
-__host__ __device__ __forceinline__ float sqrt_free_inverse_estimate(const SqrtFreeQR<T, M>& f) {
-  float y[M], sn[M], rd[M];
-  float zmax = 0.0f;
+__host__ __device__ __forceinline__ void sqrt_free_inverse_estimate_sq(const SqrtFreeQR<T, M>& f, const T (&nrm)[M],
+                                                                       float* w2max_out, float* z2max_out) {
+  float y[M], rdd[M];
+  float z2max = 0.0f;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    T n = f.d[k];
-#pragma unroll
-    for (int i = 0; i < k; ++i) n = fma(f.d[i] * f.U[i][k], f.U[i][k], n);
     float sk = 0.0f;
 #pragma unroll
     for (int i = 0; i < k; ++i) sk = std::fma(static_cast<float>(f.U[i][k]), y[i], sk);
-    const float nf = static_cast<float>(n);
-    sn[k] = nf * est_rsqrt(nf);                     // sqrt(n_k)
-    rd[k] = est_rsqrt(static_cast<float>(f.d[k]));  // 1 / sqrt(d_k)
-    const float mag = sn[k] + std::fabs(sk);
+    const float nf = static_cast<float>(nrm[k]);
+    rdd[k] = est_rcp(static_cast<float>(f.d[k]));        // 1 / d_k
+    const float mag = nf * est_rsqrt(nf) + std::fabs(sk);  // sqrt(n_k) + |s_k|
     y[k] = sk > 0.0f ? -mag : mag;
-    const float z = mag * rd[k];
-    zmax = z > zmax ? z : zmax;
-    y[k] = y[k];  // y_k = sqrt(d_k) z_k
+    const float z2 = mag * mag * rdd[k];
+    z2max = z2 > z2max ? z2 : z2max;
   }
-  // U v = D^(-1/2) z = D^(-1) y, back substitution; w = sqrt(n) v
   float v[M];
-  float wmax = 0.0f;
+  float w2max = 0.0f;
 #pragma unroll
   for (int k = M - 1; k >= 0; --k) {
-    float t = y[k] * rd[k] * rd[k];
+    float t = y[k] * rdd[k];
 #pragma unroll
     for (int c = k + 1; c < M; ++c) t = std::fma(-static_cast<float>(f.U[k][c]), v[c], t);
     v[k] = t;
-    const float w = std::fabs(t) * sn[k];
-    wmax = w > wmax ? w : wmax;
+    const float w2 = t * t * static_cast<float>(nrm[k]);
+    w2max = w2 > w2max ? w2 : w2max;
   }
-  const float est = wmax / zmax;
-  return est == est ? est : INFINITY;
+  *w2max_out = w2max;
+  *z2max_out = z2max;
+}
+
+// The estimate itself (infinity where it is not a number).
+template <typename T, int M>
+__host__ __device__ __forceinline__ float sqrt_free_inverse_estimate(const SqrtFreeQR<T, M>& f) {
+  T nrm[M];
+  sqrt_free_colnorms(f, nrm);
+  float w2, z2;
+  sqrt_free_inverse_estimate_sq(f, nrm, &w2, &z2);
+  const float e2 = w2 / z2;
+  return e2 == e2 ? std::sqrt(e2) : INFINITY;
+}
+
+// Whether the estimate exceeds the bound K (or is not a number, or the
+// second solve overflowed).
+__host__ __device__ __forceinline__ bool inverse_estimate_exceeds(float w2max, float z2max, float K) {
+  return !(w2max <= K * K * z2max) || !(w2max <= 3.0e38f);
 }
 
 // Packed position of U[k][j] (k < j < M) in a strict upper triangle.
@@ -234,8 +279,8 @@ __device__ __forceinline__ void tpc_weights(const DeviceMesh& dm, const SchemePa
   *w_centre = static_cast<T>(sp.alpha_c) * e / bmin;
 }
 
-// The same weights in FP32-bulk from the FP32 pairs of ubar (no FP64 work
-// but eps h^2).  The pairs of cell j sit at upair[j * C] (C > 1: the pairs of
+// The same weights in FP32-bulk from the FP32 pairs of ubar, eps h_i^2 and
+// alpha rounded to FP32 on the host (no FP64 instruction).  The pairs of cell j sit at upair[j * C] (C > 1: the pairs of
 // all components interleaved, upair pointing at this thread's component).
 template <int DIM, int C = 1>
 __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const SchemeParams& sp,
@@ -255,7 +300,7 @@ __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const Sch
     }
   }
   *eh2 = e;
-  *w_centre = static_cast<float>(sp.alpha_c) * e / bmin;
+  *w_centre = sp.alpha_c32 * e / bmin;
 }
 
 }  // namespace wlseno

@@ -172,6 +172,102 @@ __device__ __forceinline__ void tpc_fold_staged(const DeviceMesh& dm, const floa
   cp_async_wait<0>();
 }
 
+// The FP32 fold of tpc_fold_staged for C > 1 lanes per cell, in chunks of
+// kChunk rows: a chunk's rows are folded as one straight-line block (no
+// branch between them, so the compiler can overlap one row's rotations with
+// the next row's), and the copies, waits and barriers are per chunk rather
+// than per row.  Records of chunks c+1 and c+2 and the ubar pairs of chunk
+// c+1 are in flight while chunk c is folded: three record slots (shared by
+// the cell's lanes, each lane copying part of them) and two ubar slots (per
+// thread).  At the start of chunk c every copy issued so far has landed (the
+// copies of chunk c-1's iteration had a whole chunk of rotations to arrive),
+// and the barrier over the cell's lanes orders their reads of chunk c-1's
+// record slot before the copy that reuses it.  A last partial chunk folds its
+// rows one by one.
+constexpr int kChunk = 4;
+
+template <int DIM, int M, int C, typename WFn>
+__device__ __forceinline__ void tpc_fold_chunked(const DeviceMesh& dm, const float2* WLSENO_BODY_RESTRICT upair,
+                                                 int64_t i, float2 pi, int n, WFn&& weights, float* eh2_out,
+                                                 float* wc_out, SqrtFreeQR<float, M>& f) {
+  static_assert(C > 1, "records shared by a cell's lanes");
+  constexpr int W4 = rec32_width(M) / 4;
+  constexpr int kCells = kTpcThreads / C, kPieces = kChunk * W4;
+  __shared__ float4 srec[3][kChunk][W4][kCells];
+  __shared__ float2 su[2][kChunk][kTpcThreads];
+  const int tid = threadIdx.x;
+  const int cell = tid / C, part = tid % C;
+  const unsigned lanes = cell_lanes<C>();
+  const int64_t stride = dm.N * W4;  // float4s between rows t and t+1 of a cell
+  const float4* rec = reinterpret_cast<const float4*>(dm.rec32) + i * W4;
+  // records of the rows of chunk c below n (16-byte pieces spread over the
+  // cell's lanes) into record slot c % 3
+  auto fetch_rec = [&](int c) {
+    const int slot = c % 3;
+#pragma unroll
+    for (int q0 = 0; q0 < kPieces; q0 += C) {
+      const int q = q0 + part, r = q / W4, k = q % W4, t = c * kChunk + r;
+      if (q < kPieces && t < n) cp_async16(&srec[slot][r][k][cell], rec + t * stride + k);
+    }
+  };
+  // ubar pairs of the rows of chunk c below n into ubar slot c % 2 (their
+  // indices from the chunk's records)
+  auto fetch_u = [&](int c) {
+    const int slot = c % 3, us = c % 2;
+#pragma unroll
+    for (int r = 0; r < kChunk; ++r) {
+      if (c * kChunk + r < n) {
+        const int j = __float_as_int(reinterpret_cast<const float*>(&srec[slot][r][M / 4][cell])[M % 4]);
+        cp_async8(&su[us][r][tid], upair + static_cast<int64_t>(j) * C);
+      }
+    }
+  };
+  sqrt_free_init(f);
+  fetch_rec(0);
+  fetch_rec(1);
+  cp_async_commit();
+  float eh2, w_centre;
+  weights(&eh2, &w_centre);
+  *eh2_out = eh2;
+  *wc_out = w_centre;
+  // one row: deviation, weight (Sec. 3.1.2), rotations
+  auto fold_row = [&](int slot, int us, int r, int t) {
+    float z[M + 1];
+#pragma unroll
+    for (int k = 0; k < W4; ++k) {
+      const float4 v = srec[slot][r][k][cell];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * k + q < M) z[4 * k + q] = vv[q];
+    }
+    const float2 pj = su[us][r][tid];
+    const float dev = (pj.x - pi.x) + (pj.y - pi.y);  // ubar_j - ubar_i
+    const float w = t == 0 ? w_centre : eh2 * recip_t(fmaf(dev, dev, eh2));
+    z[M] = dev;
+    sqrt_free_fold(f, z, w * w);
+  };
+  cp_async_wait<0>();
+  __syncwarp(lanes);
+  fetch_u(0);
+  cp_async_commit();
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  for (int c = 0; c < nchunks; ++c) {
+    cp_async_wait<0>();
+    __syncwarp(lanes);
+    if ((c + 1) * kChunk < n) fetch_u(c + 1);
+    if ((c + 2) * kChunk < n) fetch_rec(c + 2);
+    cp_async_commit();
+    const int slot = c % 3, us = c % 2, t0 = c * kChunk;
+    if (t0 + kChunk <= n) {
+#pragma unroll
+      for (int r = 0; r < kChunk; ++r) fold_row(slot, us, r, t0 + r);
+    } else {
+      for (int r = 0; r < n - t0; ++r) fold_row(slot, us, r, t0 + r);
+    }
+  }
+}
+
 // The FP32 fold of tpc_fold_staged with the rows formed on the fly: the
 // 16-byte geometry record (offset and index) kLeadR rows ahead, and the pair
 // of ubar_j with cell j's own moments kLeadU rows ahead, through the same
@@ -276,24 +372,81 @@ __device__ __forceinline__ void tpc_write(const DeviceMesh& dm, int64_t i, doubl
 
 // The FP32-deviation output alone (no coefficients): with the FP64 output
 // path compiled out, no FP64 instruction is predicated into the FP32 kernel.
+// Copies of n floats between 8-byte aligned addresses in the widest
+// accesses their count allows (each cell's point offsets and deviations
+// start at a multiple of 8 bytes: n is even).
+template <int NF>
+__device__ __forceinline__ void load_floats(const float* WLSENO_BODY_RESTRICT src, float (&dst)[NF]) {
+  static_assert(NF % 2 == 0, "even counts");
+  if constexpr (NF % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < NF / 4; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(src)[k];
+      dst[4 * k] = v.x, dst[4 * k + 1] = v.y, dst[4 * k + 2] = v.z, dst[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NF / 2; ++k) {
+      const float2 v = reinterpret_cast<const float2*>(src)[k];
+      dst[2 * k] = v.x, dst[2 * k + 1] = v.y;
+    }
+  }
+}
+template <int NF>
+__device__ __forceinline__ void store_floats(float* WLSENO_BODY_RESTRICT dst, const float (&src)[NF]) {
+  static_assert(NF % 2 == 0, "even counts");
+  if constexpr (NF % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < NF / 4; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NF / 2; ++k) reinterpret_cast<float2*>(dst)[k] = make_float2(src[2 * k], src[2 * k + 1]);
+  }
+}
+
+// The polynomial's deviations from ubar_i at the cell's facet points.
 template <typename T, int DIM, int M>
-__device__ __forceinline__ void tpc_write_dev(const DeviceMesh& dm, int64_t i, const T (&x)[M],
-                                              float* WLSENO_BODY_RESTRICT fdev, T* dev_out) {
+__device__ __forceinline__ void tpc_eval_dev(const DeviceMesh& dm, int64_t i, const T (&x)[M],
+                                             T (&dev)[(DIM + 1) * nq_of(DIM)]) {
   constexpr int NP = (DIM + 1) * nq_of(DIM);
   const T* P = tpc_points<T>(dm) + i * NP * DIM;
+  T pts[NP * DIM];
+  if constexpr (sizeof(T) == 4) {
+    // FP32 offsets of a cell: 8 (1-D), 48 (2-D) or 144 (3-D) bytes from a
+    // multiple of their size
+    load_floats<NP * DIM>(P, pts);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NP * DIM; ++k) pts[k] = P[k];
+  }
 #pragma unroll
   for (int pt = 0; pt < NP; ++pt) {
     T yy[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) yy[a] = P[pt * DIM + a];
+    for (int a = 0; a < DIM; ++a) yy[a] = pts[pt * DIM + a];
     T mono[M];
     eval_monomials<T, DIM, M>(yy, mono);
     T sh = T(0);
 #pragma unroll
     for (int c = 0; c < M; ++c) sh = fma(x[c], mono[c], sh);
-    if (dev_out) dev_out[pt] = sh;
-    fdev[i * NP + pt] = static_cast<float>(sh);
+    dev[pt] = sh;
   }
+}
+
+template <typename T, int DIM, int M>
+__device__ __forceinline__ void tpc_write_dev(const DeviceMesh& dm, int64_t i, const T (&x)[M],
+                                              float* WLSENO_BODY_RESTRICT fdev, T* dev_out) {
+  constexpr int NP = (DIM + 1) * nq_of(DIM);
+  T dev[NP];
+  tpc_eval_dev<T, DIM, M>(dm, i, x, dev);
+  float out[NP];
+#pragma unroll
+  for (int pt = 0; pt < NP; ++pt) {
+    if (dev_out) dev_out[pt] = dev[pt];
+    out[pt] = static_cast<float>(dev[pt]);
+  }
+  store_floats<NP>(fdev + i * NP, out);
 }
 
 template <typename T, int DIM, int M>
@@ -355,7 +508,7 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
   ubar += coff;
   if (coeffs) coeffs += coff * M;
   if (fvals) fvals += coff * NP;
-  if (fdev) fdev += coff * NP;
+  if (fdev && C == 1) fdev += coff * NP;  // (C > 1: the traces of all components, [N][NP][C])
   T eh2, wc;
   SqrtFreeQR<T, M> f;
   float2 pi = make_float2(0.0f, 0.0f);
@@ -367,38 +520,60 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
     auto wfn = [&](float* e, float* w) { tpc_weights_pair<DIM, C>(dm, sp, up, i, pi, e, w); };
     if constexpr (OTF)
       tpc_fold_staged_otf<DIM, M, C>(dm, up, i, pi, n, wfn, &eh2, &wc, f);
+    else if constexpr (C > 1)
+      tpc_fold_chunked<DIM, M, C>(dm, up, i, pi, n, wfn, &eh2, &wc, f);
     else
       tpc_fold_staged<DIM, M, C>(dm, up, i, pi, n, wfn, &eh2, &wc, f);
-    ui = ubar[i];  // needed by the outputs only (after the fold)
+    // needed by the FP64 outputs and the refine records only: not loaded
+    // for the deviation outputs (see the refine record below)
+    ui = fdev && !coeffs ? 0.0 : ubar[i];
   } else {
     ui = ubar[i];
     tpc_weights<T, DIM>(dm, sp, ubar, i, ui, &eh2, &wc);
     tpc_fold<DIM, M>(dm, ubar, i, ui, n, eh2, wc, f, &w_spread);
   }
-  T qmax, qmin;
-  sqrt_free_spread(f, &qmax, &qmin);
+  T qmax, qmin, nrm[M];
+  sqrt_free_colnorms(f, nrm);  // shared by the two conditioning tests
+  sqrt_free_spread(f, nrm, &qmax, &qmin);
   T x[M];
   sqrt_free_solve(f, x);
   if constexpr (C > 1) {
+    // the C threads of the cell: each evaluates its component's traces
+    // hi + (lo + dev) (Sec. 3.2 polynomial, FP32) and puts them, with its
+    // average hi + lo, in shared memory; then each tests the points p =
+    // lane, lane + C, ... for rho and p > 1e-12 with all components
+    // (conserved rho, rho u_1 .. rho u_dim, E) and, after the cell's lanes
+    // agree, writes those points' traces -- or the averages, when any point
+    // fails -- to fdev as [N][NP] float4 (the components of a point together)
     T dv[NP];
-    tpc_write<T, DIM, M>(dm, i, ui, x, coeffs, fvals, fdev, dv);
-    // rho and p at every facet point from the C threads of the cell
-    // (conserved rho, rho u_1 .. rho u_dim, E; FP32 traces hi + (lo + dev))
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned seg = ((1u << C) - 1u) << (lane & ~static_cast<unsigned>(C - 1));
+    tpc_eval_dev<T, DIM, M>(dm, i, x, dv);
+    __shared__ float4 spos[kTpcThreads / C][NP + 1];
+    static_assert(C == 4, "one float4 per facet point");
+    const int cell = threadIdx.x / C;
+    float* sp_cell = reinterpret_cast<float*>(&spos[cell][0]);
+#pragma unroll
+    for (int pt = 0; pt < NP; ++pt) sp_cell[pt * C + comp] = pi.x + (pi.y + static_cast<float>(dv[pt]));
+    sp_cell[NP * C + comp] = pi.x + (pi.y + 0.0f);
+    const unsigned seg = cell_lanes<C>();
+    __syncwarp(seg);
     const float gm1 = work.gamma - 1.0f;
     bool ok = true;
 #pragma unroll
-    for (int pt = 0; pt < NP; ++pt) {
-      const float v = pi.x + (pi.y + static_cast<float>(dv[pt]));
-      float U[C];
+    for (int p0 = 0; p0 < NP; p0 += C) {
+      const int pt = p0 + comp;
+      if (pt < NP) {
+        const float4 U = spos[cell][pt];
+        const float ke = fmaf(U.z, U.z, U.y * U.y);
+        const float pr = gm1 * (U.w - 0.5f * ke * recip_t(U.x));  // a threshold test
+        ok = ok && U.x > 1e-12f && pr > 1e-12f;
+      }
+    }
+    ok = __all_sync(seg, ok);
+    float4* trace = reinterpret_cast<float4*>(fdev) + i * NP;
 #pragma unroll
-      for (int c = 0; c < C; ++c) U[c] = __shfl_sync(seg, v, c, C);
-      float ke = 0.0f;
-#pragma unroll
-      for (int a = 0; a < C - 2; ++a) ke = fmaf(U[1 + a], U[1 + a], ke);
-      const float pr = gm1 * (U[C - 1] - 0.5f * ke * recip_t(U[0]));  // a threshold test
-      ok = ok && U[0] > 1e-12f && pr > 1e-12f;
+    for (int p0 = 0; p0 < NP; p0 += C) {
+      const int pt = p0 + comp;
+      if (pt < NP) trace[pt] = spos[cell][ok ? pt : NP];
     }
     if (comp == 0) {
       work.pos_ok[i] = ok ? 1 : 0;
@@ -410,8 +585,10 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
   // a cell is flagged when its spread passes the flag threshold or its
   // inverse estimate passes the pivot bound (then it always takes the
   // pivoted path); a non-finite factor fails both tests
-  const float zest = sqrt_free_inverse_estimate(f);
-  const bool near_singular = !(zest <= static_cast<float>(pivot_threshold)) || !(w_spread <= kWeightSpread);
+  float w2max, z2max;
+  sqrt_free_inverse_estimate_sq(f, nrm, &w2max, &z2max);
+  const bool near_singular = inverse_estimate_exceeds(w2max, z2max, static_cast<float>(pivot_threshold)) ||
+                             !(w_spread <= kWeightSpread);
   if (!near_singular && qmax <= flag_threshold * flag_threshold * qmin) return;
   const int tag = static_cast<int>(coff + i);  // (component, cell) of the lists
   if (sizeof(T) == 4) atomicAdd(&counters[0], 1ull);
@@ -435,8 +612,9 @@ __device__ __forceinline__ void recon_tpc_cell(const DeviceMesh& dm, const Schem
       for (int j = k + 1; j < M; ++j) v[4 + 2 * M + strict_upper_index(M, k, j)] = static_cast<float>(f.U[k][j]);
     constexpr int RE = refine_record_eps(M);
     v[RE] = static_cast<float>(eh2);
-    v[RE + 1] = __int_as_float(__double2loint(ui));
-    v[RE + 2] = __int_as_float(__double2hiint(ui));
+    const double ui_rec = sizeof(T) == 4 && fdev && !coeffs ? ubar[i] : ui;
+    v[RE + 1] = __int_as_float(__double2loint(ui_rec));
+    v[RE + 2] = __int_as_float(__double2hiint(ui_rec));
 #pragma unroll
     for (int c = RE + 3; c < RW; ++c) v[c] = 0.0f;
     const int slot = atomicAdd(&work.counts[1], 1);
@@ -483,6 +661,18 @@ recon_tpc_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTR
 // the main kernel's outputs for those cells.
 // The sweep for global thread gt of nthreads (whole warps): the kernel's body
 // and the refinement phase of the persistent step.
+// The traces of an all-components context (its work carries the
+// positivity flags; fdev then holds [N][NP][C] traces), else none.
+__host__ __device__ inline TraceOut trace_out(const ReconOut& out, const TpcWork& work) {
+  TraceOut tr;
+  if (work.pos_ok) {
+    tr.base = out.fdev;
+    tr.upair = work.upair;
+    tr.pos_ok = work.pos_ok;
+  }
+  return tr;
+}
+
 template <int DIM, int M, int L, int RPL>
 __device__ __forceinline__ void refine_records(const DeviceMesh& dm, const double* WLSENO_BODY_RESTRICT ubar,
                                                double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals,
@@ -644,7 +834,14 @@ __device__ __forceinline__ void refine_records(const DeviceMesh& dm, const doubl
         sh = fmaf(xh[c], mono[c], sh);
         sl = fmaf(dl[c], mono[c], sl);
       }
-      if (fdev)
+      if (work.pos_ok) {
+        // all-components context: the component's trace, where used
+        constexpr int TC = DIM + 2;
+        if (work.pos_ok[i]) {
+          const float2 pc = work.upair[i * TC + comp];
+          fdev[(i * NP + lane) * TC + comp] = pc.x + (pc.y + (sh + sl));
+        }
+      } else if (fdev)
         fdev[(comp * dm.N + i) * NP + lane] = sh + sl;
       else
         fvals[(comp * dm.N + i) * NP + lane] = ui + static_cast<double>(sh) + static_cast<double>(sl);
@@ -695,9 +892,10 @@ cudaError_t launch_recon_tpc(const DeviceMesh& dm, const SchemeParams& sp, const
 template <typename T, int DIM, int M>
 cudaError_t launch_list(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
                         const ReconOut& out, const TpcWork& work, cudaStream_t s) {
+  const TraceOut tr = trace_out(out, work);
   if (dm.nmax <= 40)
-    return launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, work.group_list, work.counts, s);
-  return launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, work.group_list, work.counts, s);
+    return launch_reconstruct_list<T, DIM, M, 8, 5>(dm, sp, ubar, out, work.group_list, work.counts, s, tr);
+  return launch_reconstruct_list<T, DIM, M, 16, 4>(dm, sp, ubar, out, work.group_list, work.counts, s, tr);
 }
 
 // The follow-ups on the listed cells: the refinement sweep (FP32-bulk) and

@@ -213,7 +213,7 @@ __device__ __forceinline__ void group_reconstruct_cell(
     const DeviceMesh& dm, const SchemeParams& sp, const double* WLSENO_BODY_RESTRICT ubar,
     double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
     unsigned long long* WLSENO_BODY_RESTRICT counters, unsigned char* smem_raw, int g, int gib,
-    int64_t cell, bool valid, bool listed) {
+    int64_t cell, bool valid, bool listed, const TraceOut& tr = TraceOut{}, int comp = 0) {
   constexpr int NF = DIM + 1;
   constexpr int NQ = nq_of(DIM);
   constexpr int NP = NF * NQ;
@@ -425,7 +425,16 @@ __device__ __forceinline__ void group_reconstruct_cell(
       sh += chi[c] * mono[c];
       sl += clo[c] * mono[c];
     }
-    if (fdev) {
+    if (tr.base) {
+      // the component's trace, in a cell whose traces are used
+      const float dv = static_cast<float>(sh) + static_cast<float>(sl);
+      constexpr int TC = DIM + 2;
+      if (tr.pos_ok[cell]) {
+        const float2 pc = tr.upair[cell * TC + comp];
+        tr.base[(cell * NP + pt) * TC + comp] = pc.x + (pc.y + dv);
+      }
+      finite = finite && isfinite(dv);
+    } else if (fdev) {
       const float dv = static_cast<float>(sh) + static_cast<float>(sl);
       fdev[cell * NP + pt] = dv;
       finite = finite && isfinite(dv);
@@ -465,7 +474,8 @@ __device__ __forceinline__ void reconstruct_listed(const DeviceMesh& dm, const S
                                                    double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
                                                    unsigned long long* WLSENO_BODY_RESTRICT counters,
                                                    const int* WLSENO_BODY_RESTRICT worklist, const int* WLSENO_BODY_RESTRICT wl_count,
-                                                   unsigned char* smem_raw, int64_t block, int64_t nblocks) {
+                                                   unsigned char* smem_raw, int64_t block, int64_t nblocks,
+                                                   const TraceOut& tr = TraceOut{}) {
   const int count = *reinterpret_cast<const volatile int*>(wl_count);
   const int gpb = blockDim.x / G;
   const int gib = threadIdx.x / G;
@@ -480,8 +490,9 @@ __device__ __forceinline__ void reconstruct_listed(const DeviceMesh& dm, const S
     constexpr int NP = (DIM + 1) * nq_of(DIM);
     const int64_t off = comp * dm.N;
     group_reconstruct_cell<T, DIM, M, G, R>(dm, sp, ubar + off, coeffs ? coeffs + off * M : nullptr,
-                                            fvals ? fvals + off * NP : nullptr, fdev ? fdev + off * NP : nullptr,
-                                            counters, smem_raw, threadIdx.x % G, gib, cell, valid, true);
+                                            fvals ? fvals + off * NP : nullptr,
+                                            fdev && !tr.base ? fdev + off * NP : nullptr, counters, smem_raw,
+                                            threadIdx.x % G, gib, cell, valid, true, tr, static_cast<int>(comp));
   }
 }
 
@@ -490,16 +501,16 @@ __global__ void __launch_bounds__(128)
 reconstruct_list_kernel(DeviceMesh dm, SchemeParams sp, const double* WLSENO_BODY_RESTRICT ubar,
                         double* WLSENO_BODY_RESTRICT coeffs, double* WLSENO_BODY_RESTRICT fvals, float* WLSENO_BODY_RESTRICT fdev,
                         unsigned long long* WLSENO_BODY_RESTRICT counters, const int* WLSENO_BODY_RESTRICT worklist,
-                        const int* WLSENO_BODY_RESTRICT wl_count) {
+                        const int* WLSENO_BODY_RESTRICT wl_count, TraceOut tr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   reconstruct_listed<T, DIM, M, G, R>(dm, sp, ubar, coeffs, fvals, fdev, counters, worklist, wl_count, smem_raw,
-                                      blockIdx.x, gridDim.x);
+                                      blockIdx.x, gridDim.x, tr);
 }
 
 template <typename T, int DIM, int M, int G, int R>
 cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp,
                                     const double* ubar, const ReconOut& out, const int* worklist,
-                                    const int* wl_count, cudaStream_t s) {
+                                    const int* wl_count, cudaStream_t s, const TraceOut& tr = TraceOut{}) {
   constexpr int threads = 128;
   const size_t smem = recon_smem_per_cell<T, M, G, R>() * (threads / G);
   // set before every launch: the attribute belongs to the current device's
@@ -512,7 +523,7 @@ cudaError_t launch_reconstruct_list(const DeviceMesh& dm, const SchemeParams& sp
   const int64_t groups = (dm.N * G + threads - 1) / threads;
   const unsigned blocks = static_cast<unsigned>(groups < 152 * 2 ? groups : 152 * 2);
   reconstruct_list_kernel<T, DIM, M, G, R><<<blocks, threads, smem, s>>>(
-      dm, sp, ubar, out.coeffs, out.fvals, out.fdev, out.counters, worklist, wl_count);
+      dm, sp, ubar, out.coeffs, out.fvals, out.fdev, out.counters, worklist, wl_count, tr);
   return cudaGetLastError();
 }
 

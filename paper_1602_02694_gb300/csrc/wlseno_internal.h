@@ -154,6 +154,7 @@ struct SchemeParams {
   double vel[3];
   double eps, alpha_c, rank_tol, kappa_flag;
   double gamma;             // Euler: ratio of specific heats
+  float alpha_c32;          // alpha_c rounded to FP32 on the host (FP32-bulk weights)
 };
 
 // Euler (k_euler.cu): fvals/u/out are [4][N]-major per component.
@@ -170,13 +171,12 @@ cudaError_t launch_euler_char(const DeviceMesh& dm, const SchemeParams& sp, int 
 cudaError_t launch_euler_speed(const DeviceMesh& dm, double gamma, const double* ubar,
                                unsigned long long* lmax_bits, int n_meshes, cudaStream_t s);
 // FP32-bulk 2-D Euler (k_euler32.cu): out = a u0 + b (u + dt L(u)) (or L(u))
-// from the FP32 trace deviations fdev [4][N][6] of the all-components
-// reconstruction, its positivity flags and the interleaved pairs pin / p0
-// ([N][4]) of u and u0; pout (may be null) receives the pairs of out.
-cudaError_t launch_euler2_flux32(const DeviceMesh& dm, double gamma, const float* fdev,
-                                 const unsigned char* pos_ok, const float2* pin, const float2* p0,
-                                 double a, double b, const float2* dt2, bool residual_only, double* out,
-                                 unsigned long long* counters, float2* pout, cudaStream_t s);
+// from the FP32 traces [N][6][4] of the all-components reconstruction
+// (TraceOut) and the interleaved pairs pin / p0 ([N][4]) of u and u0; pout
+// (may be null) receives the pairs of out.
+cudaError_t launch_euler2_flux32(const DeviceMesh& dm, double gamma, const float* traces, const float2* pin,
+                                 const float2* p0, double a, double b, const float2* dt2, bool residual_only,
+                                 double* out, unsigned long long* counters, float2* pout, cudaStream_t s);
 // The interleaved FP32 pairs of the 2-D Euler state and, in the same pass,
 // the largest |u| + c per mesh (FP32, as double bits) for the CFL step.
 cudaError_t launch_euler2_speed_pairs32(const DeviceMesh& dm, double gamma, const double* u,
@@ -184,6 +184,18 @@ cudaError_t launch_euler2_speed_pairs32(const DeviceMesh& dm, double gamma, cons
                                         cudaStream_t s);
 // pairs[i][c] = FP32 pair of u[c][i] (the four components of 2-D Euler).
 cudaError_t launch_euler2_split_pairs(const double* u, float2* pairs, int64_t N, cudaStream_t s);
+
+// All-components (FP32-bulk 2-D Euler) contexts: the facet values travel as
+// FP32 traces of the C = dim + 2 components together, base[(i NP + pt) C + c]
+// = hi + (lo + dev) of component c at point pt of cell i, or hi + lo for
+// every component where the cell's positivity flag is down (the
+// reconstruction writes them; its follow-ups update the components they
+// redo, in cells whose flag is up).
+struct TraceOut {
+  float* base = nullptr;                // [N][NP][C], or null: no traces
+  const float2* upair = nullptr;        // [N][C] pairs of the averages
+  const unsigned char* pos_ok = nullptr;  // [N]
+};
 
 struct ReconOut {
   double* coeffs;           // [N][m] or null
@@ -238,7 +250,8 @@ struct TpcWork {
   // components of a multi-component context are reconstructed together)
   int64_t capacity = 0;
   // multi-component (2-D Euler, FP32-bulk) kernel: the per-cell positivity
-  // flags it writes (1: the traces are used, 0: the averages) and gamma
+  // flags it writes (1: the traces are used, 0: the averages) and gamma;
+  // when set, the facet outputs (ReconOut::fdev) are the traces of TraceOut
   unsigned char* pos_ok = nullptr;
   float gamma = 0.0f;
 };
@@ -287,9 +300,10 @@ WLSENO_DECLARE_TPC(float, 3, 10)
 
 // FP32-bulk 2-D Euler, p = 3: the main kernel for all four components at once
 // (one thread per (cell, component), the state pairs work.upair interleaved
-// [N][4], ubar the [4][N] state) with the positivity flags work.pos_ok; the
-// flagged (component, cell) pairs are finished by
-// launch_recon_fixup_inst<float, 2, 6> on the same outputs.
+// [N][4], ubar the [4][N] state) with the positivity flags work.pos_ok and
+// the traces [N][6][4] in out.fdev (TraceOut); the flagged (component, cell)
+// pairs are finished by launch_recon_fixup_inst<float, 2, 6> on the same
+// outputs.
 cudaError_t launch_recon_euler2d(const DeviceMesh& dm, const SchemeParams& sp, const double* ubar,
                                  const ReconOut& out, const TpcWork& work, cudaStream_t s);
 

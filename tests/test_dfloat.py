@@ -90,3 +90,36 @@ def test_exact_cancellation_and_zero(probe):
     for line in out[:3]:
         hi, lo = (float.fromhex(t) for t in line.split())
         assert hi == 0.0 and lo == 0.0
+
+
+def test_integer_split_equals_the_fp64_split(probe):
+    # df_from_double_bits against df_from_double on bit patterns chosen to
+    # reach every branch: exponents across the whole range and at the edges
+    # of the integer path, remainders at the rounding tie (odd and even
+    # kept mantissa), zero remainders, all-ones mantissas (carry into the
+    # exponent), both signs, zeros, subnormals, infinities and NaN; and the
+    # FP64 bits of |fl32(v)| from df_f64_bits_nonneg
+    rng = np.random.default_rng(11)
+    pats = []
+    exps = list(range(940, 960)) + list(range(1130, 1150)) + list(rng.integers(0, 2048, 200)) + [1023] * 50
+    for E in exps:
+        for sign in (0, 1):
+            for kind in range(6):
+                m = int(rng.integers(0, 1 << 52, dtype=np.uint64))
+                if kind == 1:
+                    m = (m & ~((1 << 29) - 1)) | (1 << 28)  # tie
+                elif kind == 2:
+                    m = (m & ~((1 << 29) - 1))  # exact in FP32
+                elif kind == 3:
+                    m = (1 << 52) - 1  # carry into the exponent
+                elif kind == 4:
+                    m = (m & ~((1 << 29) - 1)) | (1 << 28) | (1 << 29)  # tie, odd kept mantissa
+                pats.append((sign << 63) | (int(E) << 52) | m)
+    pats += [0, 1 << 63, 0x7ff0000000000000, 0xfff0000000000000, 0x7ff8000000000000, 1, 0x000fffffffffffff,
+             0x3ff0000000000000, 0x47efffffe0000000, 0x47efffffefffffff]
+    pats += [int(b) for b in rng.integers(0, 1 << 63, 3000, dtype=np.uint64)]
+    text = "\n".join(f"{p:x}" for p in pats)
+    out = subprocess.run([probe, "split"], input=text + "\n", capture_output=True, text=True,
+                         check=True).stdout.split("\n")
+    bad = [f"{p:x}" for p, line in zip(pats, out) if line.strip() != "1 1"]
+    assert len(out) >= len(pats) and not bad, bad[:10]
