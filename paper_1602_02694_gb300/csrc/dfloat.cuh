@@ -69,8 +69,8 @@ __host__ __device__ __forceinline__ dfloat df_from_double(double v) {
 
 // The same pair from the bits of v by integer arithmetic alone (no FP64
 // instruction: on this part the FP64 pipe is the narrow one), where hi and
-// lo are normal FP32 numbers (binary exponent of v in [-73, 117]); other
-// values take df_from_double.  With v = (-1)^s (2^52 + m) 2^(e - 52): hi
+// lo are normal FP32 numbers (binary exponent of v in [-73, 117]) and for
+// zeros; other values take df_from_double.  With v = (-1)^s (2^52 + m) 2^(e - 52): hi
 // keeps the top 23 bits of m rounded to nearest, ties to even (a carry out
 // of the mantissa moves into the exponent field, as it should); the
 // remainder r = (m mod 2^29) - 2^29 [rounded up] is v - hi in units of
@@ -82,6 +82,12 @@ __host__ __device__ __forceinline__ dfloat df_from_double_bits(double v) {
   std::memcpy(&b, &v, sizeof b);
   const uint32_t hw = static_cast<uint32_t>(b >> 32);
   const int E = static_cast<int>((hw >> 20) & 0x7ffu);
+  if ((b << 1) == 0) {  // +-0: (+-0, +0)
+    const uint32_t zb = hw & 0x80000000u;
+    float z;
+    std::memcpy(&z, &zb, sizeof z);
+    return {z, 0.0f};
+  }
   if (E < 950 || E > 1140) return df_from_double(v);
   const uint32_t top = static_cast<uint32_t>(b >> 29) & 0x7fffffu;
   const uint32_t rem = static_cast<uint32_t>(b) & 0x1fffffffu;
