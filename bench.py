@@ -706,16 +706,16 @@ def roofline(wl, info, diag, precision, peaks):
 # proportion to its cells (every cell streams its own records), so the figure
 # is scaled to the workload's cell count.  Once the kernel sources change the
 # counters no longer describe the kernel and the traffic is reported as null.
-TRAFFIC_SOURCES_DIGEST = "d2726909aff6"
+TRAFFIC_SOURCES_DIGEST = "cd16d09a605a"
 TRAFFIC_BYTES_PER_CELL = {
-    ("euler1024", "fp32_bulk", "reconstruct", False): (590.06, "512x512 triangles, 2 launches"),
-    ("euler1024", "fp64", "reconstruct", False): (841.05, "512x512 triangles, 4 launches"),
-    ("burgers256", "fp32_bulk", "reconstruct", True): (725.62, "256x256 triangles, 1 launch"),
-    ("burgers256", "fp32_bulk", "reconstruct", False): (1892.42, "256x256 triangles, 1 launch"),
-    ("burgers256", "fp64", "reconstruct", False): (3290.05, "256x256 triangles, 1 launch"),
-    ("advection3d64", "fp32_bulk", "reconstruct", True): (968.32, "32^3 Kuhn tetrahedra, 1 launch"),
-    ("advection3d64", "fp32_bulk", "reconstruct", False): (2319.77, "32^3 Kuhn tetrahedra, 1 launch"),
-    ("advection3d64", "fp64", "reconstruct", False): (4296.23, "32^3 Kuhn tetrahedra, 1 launch"),
+    ("euler1024", "fp32_bulk", "reconstruct", False): (589.80, "512x512 triangles, 2 launches"),
+    ("euler1024", "fp64", "reconstruct", False): (841.71, "512x512 triangles, 4 launches"),
+    ("burgers256", "fp32_bulk", "reconstruct", True): (722.61, "256x256 triangles, 1 launch"),
+    ("burgers256", "fp32_bulk", "reconstruct", False): (1889.00, "256x256 triangles, 1 launch"),
+    ("burgers256", "fp64", "reconstruct", False): (3293.07, "256x256 triangles, 1 launch"),
+    ("advection3d64", "fp32_bulk", "reconstruct", True): (968.07, "32^3 Kuhn tetrahedra, 1 launch"),
+    ("advection3d64", "fp32_bulk", "reconstruct", False): (2320.60, "32^3 Kuhn tetrahedra, 1 launch"),
+    ("advection3d64", "fp64", "reconstruct", False): (4294.70, "32^3 Kuhn tetrahedra, 1 launch"),
 }
 
 

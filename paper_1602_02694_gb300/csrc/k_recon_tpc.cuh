@@ -105,6 +105,22 @@ __device__ __forceinline__ void sqrt_free_fold(SqrtFreeQR<T, M>& f, T (&z)[M + 1
   }
 }
 
+// The first row folded into a fresh factor (d_k = tau, U = 0), as far as row
+// 0 of the factor: its z_0 = 1 (the constant column) is absorbed there,
+// leaving a weight of tau delta / (tau + delta), about tau, for the rows
+// below, where the full fold would put entries weighted at the scale of tau,
+// far below the rounding of any row that follows.  (z_0 != 0 for every row
+// of the moment matrix, whose constant column is 1.)
+template <typename T, int M>
+__device__ __forceinline__ void sqrt_free_fold_first(SqrtFreeQR<T, M>& f, const T (&z)[M + 1], T delta) {
+  const T t = delta * z[0];
+  const T dn = fma(t, z[0], f.d[0]);
+  const T sbar = t * recip_t<T>(dn);
+  f.d[0] = dn;
+#pragma unroll
+  for (int j = 1; j <= M; ++j) f.U[0][j] = sbar * z[j];  // U[0][j] was 0: z_j unchanged by row 0
+}
+
 // Spread of the row weights above which the FP64 thread-per-cell kernel
 // sends a cell to the pivoted path (see sqrt_free_fold).
 constexpr double kWeightSpread = 1e6;

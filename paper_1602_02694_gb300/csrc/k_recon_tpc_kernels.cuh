@@ -247,6 +247,21 @@ __device__ __forceinline__ void tpc_fold_chunked(const DeviceMesh& dm, const flo
     z[M] = dev;
     sqrt_free_fold(f, z, w * w);
   };
+  // the centre row (row 0, the cell itself: ubar_j - ubar_i = 0), the first
+  // row folded
+  auto fold_centre = [&]() {
+    float z[M + 1];
+#pragma unroll
+    for (int k = 0; k < W4; ++k) {
+      const float4 v = srec[0][0][k][cell];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * k + q < M) z[4 * k + q] = vv[q];
+    }
+    z[M] = 0.0f;
+    sqrt_free_fold_first(f, z, w_centre * w_centre);
+  };
   cp_async_wait<0>();
   __syncwarp(lanes);
   fetch_u(0);
@@ -259,7 +274,11 @@ __device__ __forceinline__ void tpc_fold_chunked(const DeviceMesh& dm, const flo
     if ((c + 2) * kChunk < n) fetch_rec(c + 2);
     cp_async_commit();
     const int slot = c % 3, us = c % 2, t0 = c * kChunk;
-    if (t0 + kChunk <= n) {
+    if (c == 0 && kChunk <= n) {
+      fold_centre();
+#pragma unroll
+      for (int r = 1; r < kChunk; ++r) fold_row(0, 0, r, r);
+    } else if (t0 + kChunk <= n) {
 #pragma unroll
       for (int r = 0; r < kChunk; ++r) fold_row(slot, us, r, t0 + r);
     } else {

@@ -37,13 +37,13 @@ def probe(tmp_path_factory):
     return exe
 
 
-def solve(probe, problems):
+def solve(probe, problems, args=()):
     lines = []
     for w, A, b in problems:
         lines.append(str(len(w)))
         for t in range(len(w)):
             lines.append(" ".join(repr(float(v)) for v in [w[t], *A[t], b[t]]))
-    out = subprocess.run([probe], input="\n".join(lines) + "\n", capture_output=True, text=True,
+    out = subprocess.run([probe, *args], input="\n".join(lines) + "\n", capture_output=True, text=True,
                          check=True).stdout.split("\n")
     res = []
     for k in range(len(problems)):
@@ -135,3 +135,32 @@ def test_truncated_cells_reach_the_pivoted_path(probe):
     assert all(routed)
     # the weight spread is what catches the cells both estimates miss
     assert any(qmax <= 1e12 * qmin and est <= 1e6 for _, qmax, qmin, est in res)
+
+
+def test_first_row_folded_into_row_zero_only(probe):
+    # the centre row folded into a fresh factor as far as its row 0 (the
+    # constant column is 1 in every moment row): the same least-squares
+    # solution as the full fold, and the same conditioning tests, for
+    # weights over four decades, the centre weight among them
+    rng = np.random.default_rng(8)
+    problems = []
+    for n in (13, 13, 37, 19):
+        A = rng.normal(size=(n, M)) * np.exp(rng.uniform(-2, 2, M))[None, :]
+        A[:, 0] = 1.0
+        A[0, 1:3] = 0.0  # the centre row's first moments about its own centroid
+        w = np.exp(rng.uniform(-4, 0, n))
+        b = rng.normal(size=n)
+        b[0] = 0.0
+        problems.append((w, A, b))
+    full = solve(probe, problems)
+    head = solve(probe, problems, ("first",))
+    for (w, A, b), (x0, qmax0, qmin0, est0), (x1, qmax1, qmin1, est1) in zip(problems, full, head):
+        WA = w[:, None] * A
+        want = np.linalg.lstsq(WA, w * b, rcond=None)[0]
+        S = 1.0 / np.linalg.norm(WA, axis=0)
+        kappa = np.linalg.cond(WA * S[None, :])
+        scale = max(1.0, np.max(np.abs(want)))
+        assert np.max(np.abs(x1 - want)) <= 1e-9 * kappa * scale
+        assert np.max(np.abs(x1 - x0)) <= 1e-9 * kappa * scale
+        assert abs(qmax1 / qmin1 - qmax0 / qmin0) <= 1e-9 * qmax0 / qmin0
+        assert abs(est1 - est0) <= 1e-5 * est0
