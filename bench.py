@@ -127,7 +127,7 @@ def euler_recon_bytes_per_cell(n, m, npts, dim, on_the_fly):
     per cell: the stencil rows (stored FP32 moments, or offset records and the
     cell's own moments), the indices, the four components' FP32 pairs, h,
     facet neighbours and points, the positivity flag and the four components'
-    FP32 trace deviations."""
+    FP32 traces written."""
     C = dim + 2
     rows = n * 16 + ((m - 1 - dim + 3) // 4) * 16 if on_the_fly else n * ((m + 1 + 3) // 4) * 16
     return rows + 4 + 8 * C + 8 + 4 * (dim + 1) + npts * dim * 4 + 1 + 4 * C * npts
@@ -135,12 +135,13 @@ def euler_recon_bytes_per_cell(n, m, npts, dim, on_the_fly):
 
 def flux_bytes_per_cell(dim, npts, comps, euler):
     """Bytes a flux / RK-stage kernel must move once per cell (each input
-    datum once): the trace deviations and FP32 pairs of the state and of
-    u0 for every component, facet neighbours, facet coefficients (16 bytes
-    each), the 1/|tau| pair, and the FP64 state and pairs written."""
+    datum once): the FP32 facet values (trace deviations; for the FP32
+    Euler kernel the finished traces of all components, positivity applied)
+    and the FP32 pairs of the state and of u0 for every component, facet
+    neighbours, facet coefficients (16 bytes each), the 1/|tau| pair, and
+    the FP64 state and pairs written."""
     nf = dim + 1
-    b = comps * (4 * npts + 8 + 8) + 4 * nf + 16 * nf + 8 + comps * (8 + 8)
-    return b + (1 if euler else 0)
+    return comps * (4 * npts + 8 + 8) + 4 * nf + 16 * nf + 8 + comps * (8 + 8)
 
 
 class ClockSampler:

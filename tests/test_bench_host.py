@@ -108,7 +108,9 @@ def test_euler_and_flux_algorithmic_bytes():
     # scalar double-float flux: deviations, pairs of u and u0, neighbours,
     # facet records, 1/|tau|, FP64 state and pairs written
     assert bench.flux_bytes_per_cell(2, 6, 1, False) == 6 * 4 + 8 + 8 + 12 + 48 + 8 + 16
-    assert bench.flux_bytes_per_cell(2, 6, 4, True) == 4 * (24 + 16) + 12 + 48 + 8 + 4 * 16 + 1
+    # FP32 Euler: the traces of the four components instead of deviations
+    # and positivity flags
+    assert bench.flux_bytes_per_cell(2, 6, 4, True) == 4 * (24 + 16) + 12 + 48 + 8 + 4 * 16
 
 
 def test_measured_traffic_only_for_the_captured_kernel_sources(monkeypatch):
