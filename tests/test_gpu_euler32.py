@@ -9,7 +9,9 @@ C ABI, against the FP64 oracle:
 * the same fallback cells as the oracle's FP64 decisions;
 * exact discrete conservation over 20 steps;
 * agreement with the one-component kernels (lane-group shape) after three
-  steps, and cells flagged in every component refined."""
+  steps, cells flagged in every component refined, and every component
+  sent through the pivoted path with rank truncation (the follow-ups
+  rewrite their component of the cell's traces)."""
 import numpy as np
 import pytest
 
@@ -124,3 +126,32 @@ def test_fp32_flagged_components_are_refined(dev):
     for c in range(4):
         assert rel_l1(got[c], ref[c]) <= 1e-5, (c, rel_l1(got[c], ref[c]))
     ctx.close()
+
+
+def test_fp32_pivoted_components_update_their_traces(dev):
+    """rank_tol = 1e-2 sends every (cell, component) of the all-components
+    kernel to the pivoted lane-group path (QR with column pivoting, the rank
+    rule and basic solution of Sec. 3.3.2, FP64-residual refinement), which
+    rewrites that component of the cell's FP32 traces: the residual must
+    match the FP64 oracle's with the same tolerance, the same count of
+    rank-deficient (cell, component) systems, and every component (observed
+    max relative L1 printed on failure)."""
+    mesh = synth.tri_mesh(12, jitter=0.2, seed=1, periodic=False)
+    U = synth.euler_quadrant_initial(mesh, seed=3)[0]
+    prob = O.Problem(mesh.vertices, mesh.cells, mesh.period, p=3, ring=1.0, pde=O.EULER, min_rows=9,
+                     rank_tol=1e-2)
+    ref = O.residual(prob, U)
+    assert np.all(O.euler_positive(prob, U, O.euler_coeffs(prob, U)))
+    ctx = Context(pde="euler", precision="fp32_bulk", rank_tol=1e-2)
+    ctx.build_stencils(mesh, order_p=3, ring=1.0, min_rows=9)
+    ctx.precompute_moments()
+    u = torch.tensor(U).cuda().contiguous()
+    L = torch.empty_like(u)
+    ctx.flux_residual(u, L)
+    d = ctx.diagnostics()
+    ctx.close()
+    assert d["flagged_cells"] == 4 * prob.N and d["nonfinite"] == 0
+    assert d["rank_deficient"] > 0
+    got = L.cpu().numpy()
+    errs = [rel_l1(got[c], ref[c]) for c in range(4)]
+    assert max(errs) <= 1e-5, errs
