@@ -51,7 +51,9 @@ the design notes of the repository):
 
 Parity of every function here is pinned: the scheme in tests/test_oracle_pins.py,
 Euler in tests/test_oracle_euler.py, the geometry, facet rules, adjacency,
-radius-cut stencils and CFL wave speeds in tests/test_oracle_geometry.py.
+radius-cut stencils and CFL wave speeds in tests/test_oracle_geometry.py, the
+reverse mode (residual_vjp, rk3_step_vjp) against central differences of
+the forward in tests/test_oracle_adjoint.py.
 """
 from __future__ import annotations
 
@@ -494,6 +496,19 @@ class Problem:
         return total
 
 
+    def basis(self, i, x):
+        """The values phi_kappa(y) = prod y_c^kappa_c / kappa_c! at the point x
+        (y = (x - x_i) / h_i): eval_poly(d, i, x) = d . basis(i, x)."""
+        y = (np.asarray(x) - self.geo.centroid[i]) / self.geo.h[i]
+        out = np.empty(len(self.kappas))
+        for k, kap in enumerate(self.kappas):
+            term = 1.0
+            for c, e in enumerate(kap):
+                term *= y[c] ** e / math.factorial(e)
+            out[k] = term
+        return out
+
+
 # ----------------------------------------------------------------------------
 # facet quadrature and the Lax-Friedrichs flux (Sec. 1, Eq. (flux))
 # ----------------------------------------------------------------------------
@@ -931,3 +946,132 @@ def rk3_run(prob, ubar, n_steps, cfl=None, dt=None):
         u = rk3_step(lambda x: residual(prob, x), u, step)
         dts.append(step)
     return u, dts
+
+
+# ----------------------------------------------------------------------------
+# reverse mode (the adjoint) of the residual and of one TVD-RK3 step, scalar
+# equations.  The paper has no adjoint; this differentiates its scheme as
+# written above, step by step in reverse:
+#   L_i = -(1/|tau_i|) sum_f g_f (Eq. (fvm)), g_f the facet integral of the
+#   LF flux of Eq. (flux) with its per-facet alpha (Burgers: the maximum of
+#   |F'(u).n| over the facet's points and both sides, taken at the first
+#   maximiser in the order of facet_flux);
+#   the traces u(x_q) = d_i . phi_i(x_q) of each cell's polynomial;
+#   each cell's weighted least-squares solution (Sec. 3.1.1, rows times
+#   omega_j) in its full-rank normal form d = G^-1 A^T W^2 u_S with
+#   G = A^T W^2 A, whose differential is G dd = A^T W^2 du_S +
+#   A^T d(W^2) (u_S - A d); with lambda = G^-1 dbar this gives
+#   u_S-bar = W^2 A lambda and omega_j-bar = 2 omega_j (A lambda)_j r_j;
+#   the weights of Sec. 3.1.2, omega_j = 1/beta_j, omega_i = alpha_c/beta_i,
+#   beta_j = (u_j - u_i)^2 + eps h^2 and beta_i the minimum over the facet
+#   neighbours (at the first minimiser).
+# Full-rank cells only (a truncated cell raises), fixed stencils.
+# ----------------------------------------------------------------------------
+
+def _lf_partials(prob, um, up, n):
+    """dLF/dum, dLF/dup and dLF/dalpha of Eq. (flux) at fixed alpha."""
+    if prob.pde == ADVECTION:
+        an = float(np.dot(np.asarray(prob.velocity[:prob.dim]), n))
+        return lambda alpha: (0.5 * (an + alpha), 0.5 * (an - alpha), -0.5 * (up - um))
+    sn = float(np.sum(n))
+    return lambda alpha: (0.5 * (um * sn + alpha), 0.5 * (up * sn - alpha), -0.5 * (up - um))
+
+
+def residual_vjp(prob, ubar, Lbar):
+    """(dL/dubar)^T Lbar for the scalar equations (advection, Burgers)."""
+    if prob.pde == EULER or prob.balanced:
+        raise ValueError("the adjoint covers the scalar equations on fixed stencils")
+    ubar = np.asarray(ubar, dtype=np.float64)
+    coeffs = []
+    for i in range(prob.N):
+        d, r = prob.reconstruct_cell(ubar, i)
+        if r < prob.m:
+            raise ValueError(f"cell {i}: rank {r} < {prob.m}")
+        coeffs.append(d)
+    # L_i = -flux_out_i / |tau_i|
+    fbar = -np.asarray(Lbar, dtype=np.float64) / prob.geo.volume
+    dbar = [np.zeros(prob.m) for _ in range(prob.N)]
+    for L, fL, R in facets(prob):
+        gbar = fbar[L] - (fbar[R] if R >= 0 else 0.0)
+        pts, w, area, n, um, up = facet_states(prob, coeffs, L, fL, R)
+        if prob.pde == ADVECTION:
+            alpha, arg = normal_speed(prob, 0.0, n), None
+        else:
+            speeds = []
+            for a, b in zip(um, up):
+                speeds.append(max(normal_speed(prob, a, n), normal_speed(prob, b, n)))
+            q_star = int(np.argmax(speeds))
+            alpha = speeds[q_star]
+            a, b = um[q_star], up[q_star]
+            arg = (q_star, "m" if normal_speed(prob, a, n) >= normal_speed(prob, b, n) else "p")
+        umbar = np.zeros(len(w))
+        upbar = np.zeros(len(w))
+        alphabar = 0.0
+        for q in range(len(w)):
+            dm, dp, da = _lf_partials(prob, um[q], up[q], n)(alpha)
+            umbar[q] += gbar * area * w[q] * dm
+            upbar[q] += gbar * area * w[q] * dp
+            alphabar += gbar * area * w[q] * da
+        if arg is not None:  # alpha = |u Sum n| at its first maximiser
+            q, side = arg
+            u_star = um[q] if side == "m" else up[q]
+            dspeed = math.copysign(1.0, u_star * float(np.sum(n))) * float(np.sum(n))
+            if side == "m":
+                umbar[q] += alphabar * dspeed
+            else:
+                upbar[q] += alphabar * dspeed
+        if R < 0:  # transmissive: u+ = u-
+            umbar += upbar
+            upbar[:] = 0.0
+        for q, x in enumerate(pts):
+            dbar[L] += umbar[q] * prob.basis(L, x)
+        if R >= 0:
+            shift = min_image(prob.geo.centroid[R] - prob.geo.centroid[L], prob.period) - \
+                (prob.geo.centroid[R] - prob.geo.centroid[L])
+            for q, x in enumerate(pts):
+                dbar[R] += upbar[q] * prob.basis(R, x - shift)
+    ubar_bar = np.zeros(prob.N)
+    for i in range(prob.N):
+        S = list(prob.stencils[i])
+        face = set(int(j) for j in prob.face_nbrs[i])
+        uS = ubar[S]
+        A = prob.A(i)
+        h = prob.geo.h[i]
+        eh2 = prob.eps * h * h
+        beta = (uS - uS[0]) ** 2 + eh2
+        k_min = min((k for k in range(1, len(S)) if S[k] in face), key=lambda k: (beta[k], k))
+        beta[0] = beta[k_min]
+        omega = 1.0 / beta
+        omega[0] = prob.alpha_c / beta[0]
+        W2 = omega * omega
+        # lambda = G^-1 dbar with G = (W A)^T (W A) = R^T R (R of the QR of W A)
+        Rf = np.linalg.qr(omega[:, None] * A, mode="r")
+        lam = scipy.linalg.solve_triangular(Rf, scipy.linalg.solve_triangular(Rf.T, dbar[i], lower=True))
+        Alam = A @ lam
+        r = uS - A @ coeffs[i]
+        uSbar = W2 * Alam
+        omegabar = 2.0 * omega * Alam * r
+        betabar = -omegabar * omega * omega
+        betabar[0] = -omegabar[0] * omega[0] / beta[0]
+        betabar[k_min] += betabar[0]  # beta_i = beta of its first minimising facet neighbour
+        for k in range(1, len(S)):
+            g = 2.0 * (uS[k] - uS[0]) * betabar[k]
+            uSbar[k] += g
+            uSbar[0] -= g
+        np.add.at(ubar_bar, S, uSbar)
+    return ubar_bar
+
+
+def rk3_step_vjp(prob, ubar, dt, gbar_next):
+    """(d u^{n+1} / d u^n)^T gbar_next for one fixed-dt step of rk3_step."""
+    L = lambda x: residual(prob, x)
+    u = np.asarray(ubar, dtype=np.float64)
+    k1 = u + dt * L(u)
+    k2 = 0.75 * u + 0.25 * k1 + 0.25 * dt * L(k1)
+    g3 = np.asarray(gbar_next, dtype=np.float64)
+    gu = g3 / 3.0
+    g2 = 2.0 / 3.0 * (g3 + dt * residual_vjp(prob, k2, g3))
+    gu += 0.75 * g2
+    g1 = 0.25 * (g2 + dt * residual_vjp(prob, k1, g2))
+    gu += g1 + dt * residual_vjp(prob, u, g1)
+    return gu
