@@ -3,7 +3,9 @@ with the host compiler into a small probe (tests/host_setup_probe.cpp) and
 compared with the oracle: k-ring stencils bit-exact (periodic and
 transmissive, 1-D to 3-D, radius cut, short-stencil growth), geometry to
 rounding, facet neighbours, and the balanced-stencil candidate rings; plus
-the documented errors for an inverted cell and a stencil smaller than m."""
+the documented errors for an inverted cell, a facet shared by three cells,
+a vertex index out of range, a repeated vertex and a stencil smaller than
+m."""
 import math
 import os
 import shutil
@@ -100,3 +102,32 @@ def test_host_setup_reports_mesh_and_stencil_errors(probe):
     line = synth.line_mesh(np.linspace(0.0, 1.0, 6))
     r = run(probe, line, 5, 1.0, min_rows=3)
     assert r["status"] == -3, r  # WLSENO_ERR_STENCIL: 3-cell stencils for m = 5
+
+
+def test_host_setup_reports_malformed_meshes(probe):
+    """The documented MESH errors: a facet shared by three cells (not a
+    manifold), a vertex index out of range and a cell that repeats a vertex
+    (degenerate), each reported with a message naming the problem."""
+    mesh = synth.tri_mesh(4, periodic=False, seed=1)
+    V, Cl = mesh.vertices, mesh.cells
+    # a third triangle on the first cell's edge (v0, v1), apex beyond it
+    v0, v1, v2 = (int(x) for x in Cl[0])
+    apex = V[v0] + V[v1] - V[v2]
+    V3 = np.vstack([V, apex, apex + 0.01])
+    extra = np.array([[v1, v0, len(V)], [v1, v0, len(V) + 1]])
+    cells3 = np.vstack([Cl, extra])
+    # keep every cell positively oriented
+    for c in range(len(Cl), len(cells3)):
+        a, b, e = V3[cells3[c]]
+        if (b[0] - a[0]) * (e[1] - a[1]) - (b[1] - a[1]) * (e[0] - a[0]) < 0:
+            cells3[c, [0, 1]] = cells3[c, [1, 0]]
+    r = run(probe, synth.Mesh(V3, cells3, mesh.period, V3[cells3], n=mesh.n), 3, 1.0, min_rows=9)
+    assert r["status"] == -2 and "more than two" in r["message"], r
+    bad = Cl.copy()
+    bad[3, 2] = len(V) + 7
+    r = run(probe, synth.Mesh(V, bad, mesh.period, mesh.cell_coords, n=mesh.n), 3, 1.0, min_rows=9)
+    assert r["status"] == -2 and "out of range" in r["message"], r
+    rep = Cl.copy()
+    rep[5, 2] = rep[5, 1]
+    r = run(probe, synth.Mesh(V, rep, mesh.period, mesh.cell_coords, n=mesh.n), 3, 1.0, min_rows=9)
+    assert r["status"] == -2, r
