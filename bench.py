@@ -707,7 +707,7 @@ def roofline(wl, info, diag, precision, peaks):
 # proportion to its cells (every cell streams its own records), so the figure
 # is scaled to the workload's cell count.  Once the kernel sources change the
 # counters no longer describe the kernel and the traffic is reported as null.
-TRAFFIC_SOURCES_DIGEST = "cd16d09a605a"
+TRAFFIC_SOURCES_DIGEST = "c5b2d23237d7"
 TRAFFIC_BYTES_PER_CELL = {
     ("euler1024", "fp32_bulk", "reconstruct", False): (589.80, "512x512 triangles, 2 launches"),
     ("euler1024", "fp64", "reconstruct", False): (841.71, "512x512 triangles, 4 launches"),

@@ -248,7 +248,12 @@ typedef struct {
                               the reconstructions of the last call            */
 } wlseno_diagnostics;
 
-/* Create a context on CUDA device `device`; copies *scheme.
+/* Create a context on CUDA device `device`; copies *scheme.  When the
+ * environment variable WLSENO_DEVICE_BYTES_LIMIT holds a positive decimal
+ * integer at this call, the context's device allocations are capped at that
+ * many bytes in total: a call whose allocation would pass the cap returns
+ * WLSENO_ERR_OOM (as a failed cudaMalloc does) and allocates nothing more
+ * (the library's own budget, not the device's free memory).
  * Errors: INVALID_ARG (null, unsupported pde/precision), CUDA. */
 wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* scheme);
 

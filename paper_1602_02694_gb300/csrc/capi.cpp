@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -27,6 +28,8 @@ struct wlseno_ctx {
   bool otf = false;              // FP32-bulk main kernel forms its moment rows on the fly
   DeviceMesh dm{};
   std::vector<void*> allocs;     // every device allocation of the context
+  size_t alloc_bytes = 0;        // their total size
+  size_t alloc_limit = 0;        // WLSENO_DEVICE_BYTES_LIMIT at creation (0: none)
   int32_t* d_st_ptr = nullptr;
   int32_t* d_st_idx = nullptr;
   double* d_rmin = nullptr;
@@ -121,10 +124,16 @@ wlseno_status cuda_fail(wlseno_ctx* ctx, cudaError_t e, const char* where) {
 
 template <typename T>
 wlseno_status dalloc(wlseno_ctx* ctx, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (ctx->alloc_limit > 0 && ctx->alloc_bytes + bytes > ctx->alloc_limit)
+    return fail(ctx, WLSENO_ERR_OOM,
+                "device allocation of " + std::to_string(bytes) + " bytes would exceed the context's limit of " +
+                    std::to_string(ctx->alloc_limit) + " (WLSENO_DEVICE_BYTES_LIMIT)");
   void* raw = nullptr;
-  cudaError_t e = cudaMalloc(&raw, std::max<size_t>(count, 1) * sizeof(T));
+  cudaError_t e = cudaMalloc(&raw, bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
   ctx->allocs.push_back(raw);
+  ctx->alloc_bytes += bytes;
   *p = static_cast<T*>(raw);
   return WLSENO_OK;
 }
@@ -141,6 +150,7 @@ wlseno_status upload(wlseno_ctx* ctx, T** p, const std::vector<T>& v) {
 void free_all(wlseno_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
+  ctx->alloc_bytes = 0;
 }
 
 bool is_device_pointer(const void* p) {
@@ -561,6 +571,11 @@ wlseno_status wlseno_create(wlseno_ctx** out, int device, const wlseno_scheme* s
   wlseno_ctx* ctx = new (std::nothrow) wlseno_ctx();
   if (!ctx) return WLSENO_ERR_OOM;
   ctx->device = device;
+  if (const char* lim = std::getenv("WLSENO_DEVICE_BYTES_LIMIT")) {
+    char* end = nullptr;
+    const unsigned long long v = std::strtoull(lim, &end, 10);
+    if (end != lim && *end == '\0') ctx->alloc_limit = static_cast<size_t>(v);
+  }
   {
     DeviceGuard guard(device);
     void* h = nullptr;
