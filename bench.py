@@ -707,7 +707,7 @@ def roofline(wl, info, diag, precision, peaks):
 # proportion to its cells (every cell streams its own records), so the figure
 # is scaled to the workload's cell count.  Once the kernel sources change the
 # counters no longer describe the kernel and the traffic is reported as null.
-TRAFFIC_SOURCES_DIGEST = "c5b2d23237d7"
+TRAFFIC_SOURCES_DIGEST = "b307f525724b"
 TRAFFIC_BYTES_PER_CELL = {
     ("euler1024", "fp32_bulk", "reconstruct", False): (589.80, "512x512 triangles, 2 launches"),
     ("euler1024", "fp64", "reconstruct", False): (841.71, "512x512 triangles, 4 launches"),
@@ -720,18 +720,44 @@ TRAFFIC_BYTES_PER_CELL = {
 }
 
 
+def strip_c_comments(text):
+    """C/C++ source without its comments and with runs of white space
+    collapsed (string and character literals kept as they are), so that the
+    digest below changes with the code and not with its comments."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_sources_digest():
     """First 12 hex digits of the SHA-256 over the library's CUDA/C++
-    sources (sorted by name), which identifies the kernels a traffic
-    capture describes."""
+    sources (sorted by name, comments and white-space runs left out), which
+    identifies the kernels a traffic capture describes."""
     import hashlib
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1602_02694_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(name.encode())
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update(strip_c_comments(f.read()).encode())
     return h.hexdigest()[:12]
 
 

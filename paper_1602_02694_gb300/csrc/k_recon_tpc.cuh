@@ -296,8 +296,9 @@ __device__ __forceinline__ void tpc_weights(const DeviceMesh& dm, const SchemePa
 }
 
 // The same weights in FP32-bulk from the FP32 pairs of ubar, eps h_i^2 and
-// alpha rounded to FP32 on the host (no FP64 instruction).  The pairs of cell j sit at upair[j * C] (C > 1: the pairs of
-// all components interleaved, upair pointing at this thread's component).
+// alpha rounded to FP32 on the host (no FP64 instruction).  The pairs of
+// cell j sit at upair[j * C] (C > 1: the pairs of all components
+// interleaved, upair pointing at this thread's component).
 template <int DIM, int C = 1>
 __device__ __forceinline__ void tpc_weights_pair(const DeviceMesh& dm, const SchemeParams& sp,
                                                  const float2* WLSENO_BODY_RESTRICT upair, int64_t i, float2 pi,

@@ -88,7 +88,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // by a common multiple of both, so every slot is a compile-time constant.
 // With C > 1 the C threads of a cell share one record slot (each copies part
 // of the record) and order their copies with a barrier over the cell's lanes;
-// the ubar pairs stay per thread.  No block barrier.
+// the ubar pairs stay per thread (the all-components kernel folds its stored
+// rows with tpc_fold_chunked below instead).  No block barrier.
 constexpr int kLeadR = 7, kLeadU = 3, kUnrollS = 8;
 constexpr int kPending = (kLeadU - 1) < (kLeadR - kLeadU - 1) ? (kLeadU - 1) : (kLeadR - kLeadU - 1);
 static_assert(kPending >= 0 && kLeadR > kLeadU && kLeadU >= 1, "prefetch leads");

@@ -127,3 +127,13 @@ def test_measured_traffic_only_for_the_captured_kernel_sources(monkeypatch):
     # (more would mean the capture did not run the kernel the key names)
     alg = bench.euler_recon_bytes_per_cell(13, 6, 6, 2, False)
     assert 0.8 * alg < per_cell < 1.5 * alg
+
+
+def test_source_digest_ignores_comments_not_code():
+    # comments and white-space runs leave the stripped source unchanged;
+    # code, and comment markers inside string literals, do not
+    a = 'int f(int x) {  // twice\n  return 2 * x; /* doubled */ }\nconst char* s = "a // b";'
+    b = "int f(int x) { return 2 * x; }\n// another comment\nconst char* s = \"a // b\";"
+    assert bench.strip_c_comments(a) == bench.strip_c_comments(b)
+    assert bench.strip_c_comments(a) != bench.strip_c_comments(a.replace("2 * x", "3 * x"))
+    assert "a // b" in bench.strip_c_comments(a)
